@@ -1,0 +1,113 @@
+"""Pins of the oracle's graph, partition and halo logic."""
+import itertools
+import math
+import os
+
+import numpy as np
+
+from oracle import graph
+from paper_2606_03140_gb300 import inputs as I
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _load_fig1():
+    box = r_graph = None
+    atoms, cores, halos = [], {}, {}
+    for line in open(os.path.join(GOLD, "fig1_two_waters.txt")):
+        t = line.split()
+        if not t or t[0].startswith("#"):
+            continue
+        if t[0] == "box":
+            box = np.array([float(x) for x in t[1:4]])
+        elif t[0] == "r_graph":
+            r_graph = float(t[1])
+        elif t[0] == "atom":
+            atoms.append((int(t[2]), [float(x) for x in t[3:6]]))
+        elif t[0] == "core":
+            cores[int(t[1])] = [int(x) - 1 for x in t[2:]]
+        elif t[0] == "halo":
+            halos[int(t[1])] = [int(x) - 1 for x in t[2:]]
+    sp = np.array([a[0] for a in atoms], dtype=np.int32)
+    R = np.array([a[1] for a in atoms])
+    return sp, R, box, r_graph, cores, halos
+
+
+def test_fig1_worked_example():
+    """Paper Fig. 1: cores {1,2,3} and {4,5,6}; halos {4,5} and {3}."""
+    sp, R, box, rg, cores_ref, halos_ref = _load_fig1()
+    rp, col = graph.build_graph(R, box, rg)
+    cores = graph.rcb_partition(R, box, 3)
+    assert [list(c) for c in cores] == [cores_ref[1], cores_ref[2]]
+    hal = graph.halos(rp, col, cores)
+    assert [list(h) for h in hal] == [halos_ref[1], halos_ref[2]]
+
+
+def _brute_edges(R, box, rg):
+    N = len(R)
+    E = set()
+    for i, j in itertools.product(range(N), range(N)):
+        if i == j:
+            continue
+        d = [R[j][k] - R[i][k] for k in range(3)]
+        d = [d[k] - box[k] * round(d[k] / box[k]) for k in range(3)]
+        if math.sqrt(sum(x * x for x in d)) < rg:
+            E.add((i, j))
+    return E
+
+
+def test_graph_against_brute_force_with_density_edges():
+    s = I.small_water_box(8, 7.0, seed=11)
+    rp, col = graph.build_graph(s.R, s.box, 2.6)
+    E = {(i, int(col[p])) for i in range(s.n_atoms) for p in range(rp[i], rp[i + 1])}
+    assert E == _brute_edges(s.R, s.box, 2.6)
+    # CSR invariants: symmetric, sorted, no self loops
+    for i in range(s.n_atoms):
+        c = col[rp[i]:rp[i + 1]]
+        assert np.all(np.diff(c) > 0) and i not in c
+    # density edges: one directed entry above tau adds both directions
+    ptr = np.array([0, 1] + [1] * (s.n_atoms - 1), dtype=np.int64)
+    gd = (ptr, np.array([20], dtype=np.int32), np.array([5e-3]))
+    rp2, col2 = graph.build_graph(s.R, s.box, 2.6, gd, 1e-3)
+    E2 = {(i, int(col2[p])) for i in range(s.n_atoms) for p in range(rp2[i], rp2[i + 1])}
+    assert E2 == E | {(0, 20), (20, 0)}
+    gd_low = (ptr, np.array([20], dtype=np.int32), np.array([1e-3]))   # not above tau
+    rp3, col3 = graph.build_graph(s.R, s.box, 2.6, gd_low, 1e-3)
+    assert np.array_equal(col3, col) and np.array_equal(rp3, rp)
+
+
+def test_rcb_sizes_and_cover():
+    s = I.workload("water96")
+    for cs in (12, 7, 32, 96):
+        cores = graph.rcb_partition(s.R, s.box, cs)
+        P = max(1, round(96 / cs))
+        assert len(cores) == P
+        allat = np.sort(np.concatenate(cores))
+        assert np.array_equal(allat, np.arange(96))
+        sizes = [len(c) for c in cores]
+        assert max(sizes) - min(sizes) <= 1 + 96 // P // 8 + 1
+
+
+def test_rcb_split_rule_brute_force():
+    # first split: widest axis, sort by (coordinate, index), first floor(N*floor(P/2)/P)
+    rng = np.random.default_rng(5)
+    R = rng.uniform(0, 10, size=(23, 3))
+    R[:, 1] *= 2.0                           # y is the widest axis
+    R[3, 1] = R[7, 1]                        # a tie broken by atom index
+    box = np.array([30.0, 30.0, 30.0])
+    cores = graph.rcb_partition(R, box, 23 / 3)
+    w = R - box * np.floor(R / box)
+    order = sorted(range(23), key=lambda a: (w[a, 1], a))
+    left = sorted(order[:(23 * 1) // 3])
+    assert list(cores[0]) == left
+
+
+def test_halo_brute_force():
+    s = I.workload("water96")
+    rp, col = graph.build_graph(s.R, s.box, 3.0)
+    cores = graph.rcb_partition(s.R, s.box, 12)
+    hal = graph.halos(rp, col, cores)
+    E = _brute_edges(s.R, s.box, 3.0)
+    for c, h in zip(cores, hal):
+        ref = sorted({j for (i, j) in E if i in set(c)} - set(c))
+        assert list(h) == ref
