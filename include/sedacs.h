@@ -1,0 +1,187 @@
+/*
+ * sedacs.h -- C ABI of the GB300 (sm_103a) engine for graph-based linear-scaling shadow QMD.
+ *
+ * The method is that of arxiv 2606.03140 ("SEDACS: A Scalable Framework for Complex
+ * Chemistry Simulations"): an atom graph from a distance cutoff and the thresholded
+ * atom-condensed density matrix (Sec. "Determining the Subgraphs", Sec. "Dynamic Graph
+ * Adaption"), a core/halo partition (Fig. 1), a dense Fermi-operator solve on every
+ * core+halo principal submatrix at one global chemical potential (Sec. "Matrix Functions
+ * on a Graph", Eqs. 1-3), collection of the core rows into charges, energies and forces,
+ * and extended-Lagrangian shadow Born-Oppenheimer dynamics of the charges (Sec. "Shadow
+ * Molecular Dynamics", Eqs. NEQ/HW; SI Secs. B-C).  The electronic model is a synthetic sp
+ * Slater-Koster SCC tight-binding model whose constants are passed in sedacs_model.
+ *
+ * Conventions (every entry point):
+ *  - Units at the boundary: Angstrom, fs, amu, elementary charge, Hartree.
+ *  - Arrays are caller-owned.  Pointers are HOST pointers unless device I/O is switched
+ *    on with sedacs_set_device_io(), after which every array argument of the compute
+ *    entry points is a DEVICE pointer (cudaMalloc / torch) read and written on the
+ *    stream given there.
+ *  - Positions R are row-major [N][3]; forces and velocities likewise.
+ *  - Charges n, q are net Mulliken electron populations minus the valence count
+ *    (electron excess, e) per atom.
+ *  - Every call returns a sedacs_status; on failure sedacs_last_error() holds a message.
+ *    No C++ exception crosses the boundary.  A context is not thread-safe.
+ *  - The library allocates device memory inside the context; sedacs_destroy frees it.
+ */
+#ifndef SEDACS_H
+#define SEDACS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sedacs_ctx sedacs_ctx;
+
+typedef enum {
+  SEDACS_OK = 0,
+  SEDACS_EINVAL = 1,     /* bad argument or state */
+  SEDACS_ENOMEM = 2,     /* device allocation failed */
+  SEDACS_ECUDA = 3,      /* CUDA runtime error */
+  SEDACS_ENOCONV = 4,    /* SCC did not converge within max_iter */
+  SEDACS_ETIMEOUT = 5,   /* a bounded device wait gave up (kernel returned early) */
+  SEDACS_ENUMERIC = 6,   /* NaN / Inf found in a result */
+  SEDACS_EPRECISION = 7, /* chemical potential could not be placed in a gap */
+  SEDACS_ECAPACITY = 8   /* a fixed-size device buffer was too small */
+} sedacs_status;
+
+/* Synthetic sp Slater-Koster SCC-TB model (SI Sec. D).  Species 0 = H, 1 = C, 2 = O.
+ * v0[i][j][X], X = ss sigma, sp sigma (s on i, p on j), pp sigma, pp pi (Hartree);
+ * V_X(r) = v0 exp(-r/decay) sw(r), quintic switch sw from r_on to r_off (Angstrom);
+ * overlap = overlap_scale * V / (1 Hartree); repulsion rep_a exp(-r/rep_decay) sw(r). */
+typedef struct {
+  int32_t n_orb[3];
+  double eps_s[3], eps_p[3], hubbard_u[3], z_val[3], mass[3];
+  double v0[3][3][4];
+  double decay, overlap_scale, r_on, r_off;
+  double rep_a[3][3];
+  double rep_decay;
+} sedacs_model;
+
+/* Run parameters.  precision: 0 = plain FP64 on the CUDA cores; 1 = FP32-class (every
+ * dense product on tcgen05 tensor cores with three-way bf16 splitting, FP32 accumulation);
+ * 2 = mixed BF16 (SP2 squares with two-way bf16 splitting; S^-1/2 and the core-row
+ * back-transform three-way); 3 = pure bf16 SP2 squares (diagnostic).  In 1-3 the Ewald sums
+ * run in FP32 with FP64 reductions; electron counts, energies and forces are summed in FP64.
+ * kernel: 0 = K0 = -c_k0 I (SI Sec. B); 1 = preconditioned rank-m Krylov (SI Sec. B). */
+typedef struct {
+  double r_graph;       /* distance-graph cutoff, Angstrom */
+  double tau;           /* |D| threshold of the density graph */
+  int32_t core_size;    /* target atoms per core (cores = round(N / core_size)) */
+  int32_t precision;
+  int32_t kernel;
+  int32_t krylov_rank;  /* maximum rank m */
+  double krylov_tol;    /* relative residual tolerance of the low-rank kernel */
+  double c_k0;          /* K0 = -c I */
+  double scc_tol;       /* max |q - n| for SCC convergence, e */
+  double scc_alpha;     /* linear mixing coefficient */
+  double sp2_tol;       /* SP2 stop: Tr(X - X^2) < sp2_tol * n_orbitals */
+  int32_t sp2_kmax;     /* maximum SP2 steps */
+  int32_t ns_iters;     /* Newton-Schulz steps for S^-1/2 */
+  double ewald_tol;     /* relative accuracy of the Ewald sums (0: 1e-12 FP64, 1e-8 mixed) */
+} sedacs_params;
+
+/* Fill p with the defaults (r_graph 3.0, tau 1e-3, core_size 32, precision 1, kernel 0,
+ * krylov_rank 4, krylov_tol 1e-2, c_k0 0.5, scc_tol 1e-8, scc_alpha 0.2, sp2_tol 1e-9,
+ * sp2_kmax 60, ns_iters 6, ewald_tol 0). */
+void sedacs_default_params(sedacs_params* p);
+
+/* Create a context for N atoms of the given species in an orthorhombic periodic box
+ * (box > 2 * r_off on every axis is not required; box > r_off is).  Copies every input. */
+sedacs_status sedacs_create(int32_t n_atoms, const int32_t* species, const double box[3], const sedacs_model* model,
+                            const sedacs_params* params, sedacs_ctx** out);
+void sedacs_destroy(sedacs_ctx* ctx);
+const char* sedacs_last_error(const sedacs_ctx* ctx);
+
+/* Device I/O: on != 0 makes every array argument a device pointer used on `stream`
+ * (a cudaStream_t, may be 0 for the legacy default stream).  on = 0 restores host I/O. */
+sedacs_status sedacs_set_device_io(sedacs_ctx* ctx, int32_t on, void* stream);
+
+/* ---- a1: atom graph (Sec. "Determining the Subgraphs", Fig. 1a/e; Sec. "Dynamic Graph Adaption").
+ * Edge (I,J), I != J, iff the minimum-image distance < r_graph or the density graph
+ * value exceeds tau in either direction.  gd: optional CSR over atoms of the previous
+ * atom-condensed density graph (ptr [N+1] int64, col int32, val double; NULL = none).
+ * use_prev_D != 0 takes the density graph of the last sedacs_subgraph_density call instead.
+ * The graph is kept in the context; *nnz receives its number of directed edges.
+ * Integer result, bit-reproducible (separately rounded IEEE operations, no FMA). */
+sedacs_status sedacs_graph_build(sedacs_ctx* ctx, const double* R, const int64_t* gd_ptr, const int32_t* gd_col,
+                                 const double* gd_val, int64_t gd_nnz, int32_t use_prev_D, int64_t* nnz);
+/* Copy the current graph out: row_ptr [N+1], col [nnz] (columns ascending per row). */
+sedacs_status sedacs_graph_get(sedacs_ctx* ctx, int64_t* row_ptr, int32_t* col);
+
+/* ---- a2: cores and halos (Fig. 1b/c).  Recursive coordinate bisection of the wrapped
+ * positions into round(N/core_size) cores, then the one-hop halo of every core on the
+ * current graph.  *n_parts receives the number of subgraphs. */
+sedacs_status sedacs_partition(sedacs_ctx* ctx, const double* R, int32_t* n_parts);
+/* Use caller-given cores (core_ptr [n_parts+1], core atoms ascending) instead of RCB. */
+sedacs_status sedacs_set_cores(sedacs_ctx* ctx, int32_t n_parts, const int64_t* core_ptr, const int32_t* core);
+/* Recompute the halos of the current cores on the current graph. */
+sedacs_status sedacs_update_halos(sedacs_ctx* ctx);
+/* Sizes of the current subgraphs: *n_parts, total core atoms, total subgraph atoms. */
+sedacs_status sedacs_parts_sizes(sedacs_ctx* ctx, int32_t* n_parts, int64_t* n_sub_atoms);
+/* Subgraph atom lists: sub_ptr [n_parts+1], sub_atoms (core ascending then halo ascending),
+ * n_core [n_parts] (core atoms lead every list). */
+sedacs_status sedacs_parts_get(sedacs_ctx* ctx, int64_t* sub_ptr, int32_t* sub_atoms, int32_t* n_core);
+
+/* ---- a3: Coulomb potential V = gamma b by Ewald summation (SI Sec. D), Hartree per e. */
+sedacs_status sedacs_coulomb_potential(sedacs_ctx* ctx, const double* R, const double* b, double* V);
+
+/* ---- a4-a9: graph-partitioned density (Eqs. 1-3) at trial charges n for the current
+ * graph and subgraphs.  Per subgraph: gather h = H0 + 1/2 (S V + V S) and s, Z = s^-1/2
+ * (Newton-Schulz), h~ = Z h Z, the mu-branch SP2 recursion for the T -> 0 Fermi operator,
+ * core rows D_c = 2 Z_c X Z and W_c = 2 Z_c X h~ Z; then Mulliken charges, band energy and
+ * the density graph.  mu: in = chemical potential (Hartree) or NaN to place it at the middle
+ * of the collected gap; out = the value used.  q [N] out, e_band out (Hartree),
+ * sp2_iters [n_parts] out (nullable). */
+sedacs_status sedacs_subgraph_density(sedacs_ctx* ctx, const double* R, const double* n, double* mu, double* q,
+                                      double* e_band, int32_t* sp2_iters);
+/* Energies of the last density call: e[0] band Tr[D H0], e[1] Coulomb 1/2 (2q - n)^T gamma n,
+ * e[2] repulsion, e[3] total shadow potential (Hartree). */
+sedacs_status sedacs_energy(sedacs_ctx* ctx, double* e);
+/* ---- a10: forces of the last density call at fixed n (Eq. NEQ), Hartree/Angstrom [N][3]. */
+sedacs_status sedacs_forces(sedacs_ctx* ctx, double* F);
+/* Density graph of the last density call: sizes, then rows (core atom I: G^D_IJ over its subgraph). */
+sedacs_status sedacs_density_graph_size(sedacs_ctx* ctx, int64_t* nnz);
+sedacs_status sedacs_density_graph_get(sedacs_ctx* ctx, int64_t* ptr, int32_t* col, double* val);
+/* Dense blocks of subgraph `part` from the last density call (row-major, n x n, FP64 copy):
+ * which = 0 h, 1 s, 2 Z, 3 h~; core rows (n_core_orb x n): 4 D_c, 5 W_c.  *n, *n_core_orb out. */
+sedacs_status sedacs_subgraph_matrix(sedacs_ctx* ctx, int32_t part, int32_t which, double* out, int32_t* n,
+                                     int32_t* n_core_orb);
+
+/* ---- a11: charge response dq/dn v at fixed mu (SI Sec. B, Eq. "dfdv"), by first-order
+ * perturbation of the SP2 recursion on every subgraph, at the state of the last density call. */
+sedacs_status sedacs_charge_response(sedacs_ctx* ctx, const double* v, double* dq);
+/* Kernel action u ~ K f = J^-1 f (SI Sec. B): K0 = -c I (kernel 0) or the preconditioned
+ * rank-m Krylov approximation (kernel 1); *rank receives the rank used. */
+sedacs_status sedacs_kernel_apply(sedacs_ctx* ctx, const double* f, double* u, int32_t* rank);
+
+/* ---- a12: self-consistent charges (Sec. "Determining the Subgraphs", SI Sec. C).  Starting
+ * from n (inout), iterates graph -> halos -> density -> n update until max |q - n| <= scc_tol
+ * (linear mixing, or the kernel quasi-Newton step once max |q - n| < 0.1 when kernel = 1).
+ * Cores must exist (sedacs_partition / sedacs_set_cores).  mu inout as in sedacs_subgraph_density. */
+sedacs_status sedacs_scc_step(sedacs_ctx* ctx, const double* R, double* n, int32_t max_iter, double* mu,
+                              double* resid_max, int32_t* iters);
+
+/* ---- a12: XL-BOMD (Eqs. NEQ/HW; integrator of the paper's refs.: K = 5 dissipation,
+ * kappa 1.82, alpha 0.018).  sedacs_xlbomd_init sets R, V (A/fs), the charge history n0
+ * (normally the SCC solution) and mu, and evaluates forces.  sedacs_xlbomd_step advances
+ * nsteps steps of dt_fs; R, V inout; energies [nsteps][3] (kinetic, shadow potential, total;
+ * Hartree) out, nullable; n_out [N] (nullable) receives the final n. */
+sedacs_status sedacs_xlbomd_init(sedacs_ctx* ctx, const double* R, const double* V, const double* n0, double mu);
+sedacs_status sedacs_xlbomd_step(sedacs_ctx* ctx, double* R, double* V, int32_t nsteps, double dt_fs,
+                                 double* energies, double* n_out);
+
+/* Wall time (ms, CUDA events on the context stream) of the phases of the last call:
+ * t[0] graph+halos, t[1] Coulomb, t[2] gather, t[3] S^-1/2 + h~, t[4] SP2, t[5] collect,
+ * t[6] forces, t[7] kernel + update.  Also the number of kernels launched since the last
+ * sedacs_reset_counters() in *launches. */
+sedacs_status sedacs_phase_times(sedacs_ctx* ctx, double* t, int64_t* launches);
+sedacs_status sedacs_reset_counters(sedacs_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SEDACS_H */

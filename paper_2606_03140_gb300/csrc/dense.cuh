@@ -1,0 +1,67 @@
+// Batched dense kernels on the per-subgraph matrices: problem descriptors shared by the
+// tensor-core (split-bf16, tcgen05) and the FP64 (SIMT) paths.
+#pragma once
+#include "common.cuh"
+
+namespace sedacs {
+
+// One matrix problem of a batched GEMM  C = alpha * A * B^T + beta * I  (B^T: B is read by
+// rows, so for the symmetric operands of the method B^T = B).  Offsets are bytes from
+// the arena base.  For the tensor-core path A and B are blocked split-bf16 planes and the
+// master output is fp32 row-major; for the FP64 path every matrix is fp64 row-major.
+struct GemmMat {
+  long long a_off, b_off;        // operand 0-th plane (tensor path) or matrix (fp64 path)
+  long long a_plane, b_plane;    // bytes between planes
+  long long out_off;             // row-major master output (-1: none)
+  long long outp_off;            // blocked planes output (-1: none; tensor path only)
+  long long outp_plane;
+  long long x_off;               // SP2: master of the current iterate
+  long long buf_stride;          // SP2 ping/pong distance (bytes) for a, b, x and the outputs
+  long long tr_off;              // SP2: trace partial slots (doubles from the slot base)
+  long long c_off;               // response mode: master of X dX (added to the product)
+  int n_pad;                     // row stride of every operand (multiple of 128)
+  int m_real;                    // valid output rows
+  int n_real;                    // valid output columns
+  int k_real;                    // valid inner dimension
+  int b_from_sp2;                // generic mode: B taken from the SP2 result buffer
+  int a_from_sp2;
+  int pad0, pad1;
+};
+
+struct GemmWork {
+  int mat, tm, tn, pad;
+};
+
+// Per-subgraph state of the mu-branch SP2 recursion.
+struct Sp2State {
+  double y;          // image of mu under the polynomial so far
+  double t;          // last idempotency error Tr(X - X^2)
+  double tol;        // stop when t < tol
+  int active;        // 1 while iterating
+  int iters;         // completed steps
+  int cur;           // buffer holding the current iterate
+  int kmax;
+};
+
+// kModeRsp: first-order response step of the SP2 recursion.  With R1 = X dX (c_off) and the
+// product P = dX X: dX <- R1 + P (square branch) or 2 dX - R1 - P (other branch); A, B and
+// x (= dX master) are taken from buffer `cur`, the output goes to buffer 1 - cur.
+enum GemmMode : int { kModeGeneric = 0, kModeSp2 = 1, kModeRsp = 2 };
+
+struct GemmParams {
+  const GemmWork* work;
+  const GemmMat* mats;
+  uint8_t* arena;
+  double* tr_slots;
+  Sp2State* sp2;
+  int* err;
+  int mode;
+  int nsplit_out;     // tensor path: number of bf16 planes written (0..3)
+  float alpha, beta;
+};
+
+// Host launchers (dense.cu)
+void launch_gemm_tc(const GemmParams& p, int n_work, int nsplit, cudaStream_t s);
+void launch_gemm_f64(const GemmParams& p, int n_work, cudaStream_t s);
+
+}  // namespace sedacs

@@ -1,0 +1,356 @@
+// Batched GEMMs over the per-subgraph matrices.
+//
+//  * tc_gemm<NSPLIT>: 5th-generation tensor cores.  One CTA per 128x128 output tile, four
+//    warps.  Thread 0 streams 16 KB operand blocks (already in the swizzled shared-memory
+//    image, see blocked_offset) with bulk copies into a 2-3 stage ring guarded by
+//    mbarriers; thread 32 issues tcgen05.mma (M=128, N=128, K=16, bf16 in, fp32 in TMEM)
+//    over the split products hi*hi (+ hi*mid + mid*hi (+ hi*lo + mid*mid + lo*hi)) and
+//    commits to the ring's "empty" barriers; all four warps then drain TMEM with
+//    tcgen05.ld and run the epilogue (generic alpha*AB^T + beta*I, or one step of the
+//    mu-branch SP2 recursion with its trace partials) writing the fp32 master and the
+//    split planes of the result.
+//  * f64_gemm: the same problems and epilogues in FP64 on the CUDA cores (64x64 tiles).
+#include "dense.cuh"
+
+namespace sedacs {
+
+namespace {
+
+template <int NSPLIT>
+struct TcCfg {
+  static constexpr int kStages = (NSPLIT == 3) ? 2 : 3;
+  static constexpr int kStageBytes = 2 * NSPLIT * kBlkBytes;
+  static constexpr int kSmem = kStages * kStageBytes + 1024 + 256;
+  static constexpr int kNumProd = (NSPLIT == 1) ? 1 : (NSPLIT == 2 ? 3 : 6);
+};
+
+// (a-plane, b-plane) of the kept split products: i + j <= NSPLIT - 1.
+__device__ __forceinline__ void prod_planes(int idx, int& pa, int& pb) {
+  const int tab_a[6] = {0, 0, 1, 0, 1, 2};
+  const int tab_b[6] = {0, 1, 0, 2, 1, 0};
+  pa = tab_a[idx];
+  pb = tab_b[idx];
+}
+
+__device__ __forceinline__ void store_planes8(uint8_t* arena, long long base, long long plane, int nsplit,
+                                              int n_pad, int row, int col, const float* v) {
+  __align__(16) __nv_bfloat16 h[8], m[8], l[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) split3(v[e], h[e], m[e], l[e]);
+  const long long off = base + blocked_offset(row, col, n_pad);
+  *reinterpret_cast<uint4*>(arena + off) = *reinterpret_cast<const uint4*>(h);
+  if (nsplit > 1) *reinterpret_cast<uint4*>(arena + off + plane) = *reinterpret_cast<const uint4*>(m);
+  if (nsplit > 2) *reinterpret_cast<uint4*>(arena + off + 2 * plane) = *reinterpret_cast<const uint4*>(l);
+}
+
+template <int NSPLIT>
+__global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const GemmParams p) {
+  using Cfg = TcCfg<NSPLIT>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + Cfg::kStages * Cfg::kStageBytes);
+  uint64_t* empty = full + Cfg::kStages;
+  uint64_t* accb = empty + Cfg::kStages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accb + 1);
+  float* red = reinterpret_cast<float*>(tmem_slot + 4);
+
+  // a CTA that finds the timeout flag raised by another CTA exits at once
+  if (*reinterpret_cast<volatile int*>(p.err) & kErrTimeout) return;
+  const GemmWork w = p.work[blockIdx.x];
+  const GemmMat m = p.mats[w.mat];
+  int cur = 0;
+  int branch_sq = 0;
+  const bool stepping = (p.mode == kModeSp2 || p.mode == kModeRsp);
+  if (stepping) {
+    const Sp2State st = p.sp2[w.mat];
+    if (!st.active) return;
+    cur = st.cur;
+    branch_sq = st.y >= 0.5;
+  } else if (m.b_from_sp2 || m.a_from_sp2) {
+    cur = p.sp2[w.mat].cur;
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long in_shift = stepping ? cur * m.buf_stride : 0;
+  const long long out_shift = stepping ? (1 - cur) * m.buf_stride : 0;
+  const uint8_t* A = p.arena + m.a_off + (stepping ? in_shift : (m.a_from_sp2 ? cur * m.buf_stride : 0));
+  const uint8_t* B = p.arena + m.b_off + (stepping ? in_shift : (m.b_from_sp2 ? cur * m.buf_stride : 0));
+  const int nkb = m.n_pad >> 6;
+  const int kb_end = (m.k_real + 63) >> 6;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < Cfg::kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accb, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(tmem_slot, 128);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  bool ok = true;
+
+  if (threadIdx.x == 0) {
+    // ---- producer: bulk copies of the operand blocks -------------------------------
+    for (int kb = 0; kb < kb_end; ++kb) {
+      const int s = kb % Cfg::kStages;
+      const int round = kb / Cfg::kStages;
+      if (kb >= Cfg::kStages && !mbar_wait(&empty[s], (round - 1) & 1)) {
+        ok = false;
+        break;
+      }
+      mbar_arrive_expect_tx(&full[s], Cfg::kStageBytes);
+      uint8_t* st = smem + s * Cfg::kStageBytes;
+      const long long aoff = ((long long)w.tm * nkb + kb) * kBlkBytes;
+      const long long boff = ((long long)w.tn * nkb + kb) * kBlkBytes;
+#pragma unroll
+      for (int pl = 0; pl < NSPLIT; ++pl) {
+        bulk_g2s(st + pl * kBlkBytes, A + pl * m.a_plane + aoff, kBlkBytes, &full[s]);
+        bulk_g2s(st + (NSPLIT + pl) * kBlkBytes, B + pl * m.b_plane + boff, kBlkBytes, &full[s]);
+      }
+    }
+  } else if (threadIdx.x == 32) {
+    // ---- MMA issuer -------------------------------------------------------------------
+    constexpr uint32_t idesc = idesc_bf16_f32(128, 128);
+    for (int kb = 0; kb < kb_end; ++kb) {
+      const int s = kb % Cfg::kStages;
+      const int round = kb / Cfg::kStages;
+      if (!mbar_wait(&full[s], round & 1)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t st = smem_u32(smem + s * Cfg::kStageBytes);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+#pragma unroll
+        for (int pr = 0; pr < Cfg::kNumProd; ++pr) {
+          int pa, pb;
+          prod_planes(pr, pa, pb);
+          const uint64_t ad = smem_desc_sw128(st + pa * kBlkBytes + kk * 32);
+          const uint64_t bd = smem_desc_sw128(st + (NSPLIT + pb) * kBlkBytes + kk * 32);
+          tc_mma_bf16(tmem, ad, bd, idesc, (kb | kk | pr) != 0 ? 1u : 0u);
+        }
+      }
+      tc_commit(&empty[s]);
+    }
+    tc_commit(accb);
+  }
+  __syncwarp();
+  if (!mbar_wait(accb, 0)) ok = false;
+  tc_fence_after();
+
+  // ---- epilogue: 128 threads, thread = output row --------------------------------------
+  const int row_local = warp * 32 + lane;
+  const int row = w.tm * 128 + row_local;
+  const uint32_t t_row = tmem + ((uint32_t)(warp * 32) << 16);
+  const bool diag_tile = (w.tm == w.tn);
+  float tr_x = 0.f, tr_x2 = 0.f;
+  float* outm = (m.out_off >= 0) ? reinterpret_cast<float*>(p.arena + m.out_off + out_shift) : nullptr;
+  const float* xm = stepping ? reinterpret_cast<const float*>(p.arena + m.x_off + in_shift) : nullptr;
+  const float* cm = (p.mode == kModeRsp) ? reinterpret_cast<const float*>(p.arena + m.c_off) : nullptr;
+  const bool row_ok = row < m.m_real;
+#pragma unroll 1
+  for (int c = 0; c < 4; ++c) {
+    float v[32];
+    tmem_ld32(t_row + c * 32, v);
+    const int col0 = w.tn * 128 + c * 32;
+    if (p.mode == kModeRsp) {
+      const float4* sx = reinterpret_cast<const float4*>(xm + (long long)row * m.n_pad + col0);
+      const float4* sc = reinterpret_cast<const float4*>(cm + (long long)row * m.n_pad + col0);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float4 a = sx[q], c4 = sc[q];
+        const float xa[4] = {a.x, a.y, a.z, a.w}, ca[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int j = 4 * q + e;
+          const bool ok_ij = row_ok && (col0 + j) < m.n_real;
+          const float sum = v[j] + ca[e];
+          v[j] = ok_ij ? (branch_sq ? sum : 2.f * xa[e] - sum) : 0.f;
+        }
+      }
+    } else if (p.mode == kModeSp2) {
+      float x[32];
+      const float4* src = reinterpret_cast<const float4*>(xm + (long long)row * m.n_pad + col0);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float4 t = src[q];
+        x[4 * q] = t.x; x[4 * q + 1] = t.y; x[4 * q + 2] = t.z; x[4 * q + 3] = t.w;
+      }
+      if (diag_tile && c == warp && row_ok) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (j == lane) { tr_x = x[j]; tr_x2 = v[j]; }
+      }
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const bool ok_ij = row_ok && (col0 + j) < m.n_real;
+        const float nv = branch_sq ? v[j] : 2.f * x[j] - v[j];
+        v[j] = ok_ij ? nv : 0.f;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int col = col0 + j;
+        const bool ok_ij = row_ok && col < m.n_real;
+        v[j] = ok_ij ? (p.alpha * v[j] + (row == col ? p.beta : 0.f)) : 0.f;
+      }
+    }
+    if (outm) {
+      float4* dst = reinterpret_cast<float4*>(outm + (long long)row * m.n_pad + col0);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    }
+    if (m.outp_off >= 0 && p.nsplit_out > 0) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        store_planes8(p.arena, m.outp_off + out_shift, m.outp_plane, p.nsplit_out, m.n_pad, row, col0 + 8 * q,
+                      v + 8 * q);
+    }
+  }
+  if (p.mode == kModeSp2 && diag_tile) {
+    // fixed-order CTA reduction of the trace partials -> one slot per diagonal tile
+    const float sx = warp_sumf(tr_x), sx2 = warp_sumf(tr_x2);
+    if (lane == 0) { red[2 * warp] = sx; red[2 * warp + 1] = sx2; }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (p.mode == kModeSp2 && diag_tile && threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int q = 0; q < 4; ++q) { a += red[2 * q]; b += red[2 * q + 1]; }
+    p.tr_slots[m.tr_off + 2 * w.tm] = a;
+    p.tr_slots[m.tr_off + 2 * w.tm + 1] = b;
+  }
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 128);
+  }
+  if (!ok) atomicOr(p.err, kErrTimeout);
+}
+
+// ------------------------------------------------------------------------------------------
+// FP64 SIMT batched GEMM, 64x64 tiles, 256 threads (4x4 outputs each), BK = 16.
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) f64_gemm_kernel(const GemmParams p) {
+  __shared__ double As[16][64 + 1];
+  __shared__ double Bs[16][64 + 1];
+  __shared__ double red[2][8];
+  const GemmWork w = p.work[blockIdx.x];
+  const GemmMat m = p.mats[w.mat];
+  int cur = 0, branch_sq = 0;
+  const bool stepping = (p.mode == kModeSp2 || p.mode == kModeRsp);
+  if (stepping) {
+    const Sp2State st = p.sp2[w.mat];
+    if (!st.active) return;
+    cur = st.cur;
+    branch_sq = st.y >= 0.5;
+  } else if (m.b_from_sp2 || m.a_from_sp2) {
+    cur = p.sp2[w.mat].cur;
+  }
+  const long long in_shift = stepping ? cur * m.buf_stride : 0;
+  const long long out_shift = stepping ? (1 - cur) * m.buf_stride : 0;
+  const double* A = reinterpret_cast<const double*>(
+      p.arena + m.a_off + (stepping ? in_shift : (m.a_from_sp2 ? cur * m.buf_stride : 0)));
+  const double* B = reinterpret_cast<const double*>(
+      p.arena + m.b_off + (stepping ? in_shift : (m.b_from_sp2 ? cur * m.buf_stride : 0)));
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int r0 = w.tm * 64, c0 = w.tn * 64;
+  const int ld = m.n_pad;
+  double acc[4][4] = {};
+  const int k_end = (m.k_real + 15) & ~15;
+  const int lr = tid >> 2, lk = (tid & 3) * 4;
+  for (int k0 = 0; k0 < k_end; k0 += 16) {
+    const double4_32a a4 = *reinterpret_cast<const double4_32a*>(A + (long long)(r0 + lr) * ld + k0 + lk);
+    const double4_32a b4 = *reinterpret_cast<const double4_32a*>(B + (long long)(c0 + lr) * ld + k0 + lk);
+    As[lk][lr] = a4.x; As[lk + 1][lr] = a4.y; As[lk + 2][lr] = a4.z; As[lk + 3][lr] = a4.w;
+    Bs[lk][lr] = b4.x; Bs[lk + 1][lr] = b4.y; Bs[lk + 2][lr] = b4.z; Bs[lk + 3][lr] = b4.w;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) { a[i] = As[k][ty * 4 + i]; b[i] = Bs[k][tx * 4 + i]; }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  double* outm = (m.out_off >= 0) ? reinterpret_cast<double*>(p.arena + m.out_off + out_shift) : nullptr;
+  const double* xm = stepping ? reinterpret_cast<const double*>(p.arena + m.x_off + in_shift) : nullptr;
+  const double* cm = (p.mode == kModeRsp) ? reinterpret_cast<const double*>(p.arena + m.c_off) : nullptr;
+  double tx_ = 0.0, tx2 = 0.0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int row = r0 + ty * 4 + i;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int col = c0 + tx * 4 + j;
+      const bool ok = row < m.m_real && col < m.n_real;
+      double v;
+      if (p.mode == kModeSp2) {
+        const double x = xm[(long long)row * ld + col];
+        if (ok && row == col) { tx_ += x; tx2 += acc[i][j]; }
+        v = branch_sq ? acc[i][j] : 2.0 * x - acc[i][j];
+      } else if (p.mode == kModeRsp) {
+        const double x = xm[(long long)row * ld + col];
+        const double sum = acc[i][j] + cm[(long long)row * ld + col];
+        v = branch_sq ? sum : 2.0 * x - sum;
+      } else {
+        v = (double)p.alpha * acc[i][j] + (row == col ? (double)p.beta : 0.0);
+      }
+      if (outm) outm[(long long)row * ld + col] = ok ? v : 0.0;
+    }
+  }
+  if (p.mode == kModeSp2 && w.tm == w.tn) {
+    const double a = warp_sum(tx_), b = warp_sum(tx2);
+    if ((tid & 31) == 0) { red[0][tid >> 5] = a; red[1][tid >> 5] = b; }
+    __syncthreads();
+    if (tid == 0) {
+      double sa = 0.0, sb = 0.0;
+      for (int q = 0; q < 8; ++q) { sa += red[0][q]; sb += red[1][q]; }
+      p.tr_slots[m.tr_off + 2 * w.tm] = sa;
+      p.tr_slots[m.tr_off + 2 * w.tm + 1] = sb;
+    }
+  }
+}
+
+}  // namespace
+
+void launch_gemm_tc(const GemmParams& p, int n_work, int nsplit, cudaStream_t s) {
+  if (n_work <= 0) return;
+  switch (nsplit) {
+    case 1: {
+      static bool init = false;
+      if (!init) { cudaFuncSetAttribute(tc_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<1>::kSmem); init = true; }
+      tc_gemm_kernel<1><<<n_work, 128, TcCfg<1>::kSmem, s>>>(p);
+      break;
+    }
+    case 2: {
+      static bool init = false;
+      if (!init) { cudaFuncSetAttribute(tc_gemm_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<2>::kSmem); init = true; }
+      tc_gemm_kernel<2><<<n_work, 128, TcCfg<2>::kSmem, s>>>(p);
+      break;
+    }
+    default: {
+      static bool init = false;
+      if (!init) { cudaFuncSetAttribute(tc_gemm_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<3>::kSmem); init = true; }
+      tc_gemm_kernel<3><<<n_work, 128, TcCfg<3>::kSmem, s>>>(p);
+      break;
+    }
+  }
+}
+
+void launch_gemm_f64(const GemmParams& p, int n_work, cudaStream_t s) {
+  if (n_work <= 0) return;
+  f64_gemm_kernel<<<n_work, 256, 0, s>>>(p);
+}
+
+}  // namespace sedacs

@@ -1,0 +1,35 @@
+// Elementwise / reduction helpers on the padded per-subgraph matrices.
+#pragma once
+#include "dense.cuh"
+
+namespace sedacs {
+
+// Placement of one subgraph's matrix in the arena.
+struct SubView {
+  long long master;        // row-major master (fp32 or fp64), byte offset
+  long long planes;        // blocked bf16 planes (byte offset of plane 0; -1 if none)
+  long long plane_stride;  // bytes between planes
+  int n_pad;               // row stride (columns)
+  int rows_pad;            // stored rows (n_pad for square, 128 * ceil(m/128) for core rows)
+  int n_real;              // valid rows = valid columns for square matrices
+  int pad;
+};
+
+void launch_split_planes(const SubView* views, int n_sub, int max_rows, uint8_t* arena, int nsplit, bool f64,
+                         cudaStream_t s);
+void launch_affine(const SubView* in, const SubView* out, int n_sub, int max_rows, uint8_t* arena, double a,
+                   double b, bool f64, cudaStream_t s);
+void launch_gershgorin(const SubView* views, int n_sub, int max_rows, const uint8_t* arena, double* lo, double* hi,
+                       const long long* row_base, double* bounds, bool f64, cudaStream_t s);
+void launch_sp2_x0(const SubView* hv, const SubView* xv, int n_sub, int max_rows, uint8_t* arena,
+                   const double* bounds, bool f64, cudaStream_t s);
+void launch_sp2_dx0(const SubView* hv, const SubView* xv, int n_sub, int max_rows, uint8_t* arena,
+                    const double* bounds, bool f64, cudaStream_t s);
+void launch_sp2_replay_init(Sp2State* st, const double* bounds, const int* n_real, const int* steps, double mu, int n,
+                            cudaStream_t s);
+void launch_sp2_init(Sp2State* st, const double* bounds, const int* n_real, double mu, double tol, int kmax, int n,
+                     cudaStream_t s);
+void launch_sp2_advance(Sp2State* st, const double* slots, const long long* tr_off, const int* n_diag,
+                        int* n_active, int n, cudaStream_t s);
+
+}  // namespace sedacs

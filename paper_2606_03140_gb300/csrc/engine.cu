@@ -1,0 +1,1442 @@
+// Host engine of the graph-partitioned shadow-QMD path (see engine.cuh).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <limits>
+
+#include "engine.cuh"
+
+using namespace sedacs;
+
+namespace sedacs {
+
+// ---------------------------------------------------------------------------------------------
+// small vector kernels
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+__global__ void charges_kernel(const double* pop, const int* species, const double* zval, double* q, int N) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) q[i] = pop[i] - zval[species[i]];
+}
+
+// out[0] = sum a*b (b may be null -> sum a); fixed-order tree in one CTA.
+__global__ void dot_kernel(const double* a, const double* b, int N, double* out) {
+  __shared__ double red[1024];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) s += b ? a[i] * b[i] : a[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = red[0];
+}
+
+// max |a - b|
+__global__ void maxdiff_kernel(const double* a, const double* b, int N, double* out) {
+  __shared__ double red[1024];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) s = fmax(s, fabs(a[i] - b[i]));
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = red[0];
+}
+
+__global__ void scale_kernel(double* y, const double* x, double a, int N) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) y[i] = a * x[i];
+}
+__global__ void axpy2_kernel(double* y, const double* x, double a, int N) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) y[i] += a * x[i];
+}
+
+__global__ void sub_kernel(double* out, const double* a, const double* b, int N) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) out[i] = a[i] - b[i];
+}
+
+__global__ void axpy_kernel(double* y, const double* x, const double* z, double a, int N) {
+  // y = y + a * (x - z)
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) y[i] += a * (x[i] - z[i]);
+}
+
+__global__ void coul_a_kernel(const double* q, const double* n, double* a, int N) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) a[i] = q[i] - 0.5 * n[i];
+}
+
+__global__ void neg_kernel(const double* x, double* y, int M) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < M) y[i] = -x[i];
+}
+
+__global__ void add_kernel(double* y, const double* x, int M) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < M) y[i] += x[i];
+}
+
+__global__ void nan_scan_kernel(const double* x, int M, int* err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < M && !isfinite(x[i])) atomicOr(err, kErrNumeric);
+}
+
+// XL-BOMD charge update (Eq. HW with dissipation): history ring h[k*N + i], head = n_t.
+__global__ void xl_update_kernel(double* hist, int head, int N, const double* u, double kappa, double alpha,
+                                 double c0, double c1, double c2, double c3, double c4, double c5, double* n_out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double c[6] = {c0, c1, c2, c3, c4, c5};
+  double h[6];
+  for (int k = 0; k < 6; ++k) h[k] = hist[((head + 6 - k) % 6) * (long long)N + i];
+  double diss = 0.0;
+  for (int k = 0; k < 6; ++k) diss += c[k] * h[k];
+  const double nn = 2.0 * h[0] - h[1] - kappa * u[i] + alpha * diss;
+  hist[((head + 1) % 6) * (long long)N + i] = nn;   // overwrites n_{t-5}
+  n_out[i] = nn;
+}
+
+__global__ void kick_kernel(double* v, const double* F, const double* mass, double half_dt_acc, int N) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < 3 * N) v[t] += half_dt_acc * F[t] / mass[t / 3];
+}
+
+__global__ void drift_kernel(double* R, const double* v, double dt, int N) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < 3 * N) R[t] += dt * v[t];
+}
+
+__global__ void kin_kernel(const double* v, const double* mass, int N, double* out) {
+  __shared__ double red[1024];
+  double s = 0.0;
+  for (int t = threadIdx.x; t < 3 * N; t += blockDim.x) s += 0.5 * mass[t / 3] * v[t] * v[t];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = red[0] / kAccHaAAmu;
+}
+
+__global__ void fill_hist_kernel(double* hist, const double* n, int N) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N)
+    for (int k = 0; k < 6; ++k) hist[k * (long long)N + i] = n[i];
+}
+
+__global__ void matrix_to_f64_kernel(const uint8_t* arena, long long off, bool f64, int rows, int cols, int ld,
+                                     double* out) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)rows * cols) return;
+  const int r = (int)(t / cols), c = (int)(t % cols);
+  out[t] = f64 ? reinterpret_cast<const double*>(arena + off)[(long long)r * ld + c]
+               : (double)reinterpret_cast<const float*>(arena + off)[(long long)r * ld + c];
+}
+
+}  // namespace
+
+inline int nblk(long long n, int tb) { return (int)((n + tb - 1) / tb); }
+
+}  // namespace sedacs
+
+// =============================================================================================
+// internal helpers
+// =============================================================================================
+#define CUCHK(x)                                                                  \
+  do {                                                                            \
+    cudaError_t e__ = (x);                                                        \
+    if (e__ != cudaSuccess) {                                                     \
+      ctx->err = std::string(#x) + ": " + cudaGetErrorString(e__);                 \
+      return e__ == cudaErrorMemoryAllocation ? SEDACS_ENOMEM : SEDACS_ECUDA;       \
+    }                                                                             \
+  } while (0)
+
+#define STCHK(x)                           \
+  do {                                     \
+    sedacs_status s__ = (x);               \
+    if (s__ != SEDACS_OK) return s__;      \
+  } while (0)
+
+namespace {
+
+template <typename T>
+cudaError_t grow(T** p, long long* cap, long long need) {
+  if (need <= *cap && *p) return cudaSuccess;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  const long long n = std::max(need + need / 4, 16LL);
+  cudaError_t e = cudaMalloc(p, sizeof(T) * n);
+  if (e == cudaSuccess) *cap = n;
+  return e;
+}
+
+void phase_begin(sedacs_ctx* ctx, int k) { cudaEventRecord(ctx->ev[k], ctx->stream); }
+void phase_end(sedacs_ctx* ctx, int k, int slot) {
+  cudaEventRecord(ctx->ev[k + 1], ctx->stream);
+  cudaEventSynchronize(ctx->ev[k + 1]);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, ctx->ev[k], ctx->ev[k + 1]);
+  ctx->t_phase[slot] += ms;
+}
+
+sedacs_status check_dev_err(sedacs_ctx* ctx) {
+  int e = 0;
+  CUCHK(cudaMemcpyAsync(&e, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CUCHK(cudaStreamSynchronize(ctx->stream));
+  if (e) {
+    cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream);
+    if (e & kErrTimeout) { ctx->err = "a bounded device wait gave up"; return SEDACS_ETIMEOUT; }
+    if (e & kErrCapacity) { ctx->err = "a fixed device buffer was too small"; return SEDACS_ECAPACITY; }
+    if (e & kErrNumeric) { ctx->err = "NaN or Inf in a result"; return SEDACS_ENUMERIC; }
+    ctx->err = "device error flag";
+    return SEDACS_ECUDA;
+  }
+  return SEDACS_OK;
+}
+
+double host_scalar(sedacs_ctx* ctx, const double* d) {
+  double v = 0.0;
+  cudaMemcpyAsync(&v, d, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+  cudaStreamSynchronize(ctx->stream);
+  return v;
+}
+
+sedacs_status copy_in(sedacs_ctx* ctx, double* dst, const double* src, long long count) {
+  if (!src) { ctx->err = "null input array"; return SEDACS_EINVAL; }
+  CUCHK(cudaMemcpyAsync(dst, src, sizeof(double) * count, cudaMemcpyDefault, ctx->stream));
+  return SEDACS_OK;
+}
+sedacs_status copy_out(sedacs_ctx* ctx, void* dst, const void* src, size_t bytes) {
+  if (!dst) return SEDACS_OK;
+  CUCHK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, ctx->stream));
+  if (!ctx->dev_io) CUCHK(cudaStreamSynchronize(ctx->stream));
+  return SEDACS_OK;
+}
+
+// ---- geometry-dependent data: pair list within r_off, SK blocks, Ewald tables ---------------
+sedacs_status prepare_geometry(sedacs_ctx* ctx) {
+  if (ctx->geom_valid) return SEDACS_OK;
+  const int N = ctx->N;
+  cudaStream_t s = ctx->stream;
+  CUCHK(grow(&ctx->d_pptr, &ctx->rows_cap, (long long)N + 1) == cudaSuccess ? cudaSuccess : cudaErrorMemoryAllocation);
+  long long pn = 0;
+  CUCHK(ctx->pb.build(ctx->d_R, N, ctx->box, ctx->model.r_off, nullptr, nullptr, nullptr, 0.0, ctx->d_pptr,
+                      &ctx->d_pcol, &ctx->pcol_cap, &pn, ctx->d_err, s));
+  ctx->pnnz = pn;
+  const size_t esz = ctx->f64 ? 8 : 4;
+  if (pn * 16 > ctx->blk_cap) {
+    if (ctx->d_h0b) cudaFree(ctx->d_h0b);
+    if (ctx->d_sb) cudaFree(ctx->d_sb);
+    ctx->blk_cap = pn * 16 + pn * 4 + 1024;
+    CUCHK(cudaMalloc(&ctx->d_h0b, esz * ctx->blk_cap));
+    CUCHK(cudaMalloc(&ctx->d_sb, esz * ctx->blk_cap));
+  }
+  SkGeom g;
+  for (int a = 0; a < 3; ++a) {
+    g.box[a] = ctx->box[a];
+    g.nimg[a] = (int)floor((ctx->model.r_off + 0.5 * ctx->box[a]) / ctx->box[a]);
+  }
+  launch_pair_blocks(ctx->model, ctx->d_R, ctx->d_species, ctx->d_pptr, ctx->d_pcol, N, g, ctx->d_h0b, ctx->d_sb,
+                     ctx->f64, s);
+  ctx->launches += 1;
+  CUCHK(ctx->ew.prepare(ctx->d_R, ctx->d_species, s));
+  ctx->launches += 3;
+  ctx->geom_valid = true;
+  ctx->z_valid = false;
+  return SEDACS_OK;
+}
+
+SkGeom sk_geom(const sedacs_ctx* ctx) {
+  SkGeom g;
+  for (int a = 0; a < 3; ++a) {
+    g.box[a] = ctx->box[a];
+    g.nimg[a] = (int)floor((ctx->model.r_off + 0.5 * ctx->box[a]) / ctx->box[a]);
+  }
+  return g;
+}
+
+// ---- arena layout and GEMM tables -------------------------------------------------------------
+long long mptr(const sedacs_ctx* ctx, int sl, int i, int copy = 0) {
+  const Slot& S = ctx->slot[sl];
+  const long long el = S.rows ? ctx->lay.rw_off[i] : ctx->lay.sq_off[i];
+  return S.base + copy * S.copy_stride + el * (ctx->f64 ? 8 : 4);
+}
+long long pptr_(const sedacs_ctx* ctx, int sl, int i, int copy = 0) {
+  const Slot& S = ctx->slot[sl];
+  if (!S.planes) return -1;
+  const long long el = S.rows ? ctx->lay.rw_off[i] : ctx->lay.sq_off[i];
+  return S.base + copy * S.copy_stride + S.master_bytes + el * 2;
+}
+
+sedacs_status build_op(sedacs_ctx* ctx, int id, int a, int b, int out, int mode, float alpha, float beta,
+                       bool b_from_sp2, bool a_from_sp2 = false) {
+  const Layout& L = ctx->lay;
+  std::vector<GemmMat> mats(L.n_sub);
+  std::vector<GemmWork> work;
+  const bool rows_out = ctx->slot[out].rows;
+  for (int i = 0; i < L.n_sub; ++i) {
+    GemmMat m{};
+    m.a_off = ctx->f64 ? mptr(ctx, a, i) : pptr_(ctx, a, i);
+    m.b_off = ctx->f64 ? mptr(ctx, b, i) : pptr_(ctx, b, i);
+    m.a_plane = ctx->slot[a].plane_stride;
+    m.b_plane = ctx->slot[b].plane_stride;
+    m.out_off = mptr(ctx, out, i);
+    m.outp_off = ctx->f64 ? -1 : pptr_(ctx, out, i);
+    m.outp_plane = ctx->slot[out].plane_stride;
+    m.x_off = (mode == kModeRsp) ? mptr(ctx, kR2, i) : mptr(ctx, kX, i);
+    m.c_off = mptr(ctx, kR1, i);
+    m.buf_stride = ctx->slot[kX].copy_stride;
+    m.tr_off = L.tr_off[i];
+    m.n_pad = L.n_pad[i];
+    m.m_real = rows_out ? L.n_core_orb[i] : L.n_real[i];
+    m.n_real = L.n_real[i];
+    m.k_real = L.n_real[i];
+    m.b_from_sp2 = b_from_sp2 ? 1 : 0;
+    m.a_from_sp2 = a_from_sp2 ? 1 : 0;
+    mats[i] = m;
+    if (L.n_real[i] == 0) continue;
+    const int tiles_n = L.n_pad[i] / ctx->tile;
+    const int tiles_m = (rows_out ? L.m_pad[i] : L.n_pad[i]) / ctx->tile;
+    for (int tm = 0; tm < tiles_m; ++tm)
+      for (int tn = 0; tn < tiles_n; ++tn) work.push_back({i, tm, tn, 0});
+  }
+  GemmOp& op = ctx->ops[id];
+  if (op.mats_d) cudaFree(op.mats_d);
+  if (op.work_d) cudaFree(op.work_d);
+  op.mats_d = nullptr;
+  op.work_d = nullptr;
+  CUCHK(cudaMalloc(&op.mats_d, sizeof(GemmMat) * std::max(1, L.n_sub)));
+  CUCHK(cudaMalloc(&op.work_d, sizeof(GemmWork) * std::max<size_t>(1, work.size())));
+  CUCHK(cudaMemcpyAsync(op.mats_d, mats.data(), sizeof(GemmMat) * L.n_sub, cudaMemcpyHostToDevice, ctx->stream));
+  if (!work.empty())
+    CUCHK(cudaMemcpyAsync(op.work_d, work.data(), sizeof(GemmWork) * work.size(), cudaMemcpyHostToDevice,
+                          ctx->stream));
+  op.n_work = (int)work.size();
+  op.alpha = alpha;
+  op.beta = beta;
+  op.mode = mode;
+  CUCHK(cudaStreamSynchronize(ctx->stream));
+  return SEDACS_OK;
+}
+
+void run_op(sedacs_ctx* ctx, int id, int nsplit_in, int nsplit_out) {
+  const GemmOp& op = ctx->ops[id];
+  GemmParams p;
+  p.work = op.work_d;
+  p.mats = op.mats_d;
+  p.arena = ctx->arena;
+  p.tr_slots = ctx->d_slots;
+  p.sp2 = ctx->d_sp2;
+  p.err = ctx->d_err;
+  p.mode = op.mode;
+  p.nsplit_out = nsplit_out;
+  p.alpha = op.alpha;
+  p.beta = op.beta;
+  if (ctx->f64) launch_gemm_f64(p, op.n_work, ctx->stream);
+  else launch_gemm_tc(p, op.n_work, nsplit_in, ctx->stream);
+  ctx->launches += op.n_work > 0 ? 1 : 0;
+}
+
+sedacs_status upload_views(sedacs_ctx* ctx, int sl, int copy, SubView** dst) {
+  const Layout& L = ctx->lay;
+  std::vector<SubView> v(L.n_sub);
+  for (int i = 0; i < L.n_sub; ++i) {
+    SubView s;
+    s.master = mptr(ctx, sl, i, copy);
+    s.planes = pptr_(ctx, sl, i, copy);
+    s.plane_stride = ctx->slot[sl].plane_stride;
+    s.n_pad = L.n_pad[i];
+    s.rows_pad = ctx->slot[sl].rows ? L.m_pad[i] : L.n_pad[i];
+    s.n_real = L.n_real[i];
+    s.pad = 0;
+    v[i] = s;
+  }
+  if (*dst) cudaFree(*dst);
+  *dst = nullptr;
+  CUCHK(cudaMalloc(dst, sizeof(SubView) * std::max(1, L.n_sub)));
+  CUCHK(cudaMemcpyAsync(*dst, v.data(), sizeof(SubView) * L.n_sub, cudaMemcpyHostToDevice, ctx->stream));
+  CUCHK(cudaStreamSynchronize(ctx->stream));
+  return SEDACS_OK;
+}
+
+template <typename T>
+sedacs_status upload_vec(sedacs_ctx* ctx, T** dst, const std::vector<T>& v) {
+  if (*dst) cudaFree(*dst);
+  *dst = nullptr;
+  CUCHK(cudaMalloc(dst, sizeof(T) * std::max<size_t>(1, v.size())));
+  if (!v.empty()) CUCHK(cudaMemcpyAsync(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, ctx->stream));
+  return SEDACS_OK;
+}
+
+// Rebuild everything that depends on the subgraph lists.
+sedacs_status rebuild_layout(sedacs_ctx* ctx) {
+  const int P = ctx->part.n_parts;
+  const int N = ctx->N;
+  cudaStream_t s = ctx->stream;
+  Layout& L = ctx->lay;
+  L = Layout();
+  L.n_sub = P;
+  const long long tot_rows = ctx->sub_ptr_h[P];
+  // per-subgraph core counts
+  std::vector<int> ncore(P);
+  for (int i = 0; i < P; ++i) ncore[i] = ctx->part.leaves[i].count;
+  STCHK(upload_vec(ctx, &ctx->d_n_core, ncore));
+  CUCHK(grow(&ctx->d_orb_off, &ctx->loc_cap, tot_rows) == cudaSuccess ? cudaSuccess : cudaErrorMemoryAllocation);
+  if (ctx->d_n_orb_sub) cudaFree(ctx->d_n_orb_sub);
+  if (ctx->d_n_core_orb) cudaFree(ctx->d_n_core_orb);
+  CUCHK(cudaMalloc(&ctx->d_n_orb_sub, sizeof(int) * std::max(1, P)));
+  CUCHK(cudaMalloc(&ctx->d_n_core_orb, sizeof(int) * std::max(1, P)));
+  launch_orb_offsets(ctx->d_sub_ptr, ctx->d_sub_atoms, ctx->d_species, ctx->model, ctx->d_orb_off, ctx->d_n_orb_sub,
+                     ctx->d_n_core, ctx->d_n_core_orb, P, s);
+  L.n_real.resize(P);
+  L.n_core_orb.resize(P);
+  CUCHK(cudaMemcpyAsync(L.n_real.data(), ctx->d_n_orb_sub, sizeof(int) * P, cudaMemcpyDeviceToHost, s));
+  CUCHK(cudaMemcpyAsync(L.n_core_orb.data(), ctx->d_n_core_orb, sizeof(int) * P, cudaMemcpyDeviceToHost, s));
+  ctx->sub_atoms_h.resize(tot_rows);
+  CUCHK(cudaMemcpyAsync(ctx->sub_atoms_h.data(), ctx->d_sub_atoms, sizeof(int) * tot_rows, cudaMemcpyDeviceToHost, s));
+  CUCHK(cudaStreamSynchronize(s));
+  L.n_pad.resize(P);
+  L.m_pad.resize(P);
+  L.n_core_atoms = ncore;
+  L.n_atoms.resize(P);
+  L.sq_off.resize(P);
+  L.rw_off.resize(P);
+  L.tr_off.resize(P);
+  L.n_diag.resize(P);
+  for (int i = 0; i < P; ++i) {
+    L.n_atoms[i] = (int)(ctx->sub_ptr_h[i + 1] - ctx->sub_ptr_h[i]);
+    L.n_pad[i] = std::max(128, (L.n_real[i] + 127) / 128 * 128);
+    L.m_pad[i] = std::max(128, (L.n_core_orb[i] + 127) / 128 * 128);
+    L.sq_off[i] = L.sq_total;
+    L.rw_off[i] = L.rw_total;
+    L.sq_total += (long long)L.n_pad[i] * L.n_pad[i];
+    L.rw_total += (long long)L.m_pad[i] * L.n_pad[i];
+    L.n_diag[i] = L.n_pad[i] / ctx->tile;
+    L.tr_off[i] = L.tr_total;
+    L.tr_total += 2 * L.n_diag[i];
+    L.max_npad = std::max(L.max_npad, L.n_pad[i]);
+    L.max_mpad = std::max(L.max_mpad, L.m_pad[i]);
+  }
+  // arena slots
+  const int esz = ctx->f64 ? 8 : 4;
+  const bool planes = !ctx->f64;
+  long long off = 0;
+  for (int k = 0; k < kNumSlots; ++k) {
+    Slot& S = ctx->slot[k];
+    S.rows = (k == kT1 || k == kDc || k == kT2 || k == kWc || k == kdT1 || k == kdDc);
+    S.planes = planes && !(k == kDc || k == kWc || k == kdDc);
+    S.copies = (k == kX || k == kR1 || k == kR2) ? 2 : 1;
+    const long long el = S.rows ? L.rw_total : L.sq_total;
+    S.master_bytes = (el * esz + 1023) / 1024 * 1024;
+    S.plane_stride = el * 2;
+    S.copy_stride = S.master_bytes + (S.planes ? (3 * el * 2 + 1023) / 1024 * 1024 : 0);
+    S.base = off;
+    off += S.copy_stride * S.copies;
+  }
+  if ((size_t)off > ctx->arena_cap) {
+    if (ctx->arena) cudaFree(ctx->arena);
+    ctx->arena = nullptr;
+    const size_t want = (size_t)off + (size_t)off / 4;
+    CUCHK(cudaMalloc(&ctx->arena, want));
+    ctx->arena_cap = want;
+  }
+  // views and per-subgraph offset arrays
+  for (int k = 0; k < kNumSlots; ++k) STCHK(upload_views(ctx, k, 0, &ctx->d_views[k]));
+  STCHK(upload_views(ctx, kX, 1, &ctx->d_views_x1));
+  std::vector<long long> hoff(P), soff(P), dco(P), wco(P), rbase(P), troff(P), ddco(P), dhoff(P);
+  std::vector<int> npad(P), nreal(P), ndiag(P);
+  long long rb = 0;
+  for (int i = 0; i < P; ++i) {
+    hoff[i] = mptr(ctx, kH, i);
+    soff[i] = mptr(ctx, kS, i);
+    dco[i] = mptr(ctx, kDc, i);
+    wco[i] = mptr(ctx, kWc, i);
+    ddco[i] = mptr(ctx, kdDc, i);
+    dhoff[i] = mptr(ctx, kdH, i);
+    rbase[i] = rb;
+    rb += L.n_pad[i];
+    troff[i] = L.tr_off[i];
+    npad[i] = L.n_pad[i];
+    nreal[i] = L.n_real[i];
+    ndiag[i] = L.n_diag[i];
+  }
+  STCHK(upload_vec(ctx, &ctx->d_hoff, hoff));
+  STCHK(upload_vec(ctx, &ctx->d_soff, soff));
+  STCHK(upload_vec(ctx, &ctx->d_dcoff, dco));
+  STCHK(upload_vec(ctx, &ctx->d_wcoff, wco));
+  STCHK(upload_vec(ctx, &ctx->d_dcoff_d, ddco));
+  STCHK(upload_vec(ctx, &ctx->d_dhoff, dhoff));
+  STCHK(upload_vec(ctx, &ctx->d_rowbase, rbase));
+  STCHK(upload_vec(ctx, &ctx->d_tr_off, troff));
+  STCHK(upload_vec(ctx, &ctx->d_n_pad, npad));
+  STCHK(upload_vec(ctx, &ctx->d_n_real, nreal));
+  STCHK(upload_vec(ctx, &ctx->d_n_diag, ndiag));
+  if (ctx->d_glo) cudaFree(ctx->d_glo);
+  if (ctx->d_ghi) cudaFree(ctx->d_ghi);
+  if (ctx->d_bounds) cudaFree(ctx->d_bounds);
+  if (ctx->d_slots) cudaFree(ctx->d_slots);
+  if (ctx->d_sp2) cudaFree(ctx->d_sp2);
+  CUCHK(cudaMalloc(&ctx->d_glo, sizeof(double) * std::max(1LL, rb)));
+  CUCHK(cudaMalloc(&ctx->d_ghi, sizeof(double) * std::max(1LL, rb)));
+  CUCHK(cudaMalloc(&ctx->d_bounds, sizeof(double) * 2 * std::max(1, P)));
+  CUCHK(cudaMalloc(&ctx->d_slots, sizeof(double) * std::max(1LL, L.tr_total)));
+  CUCHK(cudaMalloc(&ctx->d_sp2, sizeof(Sp2State) * std::max(1, P)));
+  // subgraph-of-row, core lists, local index table, density-graph row pointers
+  std::vector<int> sor(tot_rows), csub, cloc;
+  std::vector<long long> gdp(N + 1, 0);
+  std::vector<int> gdlen(N, 0);
+  for (int i = 0; i < P; ++i) {
+    for (long long q = ctx->sub_ptr_h[i]; q < ctx->sub_ptr_h[i + 1]; ++q) sor[q] = i;
+    for (int a = 0; a < ncore[i]; ++a) {
+      csub.push_back(i);
+      cloc.push_back(a);
+      gdlen[ctx->sub_atoms_h[ctx->sub_ptr_h[i] + a]] = L.n_atoms[i];
+    }
+  }
+  for (int A = 0; A < N; ++A) gdp[A + 1] = gdp[A] + gdlen[A];
+  ctx->n_core_total = (int)csub.size();
+  STCHK(upload_vec(ctx, &ctx->d_sub_of_row, sor));
+  STCHK(upload_vec(ctx, &ctx->d_core_sub, csub));
+  STCHK(upload_vec(ctx, &ctx->d_core_local, cloc));
+  if (ctx->d_gd_ptr) cudaFree(ctx->d_gd_ptr);
+  ctx->d_gd_ptr = nullptr;
+  STCHK(upload_vec(ctx, &ctx->d_gd_ptr, gdp));
+  ctx->gd_nnz = gdp[N];
+  CUCHK(grow(&ctx->d_gd_col, &ctx->gd_cap, ctx->gd_nnz + 1) == cudaSuccess ? cudaSuccess : cudaErrorMemoryAllocation);
+  if (ctx->d_gd_val) cudaFree(ctx->d_gd_val);
+  CUCHK(cudaMalloc(&ctx->d_gd_val, sizeof(double) * ctx->gd_cap));
+  if (ctx->d_loc) cudaFree(ctx->d_loc);
+  CUCHK(cudaMalloc(&ctx->d_loc, sizeof(int) * (size_t)N * std::max(1, P)));
+  launch_loc_fill(ctx->d_sub_ptr, ctx->d_sub_atoms, ctx->d_loc, N, P, s);
+  // GEMM tables
+  const bool f = ctx->f64;
+  (void)f;
+  STCHK(build_op(ctx, OP_NS_Y1, kS, kT, kY1, kModeGeneric, 1.f, 0.f, false));
+  STCHK(build_op(ctx, OP_NS_T0, kZ0, kY0, kT, kModeGeneric, -0.5f, 1.5f, false));
+  STCHK(build_op(ctx, OP_NS_T1, kZ1, kY1, kT, kModeGeneric, -0.5f, 1.5f, false));
+  STCHK(build_op(ctx, OP_NS_Y0, kY0, kT, kY1, kModeGeneric, 1.f, 0.f, false));
+  STCHK(build_op(ctx, OP_NS_Y1b, kY1, kT, kY0, kModeGeneric, 1.f, 0.f, false));
+  STCHK(build_op(ctx, OP_NS_Z0, kT, kZ0, kZ1, kModeGeneric, 1.f, 0.f, false));
+  STCHK(build_op(ctx, OP_NS_Z1, kT, kZ1, kZ0, kModeGeneric, 1.f, 0.f, false));
+  STCHK(build_op(ctx, OP_P0, kZ0, kH, kP, kModeGeneric, 1.f, 0.f, false));
+  STCHK(build_op(ctx, OP_P1, kZ1, kH, kP, kModeGeneric, 1.f, 0.f, false));
+  STCHK(build_op(ctx, OP_HT0, kP, kZ0, kHt, kModeGeneric, 1.f, 0.f, false));
+  STCHK(build_op(ctx, OP_HT1, kP, kZ1, kHt, kModeGeneric, 1.f, 0.f, false));
+  STCHK(build_op(ctx, OP_SP2, kX, kX, kX, kModeSp2, 1.f, 0.f, false));
+  STCHK(build_op(ctx, OP_T1_0, kZ0, kX, kT1, kModeGeneric, 1.f, 0.f, true));
+  STCHK(build_op(ctx, OP_T1_1, kZ1, kX, kT1, kModeGeneric, 1.f, 0.f, true));
+  STCHK(build_op(ctx, OP_DC0, kT1, kZ0, kDc, kModeGeneric, 2.f, 0.f, false));
+  STCHK(build_op(ctx, OP_DC1, kT1, kZ1, kDc, kModeGeneric, 2.f, 0.f, false));
+  STCHK(build_op(ctx, OP_T2, kT1, kHt, kT2, kModeGeneric, 1.f, 0.f, false));
+  STCHK(build_op(ctx, OP_WC0, kT2, kZ0, kWc, kModeGeneric, 2.f, 0.f, false));
+  STCHK(build_op(ctx, OP_WC1, kT2, kZ1, kWc, kModeGeneric, 2.f, 0.f, false));
+  // response tables
+  STCHK(build_op(ctx, OP_RSP_A, kX, kR2, kR1, kModeGeneric, 1.f, 0.f, true, true));
+  STCHK(build_op(ctx, OP_RSP_B, kR2, kX, kR2, kModeRsp, 1.f, 0.f, false));
+  STCHK(build_op(ctx, OP_DP0, kZ0, kdH, kP, kModeGeneric, 1.f, 0.f, false));
+  STCHK(build_op(ctx, OP_DP1, kZ1, kdH, kP, kModeGeneric, 1.f, 0.f, false));
+  STCHK(build_op(ctx, OP_DHT0, kP, kZ0, kdHt, kModeGeneric, 1.f, 0.f, false));
+  STCHK(build_op(ctx, OP_DHT1, kP, kZ1, kdHt, kModeGeneric, 1.f, 0.f, false));
+  STCHK(build_op(ctx, OP_DT1_0, kZ0, kR2, kdT1, kModeGeneric, 1.f, 0.f, true));
+  STCHK(build_op(ctx, OP_DT1_1, kZ1, kR2, kdT1, kModeGeneric, 1.f, 0.f, true));
+  STCHK(build_op(ctx, OP_DDC0, kdT1, kZ0, kdDc, kModeGeneric, 2.f, 0.f, false));
+  STCHK(build_op(ctx, OP_DDC1, kdT1, kZ1, kdDc, kModeGeneric, 2.f, 0.f, false));
+  ctx->have_subs = true;
+  ctx->z_valid = false;
+  ctx->sp2_iters_h.assign(P, 0);
+  CUCHK(cudaStreamSynchronize(s));
+  return SEDACS_OK;
+}
+
+// ---- dense stages ------------------------------------------------------------------------------
+int max_rows(const sedacs_ctx* ctx) { return ctx->lay.max_npad; }
+
+void gather_hs(sedacs_ctx* ctx) {
+  cudaStream_t s = ctx->stream;
+  const Layout& L = ctx->lay;
+  const int esz = ctx->f64 ? 8 : 4;
+  cudaMemsetAsync(ctx->arena + ctx->slot[kS].base, 0, L.sq_total * esz, s);
+  cudaMemsetAsync(ctx->arena + ctx->slot[kH].base, 0, L.sq_total * esz, s);
+  launch_gather(ctx->model, ctx->d_sub_ptr, ctx->d_sub_atoms, ctx->d_orb_off, ctx->d_species, ctx->d_pptr,
+                ctx->d_pcol, ctx->d_h0b, ctx->d_sb, ctx->d_loc, ctx->N, ctx->d_V, ctx->d_hoff, ctx->d_soff,
+                ctx->d_n_pad, ctx->arena, L.n_sub, ctx->d_sub_of_row, ctx->sub_ptr_h[L.n_sub], 0, ctx->f64, s);
+  ctx->launches += 3;
+  if (!ctx->f64) {
+    launch_split_planes(ctx->d_views[kH], L.n_sub, max_rows(ctx), ctx->arena, ctx->nsplit_ns, false, s);
+    ctx->launches += 1;
+  }
+}
+
+// Z = s^-1/2 by the coupled Newton-Schulz iteration Y0 = s, Z0 = I, T = (3I - Z Y)/2,
+// Y <- Y T, Z <- T Z (quadratic convergence for ||I - s|| < 1).
+void compute_z(sedacs_ctx* ctx) {
+  cudaStream_t s = ctx->stream;
+  const Layout& L = ctx->lay;
+  const int mr = max_rows(ctx);
+  const int ns = ctx->nsplit_ns;
+  if (!ctx->f64) launch_split_planes(ctx->d_views[kS], L.n_sub, mr, ctx->arena, ns, false, s);
+  launch_affine(ctx->d_views[kS], ctx->d_views[kT], L.n_sub, mr, ctx->arena, -0.5, 1.5, ctx->f64, s);
+  if (!ctx->f64) launch_split_planes(ctx->d_views[kT], L.n_sub, mr, ctx->arena, ns, false, s);
+  run_op(ctx, OP_NS_Y1, ns, ns);                       // Y1 = s T0
+  launch_affine(ctx->d_views[kT], ctx->d_views[kZ1], L.n_sub, mr, ctx->arena, 1.0, 0.0, ctx->f64, s);   // Z1 = T0
+  if (!ctx->f64) launch_split_planes(ctx->d_views[kZ1], L.n_sub, mr, ctx->arena, ns, false, s);
+  ctx->launches += ctx->f64 ? 2 : 5;
+  int c = 1;
+  const int K = std::max(2, ctx->prm.ns_iters);
+  for (int k = 2; k <= K; ++k) {
+    run_op(ctx, c == 0 ? OP_NS_T0 : OP_NS_T1, ns, ns);      // T = 1.5 I - 0.5 Z[c] Y[c]
+    if (k < K) run_op(ctx, c == 0 ? OP_NS_Y0 : OP_NS_Y1b, ns, ns);   // Y[1-c] = Y[c] T
+    run_op(ctx, c == 0 ? OP_NS_Z0 : OP_NS_Z1, ns, ns);      // Z[1-c] = T Z[c]
+    c = 1 - c;
+  }
+  ctx->zc = c;
+  ctx->z_valid = true;
+}
+
+void compute_ht(sedacs_ctx* ctx) {
+  const int ns = ctx->nsplit_ns;
+  run_op(ctx, ctx->zc == 0 ? OP_P0 : OP_P1, ns, ns);     // P = Z h
+  run_op(ctx, ctx->zc == 0 ? OP_HT0 : OP_HT1, ns, ns);   // h~ = P Z
+  launch_gershgorin(ctx->d_views[kHt], ctx->lay.n_sub, max_rows(ctx), ctx->arena, ctx->d_glo, ctx->d_ghi,
+                    ctx->d_rowbase, ctx->d_bounds, ctx->f64, ctx->stream);
+  ctx->launches += 2;
+  ctx->bounds_h.resize(2 * ctx->lay.n_sub);
+  cudaMemcpyAsync(ctx->bounds_h.data(), ctx->d_bounds, sizeof(double) * 2 * ctx->lay.n_sub, cudaMemcpyDeviceToHost,
+                  ctx->stream);
+}
+
+// mu-branch SP2 (T -> 0 Fermi operator, Sec. "Density Matrix Evaluation on Partitioned Graphs").
+sedacs_status run_sp2(sedacs_ctx* ctx, double mu, int kmax) {
+  cudaStream_t s = ctx->stream;
+  const Layout& L = ctx->lay;
+  const int mr = max_rows(ctx);
+  launch_sp2_x0(ctx->d_views[kHt], ctx->d_views[kX], L.n_sub, mr, ctx->arena, ctx->d_bounds, ctx->f64, s);
+  if (!ctx->f64) launch_split_planes(ctx->d_views[kX], L.n_sub, mr, ctx->arena, ctx->nsplit_sp2, false, s);
+  launch_sp2_init(ctx->d_sp2, ctx->d_bounds, ctx->d_n_real, mu, ctx->prm.sp2_tol, kmax, L.n_sub, s);
+  ctx->launches += ctx->f64 ? 2 : 3;
+  if (!ctx->d_nactive) CUCHK(cudaMalloc(&ctx->d_nactive, sizeof(int)));
+  for (int k = 0; k < kmax; ++k) {
+    run_op(ctx, OP_SP2, ctx->nsplit_sp2, ctx->nsplit_sp2);
+    cudaMemsetAsync(ctx->d_nactive, 0, sizeof(int), s);
+    launch_sp2_advance(ctx->d_sp2, ctx->d_slots, ctx->d_tr_off, ctx->d_n_diag, ctx->d_nactive, L.n_sub, s);
+    ctx->launches += 1;
+    if (k >= 6 && (k % 3 == 0 || k == kmax - 1)) {
+      int na = 0;
+      CUCHK(cudaMemcpyAsync(&na, ctx->d_nactive, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CUCHK(cudaStreamSynchronize(s));
+      if (na == 0) break;
+    }
+  }
+  return SEDACS_OK;
+}
+
+void back_transform(sedacs_ctx* ctx, bool with_w) {
+  const int ns = ctx->nsplit_ns;
+  const int z = ctx->zc;
+  run_op(ctx, z == 0 ? OP_T1_0 : OP_T1_1, ctx->nsplit_sp2 > ns ? ctx->nsplit_sp2 : ns, ns);   // T1 = Z_c X
+  run_op(ctx, z == 0 ? OP_DC0 : OP_DC1, ns, 0);                                          // D_c = 2 T1 Z
+  if (with_w) {
+    run_op(ctx, OP_T2, ns, ns);                                                          // T2 = T1 h~
+    run_op(ctx, z == 0 ? OP_WC0 : OP_WC1, ns, 0);                                        // W_c = 2 T2 Z
+  }
+}
+
+// Populations / band energy (and forces) from the core rows; q = pop - Z; returns N_e count.
+sedacs_status observe(sedacs_ctx* ctx, bool with_forces, double* n_count) {
+  cudaStream_t s = ctx->stream;
+  const SkGeom g = sk_geom(ctx);
+  if (with_forces) cudaMemsetAsync(ctx->d_dU, 0, sizeof(double) * 3 * ctx->N, s);
+  launch_observables(ctx->model, ctx->d_R, ctx->d_species, g, ctx->d_sub_ptr, ctx->d_sub_atoms, ctx->d_orb_off,
+                     ctx->part.perm, ctx->d_core_sub, ctx->d_core_local, ctx->n_core_total, ctx->d_pptr, ctx->d_pcol,
+                     ctx->d_h0b, ctx->d_sb, ctx->d_loc, ctx->N, ctx->d_V, ctx->arena, ctx->arena, ctx->d_dcoff,
+                     ctx->d_wcoff, ctx->d_n_pad, ctx->d_pop, ctx->d_eband, ctx->d_dU, with_forces ? 1 : 0, ctx->f64, s);
+  charges_kernel<<<nblk(ctx->N, 128), 128, 0, s>>>(ctx->d_pop, ctx->d_species, ctx->d_zval, ctx->d_q, ctx->N);
+  dot_kernel<<<1, 1024, 0, s>>>(ctx->d_pop, nullptr, ctx->N, ctx->d_scal);
+  ctx->launches += 3;
+  if (n_count) *n_count = host_scalar(ctx, ctx->d_scal);
+  return SEDACS_OK;
+}
+
+// T -> 0 electron count at trial mu (SP2 + D_c rows + populations).
+sedacs_status count_at(sedacs_ctx* ctx, double mu, int kmax, double* nel) {
+  STCHK(run_sp2(ctx, mu, kmax));
+  back_transform(ctx, false);
+  return observe(ctx, false, nel);
+}
+
+// mu at the middle of the collected gap: the smallest mu with N0 >= N_e - 1/2 (top of the
+// occupied levels) and the smallest mu with N0 > N_e + 1/2 (bottom of the empty ones).
+sedacs_status solve_mu(sedacs_ctx* ctx, double* mu_out) {
+  double lo = 1e300, hi = -1e300;
+  for (int i = 0; i < ctx->lay.n_sub; ++i) {
+    if (ctx->lay.n_real[i] == 0) continue;
+    lo = std::min(lo, ctx->bounds_h[2 * i]);
+    hi = std::max(hi, ctx->bounds_h[2 * i + 1]);
+  }
+  const double ne = ctx->n_electrons, kap = 0.5, delta = 1e-3;
+  const int kt = 40;
+  double a = lo, b = hi, nel = 0.0;
+  while (b - a > delta) {
+    const double m = 0.5 * (a + b);
+    STCHK(count_at(ctx, m, kt, &nel));
+    if (nel >= ne - kap) b = m; else a = m;
+  }
+  const double mu_h = b;
+  a = mu_h;
+  b = hi;
+  while (b - a > delta) {
+    const double m = 0.5 * (a + b);
+    STCHK(count_at(ctx, m, kt, &nel));
+    if (nel > ne + kap) b = m; else a = m;
+  }
+  const double mu_l = a;
+  *mu_out = 0.5 * (mu_h + mu_l);
+  return SEDACS_OK;
+}
+
+sedacs_status density_core(sedacs_ctx* ctx, double* mu_io) {
+  if (!ctx->have_subs) { ctx->err = "no subgraphs: call sedacs_graph_build and sedacs_partition first"; return SEDACS_EINVAL; }
+  cudaStream_t s = ctx->stream;
+  STCHK(prepare_geometry(ctx));
+  phase_begin(ctx, 0);
+  CUCHK(ctx->ew.potential(ctx->d_n, ctx->d_V, s));
+  ctx->launches += 6;
+  phase_end(ctx, 0, 1);
+  phase_begin(ctx, 0);
+  gather_hs(ctx);
+  phase_end(ctx, 0, 2);
+  phase_begin(ctx, 0);
+  if (!ctx->z_valid) compute_z(ctx);
+  if (!ctx->f64) launch_split_planes(ctx->d_views[kH], ctx->lay.n_sub, max_rows(ctx), ctx->arena, ctx->nsplit_ns, false, s);
+  compute_ht(ctx);
+  CUCHK(cudaStreamSynchronize(s));
+  phase_end(ctx, 0, 3);
+  double mu = *mu_io;
+  double nel = 0.0;
+  phase_begin(ctx, 0);
+  if (std::isnan(mu)) STCHK(solve_mu(ctx, &mu));
+  STCHK(run_sp2(ctx, mu, ctx->prm.sp2_kmax));
+  phase_end(ctx, 0, 4);
+  phase_begin(ctx, 0);
+  back_transform(ctx, true);
+  STCHK(observe(ctx, false, &nel));
+  if (std::fabs(nel - ctx->n_electrons) > 0.5) {
+    // mu left the gap (the levels moved): place it again
+    STCHK(solve_mu(ctx, &mu));
+    STCHK(run_sp2(ctx, mu, ctx->prm.sp2_kmax));
+    back_transform(ctx, true);
+    STCHK(observe(ctx, false, &nel));
+  }
+  launch_gd(ctx->model, ctx->d_sub_ptr, ctx->d_sub_atoms, ctx->d_orb_off, ctx->d_species, ctx->part.perm,
+            ctx->d_core_sub, ctx->d_core_local, ctx->n_core_total, ctx->arena, ctx->f64, ctx->d_dcoff, ctx->d_n_pad,
+            ctx->d_gd_ptr, ctx->d_gd_col, ctx->d_gd_val, s);
+  ctx->launches += 1;
+  nan_scan_kernel<<<nblk(ctx->N, 256), 256, 0, s>>>(ctx->d_q, ctx->N, ctx->d_err);
+  ctx->launches += 1;
+  // band and Coulomb energies
+  dot_kernel<<<1, 1024, 0, s>>>(ctx->d_eband, nullptr, ctx->N, ctx->d_scal + 1);
+  coul_a_kernel<<<nblk(ctx->N, 128), 128, 0, s>>>(ctx->d_q, ctx->d_n, ctx->d_tmp, ctx->N);
+  dot_kernel<<<1, 1024, 0, s>>>(ctx->d_tmp, ctx->d_V, ctx->N, ctx->d_scal + 2);
+  ctx->launches += 3;
+  double sc[3];
+  CUCHK(cudaMemcpyAsync(sc, ctx->d_scal, sizeof(double) * 3, cudaMemcpyDeviceToHost, s));
+  CUCHK(cudaStreamSynchronize(s));
+  phase_end(ctx, 0, 5);
+  ctx->e_band = sc[1];
+  ctx->e_coul = sc[2];
+  ctx->mu = mu;
+  *mu_io = mu;
+  std::vector<Sp2State> st(ctx->lay.n_sub);
+  CUCHK(cudaMemcpy(st.data(), ctx->d_sp2, sizeof(Sp2State) * ctx->lay.n_sub, cudaMemcpyDeviceToHost));
+  for (int i = 0; i < ctx->lay.n_sub; ++i) ctx->sp2_iters_h[i] = st[i].iters;
+  ctx->have_density = true;
+  ctx->have_gd = true;
+  ctx->have_forces = false;
+  return check_dev_err(ctx);
+}
+
+sedacs_status forces_core(sedacs_ctx* ctx) {
+  if (!ctx->have_density) { ctx->err = "no density: call sedacs_subgraph_density first"; return SEDACS_EINVAL; }
+  cudaStream_t s = ctx->stream;
+  phase_begin(ctx, 0);
+  STCHK(observe(ctx, true, nullptr));
+  coul_a_kernel<<<nblk(ctx->N, 128), 128, 0, s>>>(ctx->d_q, ctx->d_n, ctx->d_tmp, ctx->N);
+  CUCHK(ctx->ew.gradient(ctx->d_tmp, ctx->d_n, ctx->d_F, s));
+  add_kernel<<<nblk(3 * ctx->N, 256), 256, 0, s>>>(ctx->d_dU, ctx->d_F, 3 * ctx->N);
+  launch_repulsion(ctx->model, ctx->d_R, ctx->d_species, sk_geom(ctx), ctx->d_pptr, ctx->d_pcol, ctx->N, ctx->d_erep,
+                   ctx->d_dU, s);
+  neg_kernel<<<nblk(3 * ctx->N, 256), 256, 0, s>>>(ctx->d_dU, ctx->d_F, 3 * ctx->N);
+  nan_scan_kernel<<<nblk(3 * ctx->N, 256), 256, 0, s>>>(ctx->d_F, 3 * ctx->N, ctx->d_err);
+  dot_kernel<<<1, 1024, 0, s>>>(ctx->d_erep, nullptr, ctx->N, ctx->d_scal + 3);
+  ctx->launches += 11;
+  ctx->e_rep = host_scalar(ctx, ctx->d_scal + 3);
+  phase_end(ctx, 0, 6);
+  ctx->have_forces = true;
+  return check_dev_err(ctx);
+}
+
+sedacs_status graph_core(sedacs_ctx* ctx, const long long* gptr, const int* gcol, const double* gval) {
+  cudaStream_t s = ctx->stream;
+  CUCHK(grow(&ctx->d_row_ptr, &ctx->rows_cap, (long long)ctx->N + 1) == cudaSuccess ? cudaSuccess
+                                                                                   : cudaErrorMemoryAllocation);
+  long long nnz = 0;
+  CUCHK(ctx->gb.build(ctx->d_R, ctx->N, ctx->box, ctx->prm.r_graph, gptr, gcol, gval, ctx->prm.tau, ctx->d_row_ptr,
+                      &ctx->d_col, &ctx->col_cap, &nnz, ctx->d_err, s));
+  ctx->launches += 9;
+  ctx->nnz = nnz;
+  ctx->have_graph = true;
+  return check_dev_err(ctx);
+}
+
+sedacs_status halos_core(sedacs_ctx* ctx) {
+  if (!ctx->have_graph || !ctx->have_cores) { ctx->err = "graph and cores are required"; return SEDACS_EINVAL; }
+  std::vector<long long> old = ctx->sub_ptr_h;
+  CUCHK(ctx->part.halos(ctx->d_row_ptr, ctx->d_col, ctx->N, &ctx->d_sub_ptr, &ctx->d_sub_atoms, &ctx->sub_cap,
+                        ctx->sub_ptr_h, ctx->stream));
+  ctx->launches += 3;
+  return rebuild_layout(ctx);
+}
+
+// one graph -> halos -> density cycle with the previous density graph
+sedacs_status cycle(sedacs_ctx* ctx, double* mu) {
+  phase_begin(ctx, 0);
+  STCHK(graph_core(ctx, ctx->have_gd ? ctx->d_gd_ptr : nullptr, ctx->have_gd ? ctx->d_gd_col : nullptr,
+                   ctx->have_gd ? ctx->d_gd_val : nullptr));
+  STCHK(halos_core(ctx));
+  phase_end(ctx, 0, 0);
+  return density_core(ctx, mu);
+}
+
+// ---- charge response and low-rank kernel (SI Sec. B) ------------------------------------------
+
+double dev_dot(sedacs_ctx* ctx, const double* a, const double* b) {
+  dot_kernel<<<1, 1024, 0, ctx->stream>>>(a, b, ctx->N, ctx->d_scal + 8);
+  ctx->launches += 1;
+  return host_scalar(ctx, ctx->d_scal + 8);
+}
+
+// dq = dq/dn v at fixed mu: dV = gamma v, dh = 1/2 (s dV + dV s), dh~ = Z dh Z, first-order
+// SP2 replay dX (same branch sequence and step count as the last density call), then
+// dD_c = 2 Z_c dX Z and dq_A = sum dD_AB . S_AB.
+sedacs_status response_core(sedacs_ctx* ctx, const double* d_v, double* d_dq) {
+  if (!ctx->have_density) { ctx->err = "no density: call sedacs_subgraph_density first"; return SEDACS_EINVAL; }
+  cudaStream_t s = ctx->stream;
+  const Layout& L = ctx->lay;
+  const int mr = max_rows(ctx);
+  const int ns = ctx->nsplit_ns, n2 = ctx->nsplit_sp2;
+  const int esz = ctx->f64 ? 8 : 4;
+  CUCHK(ctx->ew.potential(d_v, ctx->d_tmp, s));
+  cudaMemsetAsync(ctx->arena + ctx->slot[kdH].base, 0, L.sq_total * esz, s);
+  launch_gather(ctx->model, ctx->d_sub_ptr, ctx->d_sub_atoms, ctx->d_orb_off, ctx->d_species, ctx->d_pptr,
+                ctx->d_pcol, ctx->d_h0b, ctx->d_sb, ctx->d_loc, ctx->N, ctx->d_tmp, ctx->d_dhoff, ctx->d_soff,
+                ctx->d_n_pad, ctx->arena, L.n_sub, ctx->d_sub_of_row, ctx->sub_ptr_h[L.n_sub], 1, ctx->f64, s);
+  if (!ctx->f64) launch_split_planes(ctx->d_views[kdH], L.n_sub, mr, ctx->arena, ns, false, s);
+  ctx->launches += 8;
+  run_op(ctx, ctx->zc == 0 ? OP_DP0 : OP_DP1, ns, ns);
+  run_op(ctx, ctx->zc == 0 ? OP_DHT0 : OP_DHT1, ns, ns);
+  launch_sp2_x0(ctx->d_views[kHt], ctx->d_views[kX], L.n_sub, mr, ctx->arena, ctx->d_bounds, ctx->f64, s);
+  launch_sp2_dx0(ctx->d_views[kdHt], ctx->d_views[kR2], L.n_sub, mr, ctx->arena, ctx->d_bounds, ctx->f64, s);
+  if (!ctx->f64) {
+    launch_split_planes(ctx->d_views[kX], L.n_sub, mr, ctx->arena, n2, false, s);
+    launch_split_planes(ctx->d_views[kR2], L.n_sub, mr, ctx->arena, n2, false, s);
+  }
+  STCHK(upload_vec(ctx, &ctx->d_steps, ctx->sp2_iters_h));
+  launch_sp2_replay_init(ctx->d_sp2, ctx->d_bounds, ctx->d_n_real, ctx->d_steps, ctx->mu, L.n_sub, s);
+  ctx->launches += 5;
+  int kmax = 0;
+  for (int k : ctx->sp2_iters_h) kmax = std::max(kmax, k);
+  if (!ctx->d_nactive) CUCHK(cudaMalloc(&ctx->d_nactive, sizeof(int)));
+  for (int k = 0; k < kmax; ++k) {
+    run_op(ctx, OP_RSP_A, n2, 0);       // R1 = X dX
+    run_op(ctx, OP_RSP_B, n2, n2);      // dX <- R1 + dX X  or  2 dX - R1 - dX X
+    run_op(ctx, OP_SP2, n2, n2);        // X  <- X^2  or  2 X - X^2
+    launch_sp2_advance(ctx->d_sp2, ctx->d_slots, ctx->d_tr_off, ctx->d_n_diag, ctx->d_nactive, L.n_sub, s);
+    ctx->launches += 1;
+  }
+  run_op(ctx, ctx->zc == 0 ? OP_DT1_0 : OP_DT1_1, n2 > ns ? n2 : ns, ns);   // dT1 = Z_c dX
+  run_op(ctx, ctx->zc == 0 ? OP_DDC0 : OP_DDC1, ns, 0);                     // dD_c = 2 dT1 Z
+  launch_observables(ctx->model, ctx->d_R, ctx->d_species, sk_geom(ctx), ctx->d_sub_ptr, ctx->d_sub_atoms,
+                     ctx->d_orb_off, ctx->part.perm, ctx->d_core_sub, ctx->d_core_local, ctx->n_core_total,
+                     ctx->d_pptr, ctx->d_pcol, ctx->d_h0b, ctx->d_sb, ctx->d_loc, ctx->N, ctx->d_tmp, ctx->arena,
+                     ctx->arena, ctx->d_dcoff_d, ctx->d_dcoff_d, ctx->d_n_pad, d_dq, ctx->d_tmp2, ctx->d_dU, 0,
+                     ctx->f64, s);
+  ctx->launches += 1;
+  return check_dev_err(ctx);
+}
+
+// u ~ (K0 J)^-1 K0 f with K0 = -c I (SI Sec. B, Eqs. "PreKernel"-"LowRankEEOM").
+sedacs_status kernel_core(sedacs_ctx* ctx, const double* f, double* u, int* rank_out) {
+  cudaStream_t s = ctx->stream;
+  const int N = ctx->N;
+  const double c = ctx->prm.c_k0;
+  double* k0f = ctx->d_vec;
+  double* vec = ctx->d_vec + 1LL * N;
+  auto V_ = [&](int j) { return ctx->d_vec + (2LL + j) * N; };
+  auto F_ = [&](int j) { return ctx->d_vec + (10LL + j) * N; };
+  double* dq = ctx->d_vec + 18LL * N;
+  double* r = ctx->d_vec + 19LL * N;
+  scale_kernel<<<nblk(N, 128), 128, 0, s>>>(k0f, f, -c, N);
+  ctx->launches += 1;
+  int m_max = (ctx->prm.kernel == 1) ? std::min(8, std::max(0, ctx->prm.krylov_rank)) : 0;
+  if (m_max == 0) {
+    cudaMemcpyAsync(u, k0f, sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
+    *rank_out = 0;
+    return SEDACS_OK;
+  }
+  const double nk0 = std::sqrt(dev_dot(ctx, k0f, k0f));
+  if (nk0 == 0.0) {
+    cudaMemsetAsync(u, 0, sizeof(double) * N, s);
+    *rank_out = 0;
+    return SEDACS_OK;
+  }
+  cudaMemcpyAsync(vec, k0f, sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
+  std::vector<double> coef;
+  int m = 0;
+  for (int j = 0; j < m_max; ++j) {
+    for (int i = 0; i < m; ++i) {      // modified Gram-Schmidt
+      const double d = dev_dot(ctx, V_(i), vec);
+      axpy2_kernel<<<nblk(N, 128), 128, 0, s>>>(vec, V_(i), -d, N);
+    }
+    const double nrm = std::sqrt(dev_dot(ctx, vec, vec));
+    if (nrm < 1e-14 * nk0) break;
+    scale_kernel<<<nblk(N, 128), 128, 0, s>>>(V_(j), vec, 1.0 / nrm, N);
+    STCHK(response_core(ctx, V_(j), dq));
+    // f_vj = K0 (J v) = -c (dq - v)
+    sub_kernel<<<nblk(N, 128), 128, 0, s>>>(F_(j), dq, V_(j), N);
+    scale_kernel<<<nblk(N, 128), 128, 0, s>>>(F_(j), F_(j), -c, N);
+    ctx->launches += 3 + 2 * m;
+    m = j + 1;
+    // O = F^T F, M = O^-1, coef = M F^T K0 f
+    std::vector<double> O(m * m), b(m);
+    for (int a = 0; a < m; ++a) {
+      b[a] = dev_dot(ctx, F_(a), k0f);
+      for (int bb = 0; bb <= a; ++bb) O[a * m + bb] = O[bb * m + a] = dev_dot(ctx, F_(a), F_(bb));
+    }
+    // solve O coef = b by Gauss-Jordan with partial pivoting (m <= 8)
+    std::vector<double> A(O);
+    coef = b;
+    for (int col = 0; col < m; ++col) {
+      int piv = col;
+      for (int rr = col + 1; rr < m; ++rr)
+        if (std::fabs(A[rr * m + col]) > std::fabs(A[piv * m + col])) piv = rr;
+      for (int k = 0; k < m; ++k) std::swap(A[col * m + k], A[piv * m + k]);
+      std::swap(coef[col], coef[piv]);
+      const double d = A[col * m + col];
+      if (d == 0.0) { ctx->err = "singular Krylov overlap"; return SEDACS_ENUMERIC; }
+      for (int k = 0; k < m; ++k) A[col * m + k] /= d;
+      coef[col] /= d;
+      for (int rr = 0; rr < m; ++rr) {
+        if (rr == col) continue;
+        const double f2 = A[rr * m + col];
+        for (int k = 0; k < m; ++k) A[rr * m + k] -= f2 * A[col * m + k];
+        coef[rr] -= f2 * coef[col];
+      }
+    }
+    // relative residual of the projected equation: |F coef - K0 f| / |K0 f|
+    scale_kernel<<<nblk(N, 128), 128, 0, s>>>(r, k0f, -1.0, N);
+    for (int a = 0; a < m; ++a) axpy2_kernel<<<nblk(N, 128), 128, 0, s>>>(r, F_(a), coef[a], N);
+    ctx->launches += 1 + m;
+    const double res = std::sqrt(dev_dot(ctx, r, r)) / nk0;
+    if (res < ctx->prm.krylov_tol) break;
+    cudaMemcpyAsync(vec, F_(j), sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
+  }
+  cudaMemsetAsync(u, 0, sizeof(double) * N, s);
+  for (int a = 0; a < m; ++a) axpy2_kernel<<<nblk(N, 128), 128, 0, s>>>(u, V_(a), coef[a], N);
+  ctx->launches += m;
+  *rank_out = m;
+  return SEDACS_OK;
+}
+
+}  // namespace
+
+// ===============================================================================================
+// C ABI
+// ===============================================================================================
+extern "C" {
+
+sedacs_status sedacs_kernel_apply_dev(sedacs_ctx* ctx, const double* f, double* u, int32_t* rank);
+
+void sedacs_default_params(sedacs_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->r_graph = 3.0;
+  p->tau = 1e-3;
+  p->core_size = 32;
+  p->precision = 1;
+  p->kernel = 0;
+  p->krylov_rank = 4;
+  p->krylov_tol = 1e-2;
+  p->c_k0 = 0.5;
+  p->scc_tol = 1e-8;
+  p->scc_alpha = 0.2;
+  p->sp2_tol = 1e-9;
+  p->sp2_kmax = 60;
+  p->ns_iters = 6;
+  p->ewald_tol = 0.0;
+}
+
+sedacs_status sedacs_create(int32_t n_atoms, const int32_t* species, const double box[3], const sedacs_model* model,
+                            const sedacs_params* params, sedacs_ctx** out) {
+  if (!out || n_atoms <= 0 || !species || !box || !model || !params) return SEDACS_EINVAL;
+  *out = nullptr;
+  for (int a = 0; a < 3; ++a)
+    if (!(box[a] > model->r_off)) return SEDACS_EINVAL;
+  for (int i = 0; i < n_atoms; ++i)
+    if (species[i] < 0 || species[i] > 2) return SEDACS_EINVAL;
+  if (params->precision < 0 || params->precision > 3 || params->core_size <= 0) return SEDACS_EINVAL;
+  sedacs_ctx* ctx = new sedacs_ctx();
+  ctx->N = n_atoms;
+  ctx->species_h.assign(species, species + n_atoms);
+  for (int a = 0; a < 3; ++a) ctx->box[a] = box[a];
+  ctx->prm = *params;
+  ModelDev& m = ctx->model;
+  for (int k = 0; k < 3; ++k) {
+    m.n_orb[k] = model->n_orb[k];
+    m.eps_s[k] = model->eps_s[k];
+    m.eps_p[k] = model->eps_p[k];
+    m.hubbard_u[k] = model->hubbard_u[k];
+    m.z_val[k] = model->z_val[k];
+    m.mass[k] = model->mass[k];
+    for (int j = 0; j < 3; ++j) {
+      m.rep_a[k][j] = model->rep_a[k][j];
+      for (int x = 0; x < 4; ++x) m.v0[k][j][x] = model->v0[k][j][x];
+    }
+  }
+  m.decay = model->decay;
+  m.overlap_scale = model->overlap_scale;
+  m.r_on = model->r_on;
+  m.r_off = model->r_off;
+  m.rep_decay = model->rep_decay;
+  ctx->n_electrons = 0.0;
+  for (int i = 0; i < n_atoms; ++i) ctx->n_electrons += model->z_val[species[i]];
+  ctx->f64 = params->precision == 0;
+  ctx->tile = ctx->f64 ? 64 : 128;
+  ctx->nsplit_ns = 3;
+  ctx->nsplit_sp2 = params->precision == 1 ? 3 : (params->precision == 2 ? 2 : 1);
+  if (ctx->f64) ctx->nsplit_sp2 = 3;
+  const int N = n_atoms;
+  auto fail = [&](sedacs_status st, const char* msg) {
+    sedacs_destroy(ctx);
+    (void)msg;
+    return st;
+  };
+  if (cudaMalloc(&ctx->d_err, sizeof(int)) != cudaSuccess) return fail(SEDACS_ECUDA, "alloc");
+  cudaMemset(ctx->d_err, 0, sizeof(int));
+  double** vecs[] = {&ctx->d_R, &ctx->d_n, &ctx->d_q, &ctx->d_V, &ctx->d_pop, &ctx->d_eband, &ctx->d_erep,
+                     &ctx->d_tmp, &ctx->d_tmp2};
+  for (double** p : vecs)
+    if (cudaMalloc(p, sizeof(double) * 3 * N) != cudaSuccess) return fail(SEDACS_ENOMEM, "alloc");
+  if (cudaMalloc(&ctx->d_dU, sizeof(double) * 3 * N) != cudaSuccess) return fail(SEDACS_ENOMEM, "alloc");
+  if (cudaMalloc(&ctx->d_F, sizeof(double) * 3 * N) != cudaSuccess) return fail(SEDACS_ENOMEM, "alloc");
+  if (cudaMalloc(&ctx->d_vel, sizeof(double) * 3 * N) != cudaSuccess) return fail(SEDACS_ENOMEM, "alloc");
+  if (cudaMalloc(&ctx->d_hist, sizeof(double) * 6 * N) != cudaSuccess) return fail(SEDACS_ENOMEM, "alloc");
+  if (cudaMalloc(&ctx->d_vec, sizeof(double) * 24 * N) != cudaSuccess) return fail(SEDACS_ENOMEM, "alloc");
+  if (cudaMalloc(&ctx->d_scal, sizeof(double) * 16) != cudaSuccess) return fail(SEDACS_ENOMEM, "alloc");
+  if (cudaMalloc(&ctx->d_species, sizeof(int) * N) != cudaSuccess) return fail(SEDACS_ENOMEM, "alloc");
+  cudaMemcpy(ctx->d_species, species, sizeof(int) * N, cudaMemcpyHostToDevice);
+  std::vector<double> mass(N);
+  for (int i = 0; i < N; ++i) mass[i] = model->mass[species[i]];
+  if (cudaMalloc(&ctx->d_mass, sizeof(double) * N) != cudaSuccess) return fail(SEDACS_ENOMEM, "alloc");
+  cudaMemcpy(ctx->d_mass, mass.data(), sizeof(double) * N, cudaMemcpyHostToDevice);
+  if (cudaMalloc(&ctx->d_zval, sizeof(double) * 3) != cudaSuccess) return fail(SEDACS_ENOMEM, "alloc");
+  cudaMemcpy(ctx->d_zval, model->z_val, sizeof(double) * 3, cudaMemcpyHostToDevice);
+  cudaMemset(ctx->d_n, 0, sizeof(double) * 3 * N);
+  for (auto& e : ctx->ev) cudaEventCreate(&e);
+  const double tol = params->ewald_tol > 0 ? params->ewald_tol : (ctx->f64 ? 1e-12 : 1e-8);
+  const double u[3] = {model->hubbard_u[0], model->hubbard_u[1], model->hubbard_u[2]};
+  if (ctx->ew.setup(N, box, u, ctx->f64, tol) != cudaSuccess) return fail(SEDACS_ENOMEM, "ewald");
+  *out = ctx;
+  return SEDACS_OK;
+}
+
+void sedacs_destroy(sedacs_ctx* ctx) {
+  if (!ctx) return;
+  cudaDeviceSynchronize();
+  void* ptrs[] = {ctx->d_err, ctx->d_species, ctx->d_R, ctx->d_n, ctx->d_q, ctx->d_V, ctx->d_pop, ctx->d_eband,
+                  ctx->d_dU, ctx->d_F, ctx->d_erep, ctx->d_tmp, ctx->d_tmp2, ctx->d_scal, ctx->d_vel, ctx->d_hist,
+                  ctx->d_mass, ctx->d_zval, ctx->d_vec, ctx->d_row_ptr, ctx->d_col, ctx->d_pptr, ctx->d_pcol,
+                  ctx->d_h0b, ctx->d_sb, ctx->d_gd_ptr, ctx->d_gd_col, ctx->d_gd_val, ctx->d_xgd_ptr, ctx->d_xgd_col,
+                  ctx->d_xgd_val, ctx->d_sub_ptr, ctx->d_sub_atoms, ctx->d_orb_off, ctx->d_n_orb_sub, ctx->d_n_core,
+                  ctx->d_n_core_orb, ctx->d_sub_of_row, ctx->d_core_sub, ctx->d_core_local, ctx->d_loc, ctx->arena,
+                  ctx->d_views_x1, ctx->d_hoff, ctx->d_soff, ctx->d_dcoff, ctx->d_wcoff, ctx->d_rowbase,
+                  ctx->d_tr_off, ctx->d_n_pad, ctx->d_n_real, ctx->d_n_diag, ctx->d_glo, ctx->d_ghi, ctx->d_bounds,
+                  ctx->d_slots, ctx->d_sp2, ctx->d_nactive, ctx->d_dcoff_d, ctx->d_dqpop, ctx->d_dhoff,
+                  ctx->d_steps};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (auto* v : ctx->d_views)
+    if (v) cudaFree(v);
+  for (auto& op : ctx->ops) {
+    if (op.mats_d) cudaFree(op.mats_d);
+    if (op.work_d) cudaFree(op.work_d);
+  }
+  for (auto& e : ctx->ev)
+    if (e) cudaEventDestroy(e);
+  delete ctx;
+}
+
+const char* sedacs_last_error(const sedacs_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+sedacs_status sedacs_set_device_io(sedacs_ctx* ctx, int32_t on, void* stream) {
+  if (!ctx) return SEDACS_EINVAL;
+  ctx->dev_io = on != 0;
+  ctx->stream = on ? reinterpret_cast<cudaStream_t>(stream) : 0;
+  return SEDACS_OK;
+}
+
+sedacs_status sedacs_graph_build(sedacs_ctx* ctx, const double* R, const int64_t* gd_ptr, const int32_t* gd_col,
+                                 const double* gd_val, int64_t gd_nnz, int32_t use_prev_D, int64_t* nnz) {
+  if (!ctx || !R) return SEDACS_EINVAL;
+  STCHK(copy_in(ctx, ctx->d_R, R, 3LL * ctx->N));
+  ctx->geom_valid = false;
+  const long long* gp = nullptr;
+  const int* gc = nullptr;
+  const double* gv = nullptr;
+  if (use_prev_D) {
+    if (!ctx->have_gd) { ctx->err = "no previous density graph"; return SEDACS_EINVAL; }
+    gp = ctx->d_gd_ptr; gc = ctx->d_gd_col; gv = ctx->d_gd_val;
+  } else if (gd_ptr) {
+    if (gd_nnz < 0 || !gd_col || !gd_val) return SEDACS_EINVAL;
+    CUCHK(grow(&ctx->d_xgd_col, &ctx->xgd_cap, gd_nnz + 1) == cudaSuccess ? cudaSuccess : cudaErrorMemoryAllocation);
+    if (ctx->d_xgd_val) cudaFree(ctx->d_xgd_val);
+    if (ctx->d_xgd_ptr) cudaFree(ctx->d_xgd_ptr);
+    CUCHK(cudaMalloc(&ctx->d_xgd_val, sizeof(double) * ctx->xgd_cap));
+    CUCHK(cudaMalloc(&ctx->d_xgd_ptr, sizeof(long long) * (ctx->N + 1)));
+    CUCHK(cudaMemcpyAsync(ctx->d_xgd_ptr, gd_ptr, sizeof(long long) * (ctx->N + 1), cudaMemcpyDefault, ctx->stream));
+    CUCHK(cudaMemcpyAsync(ctx->d_xgd_col, gd_col, sizeof(int) * gd_nnz, cudaMemcpyDefault, ctx->stream));
+    CUCHK(cudaMemcpyAsync(ctx->d_xgd_val, gd_val, sizeof(double) * gd_nnz, cudaMemcpyDefault, ctx->stream));
+    gp = ctx->d_xgd_ptr; gc = ctx->d_xgd_col; gv = ctx->d_xgd_val;
+  }
+  STCHK(graph_core(ctx, gp, gc, gv));
+  if (nnz) *nnz = ctx->nnz;
+  if (ctx->have_cores) STCHK(halos_core(ctx));
+  return SEDACS_OK;
+}
+
+sedacs_status sedacs_graph_get(sedacs_ctx* ctx, int64_t* row_ptr, int32_t* col) {
+  if (!ctx || !ctx->have_graph) return SEDACS_EINVAL;
+  STCHK(copy_out(ctx, row_ptr, ctx->d_row_ptr, sizeof(long long) * (ctx->N + 1)));
+  STCHK(copy_out(ctx, col, ctx->d_col, sizeof(int) * ctx->nnz));
+  CUCHK(cudaStreamSynchronize(ctx->stream));
+  return SEDACS_OK;
+}
+
+sedacs_status sedacs_partition(sedacs_ctx* ctx, const double* R, int32_t* n_parts) {
+  if (!ctx || !R) return SEDACS_EINVAL;
+  STCHK(copy_in(ctx, ctx->d_R, R, 3LL * ctx->N));
+  ctx->geom_valid = false;
+  CUCHK(ctx->part.rcb(ctx->d_R, ctx->N, ctx->box, ctx->prm.core_size, ctx->stream));
+  ctx->launches += 10;
+  ctx->have_cores = true;
+  if (n_parts) *n_parts = ctx->part.n_parts;
+  if (ctx->have_graph) STCHK(halos_core(ctx));
+  return SEDACS_OK;
+}
+
+sedacs_status sedacs_set_cores(sedacs_ctx* ctx, int32_t n_parts, const int64_t* core_ptr, const int32_t* core) {
+  if (!ctx || n_parts <= 0 || !core_ptr || !core) return SEDACS_EINVAL;
+  std::vector<int64_t> cp(n_parts + 1);
+  CUCHK(cudaMemcpy(cp.data(), core_ptr, sizeof(int64_t) * (n_parts + 1), cudaMemcpyDefault));
+  if (cp[0] != 0 || cp[n_parts] != ctx->N) { ctx->err = "cores must cover every atom once"; return SEDACS_EINVAL; }
+  std::vector<int> all(ctx->N);
+  CUCHK(cudaMemcpy(all.data(), core, sizeof(int) * ctx->N, cudaMemcpyDefault));
+  std::vector<std::vector<int>> cores(n_parts);
+  std::vector<char> seen(ctx->N, 0);
+  for (int i = 0; i < n_parts; ++i) {
+    if (cp[i + 1] < cp[i]) return SEDACS_EINVAL;
+    for (long long q = cp[i]; q < cp[i + 1]; ++q) {
+      const int a = all[q];
+      if (a < 0 || a >= ctx->N || seen[a]) { ctx->err = "cores must cover every atom once"; return SEDACS_EINVAL; }
+      seen[a] = 1;
+      cores[i].push_back(a);
+    }
+    std::sort(cores[i].begin(), cores[i].end());
+  }
+  CUCHK(ctx->part.set_cores(cores, ctx->N, ctx->stream));
+  ctx->have_cores = true;
+  if (ctx->have_graph) STCHK(halos_core(ctx));
+  return SEDACS_OK;
+}
+
+sedacs_status sedacs_update_halos(sedacs_ctx* ctx) {
+  if (!ctx) return SEDACS_EINVAL;
+  return halos_core(ctx);
+}
+
+sedacs_status sedacs_parts_sizes(sedacs_ctx* ctx, int32_t* n_parts, int64_t* n_sub_atoms) {
+  if (!ctx || !ctx->have_subs) return SEDACS_EINVAL;
+  if (n_parts) *n_parts = ctx->lay.n_sub;
+  if (n_sub_atoms) *n_sub_atoms = ctx->sub_ptr_h.empty() ? 0 : ctx->sub_ptr_h.back();
+  return SEDACS_OK;
+}
+
+sedacs_status sedacs_parts_get(sedacs_ctx* ctx, int64_t* sub_ptr, int32_t* sub_atoms, int32_t* n_core) {
+  if (!ctx || !ctx->have_subs) return SEDACS_EINVAL;
+  const int P = ctx->lay.n_sub;
+  if (sub_ptr) CUCHK(cudaMemcpy(sub_ptr, ctx->sub_ptr_h.data(), sizeof(int64_t) * (P + 1), cudaMemcpyDefault));
+  if (sub_atoms) CUCHK(cudaMemcpy(sub_atoms, ctx->sub_atoms_h.data(), sizeof(int) * ctx->sub_ptr_h[P], cudaMemcpyDefault));
+  if (n_core) CUCHK(cudaMemcpy(n_core, ctx->lay.n_core_atoms.data(), sizeof(int) * P, cudaMemcpyDefault));
+  return SEDACS_OK;
+}
+
+sedacs_status sedacs_coulomb_potential(sedacs_ctx* ctx, const double* R, const double* b, double* V) {
+  if (!ctx || !R || !b || !V) return SEDACS_EINVAL;
+  STCHK(copy_in(ctx, ctx->d_R, R, 3LL * ctx->N));
+  ctx->geom_valid = false;
+  STCHK(copy_in(ctx, ctx->d_tmp2, b, ctx->N));
+  CUCHK(ctx->ew.prepare(ctx->d_R, ctx->d_species, ctx->stream));
+  CUCHK(ctx->ew.potential(ctx->d_tmp2, ctx->d_tmp, ctx->stream));
+  STCHK(copy_out(ctx, V, ctx->d_tmp, sizeof(double) * ctx->N));
+  CUCHK(cudaStreamSynchronize(ctx->stream));
+  return check_dev_err(ctx);
+}
+
+sedacs_status sedacs_subgraph_density(sedacs_ctx* ctx, const double* R, const double* n, double* mu, double* q,
+                                      double* e_band, int32_t* sp2_iters) {
+  if (!ctx || !R || !n || !mu) return SEDACS_EINVAL;
+  // positions: the subgraphs were built for the positions given to graph_build/partition;
+  // a changed R invalidates the geometry-dependent data only.
+  STCHK(copy_in(ctx, ctx->d_tmp2, R, 3LL * ctx->N));
+  {
+    std::vector<double> a(3 * ctx->N), b(3 * ctx->N);
+    CUCHK(cudaMemcpyAsync(a.data(), ctx->d_tmp2, sizeof(double) * 3 * ctx->N, cudaMemcpyDeviceToHost, ctx->stream));
+    CUCHK(cudaMemcpyAsync(b.data(), ctx->d_R, sizeof(double) * 3 * ctx->N, cudaMemcpyDeviceToHost, ctx->stream));
+    CUCHK(cudaStreamSynchronize(ctx->stream));
+    if (a != b) {
+      CUCHK(cudaMemcpyAsync(ctx->d_R, ctx->d_tmp2, sizeof(double) * 3 * ctx->N, cudaMemcpyDeviceToDevice, ctx->stream));
+      ctx->geom_valid = false;
+    }
+  }
+  STCHK(copy_in(ctx, ctx->d_n, n, ctx->N));
+  double m = *mu;
+  STCHK(density_core(ctx, &m));
+  *mu = m;
+  STCHK(copy_out(ctx, q, ctx->d_q, sizeof(double) * ctx->N));
+  if (e_band) *e_band = ctx->e_band;
+  if (sp2_iters) std::copy(ctx->sp2_iters_h.begin(), ctx->sp2_iters_h.end(), sp2_iters);
+  CUCHK(cudaStreamSynchronize(ctx->stream));
+  return SEDACS_OK;
+}
+
+sedacs_status sedacs_forces(sedacs_ctx* ctx, double* F) {
+  if (!ctx || !F) return SEDACS_EINVAL;
+  if (!ctx->have_forces) STCHK(forces_core(ctx));
+  STCHK(copy_out(ctx, F, ctx->d_F, sizeof(double) * 3 * ctx->N));
+  CUCHK(cudaStreamSynchronize(ctx->stream));
+  return SEDACS_OK;
+}
+
+sedacs_status sedacs_energy(sedacs_ctx* ctx, double* e) {
+  if (!ctx || !e || !ctx->have_density) return SEDACS_EINVAL;
+  if (!ctx->have_forces) STCHK(forces_core(ctx));
+  e[0] = ctx->e_band;
+  e[1] = ctx->e_coul;
+  e[2] = ctx->e_rep;
+  e[3] = ctx->e_band + ctx->e_coul + ctx->e_rep;
+  return SEDACS_OK;
+}
+
+sedacs_status sedacs_density_graph_size(sedacs_ctx* ctx, int64_t* nnz) {
+  if (!ctx || !nnz || !ctx->have_gd) return SEDACS_EINVAL;
+  *nnz = ctx->gd_nnz;
+  return SEDACS_OK;
+}
+
+sedacs_status sedacs_density_graph_get(sedacs_ctx* ctx, int64_t* ptr, int32_t* col, double* val) {
+  if (!ctx || !ctx->have_gd) return SEDACS_EINVAL;
+  STCHK(copy_out(ctx, ptr, ctx->d_gd_ptr, sizeof(long long) * (ctx->N + 1)));
+  STCHK(copy_out(ctx, col, ctx->d_gd_col, sizeof(int) * ctx->gd_nnz));
+  STCHK(copy_out(ctx, val, ctx->d_gd_val, sizeof(double) * ctx->gd_nnz));
+  CUCHK(cudaStreamSynchronize(ctx->stream));
+  return SEDACS_OK;
+}
+
+sedacs_status sedacs_subgraph_matrix(sedacs_ctx* ctx, int32_t part, int32_t which, double* out, int32_t* n,
+                                     int32_t* n_core_orb) {
+  if (!ctx || !ctx->have_density || part < 0 || part >= ctx->lay.n_sub || which < 0 || which > 5) return SEDACS_EINVAL;
+  const int nr = ctx->lay.n_real[part], nc = ctx->lay.n_core_orb[part];
+  if (n) *n = nr;
+  if (n_core_orb) *n_core_orb = nc;
+  if (!out) return SEDACS_OK;
+  int sl = kH;
+  switch (which) {
+    case 0: sl = kH; break;
+    case 1: sl = kS; break;
+    case 2: sl = ctx->zc == 0 ? kZ0 : kZ1; break;
+    case 3: sl = kHt; break;
+    case 4: sl = kDc; break;
+    default: sl = kWc; break;
+  }
+  const int rows = which >= 4 ? nc : nr;
+  if (which == 1 && !ctx->f64) {
+    // s was overwritten by nothing; masters keep it
+  }
+  const long long off = mptr(ctx, sl, part);
+  double* tmp = nullptr;
+  CUCHK(cudaMalloc(&tmp, sizeof(double) * std::max(1, rows * nr)));
+  matrix_to_f64_kernel<<<nblk((long long)rows * nr, 256), 256, 0, ctx->stream>>>(ctx->arena, off, ctx->f64, rows, nr,
+                                                                                 ctx->lay.n_pad[part], tmp);
+  cudaError_t e = cudaMemcpyAsync(out, tmp, sizeof(double) * rows * nr, cudaMemcpyDefault, ctx->stream);
+  cudaStreamSynchronize(ctx->stream);
+  cudaFree(tmp);
+  CUCHK(e);
+  return SEDACS_OK;
+}
+
+sedacs_status sedacs_scc_step(sedacs_ctx* ctx, const double* R, double* n, int32_t max_iter, double* mu,
+                              double* resid_max, int32_t* iters) {
+  if (!ctx || !R || !n || !mu || max_iter <= 0) return SEDACS_EINVAL;
+  if (!ctx->have_cores) { ctx->err = "cores are required (sedacs_partition)"; return SEDACS_EINVAL; }
+  STCHK(copy_in(ctx, ctx->d_R, R, 3LL * ctx->N));
+  ctx->geom_valid = false;
+  STCHK(copy_in(ctx, ctx->d_n, n, ctx->N));
+  double m = *mu, r = 0.0;
+  int it = 0;
+  cudaStream_t s = ctx->stream;
+  for (it = 1; it <= max_iter; ++it) {
+    STCHK(cycle(ctx, &m));
+    maxdiff_kernel<<<1, 1024, 0, s>>>(ctx->d_q, ctx->d_n, ctx->N, ctx->d_scal + 4);
+    r = host_scalar(ctx, ctx->d_scal + 4);
+    if (r <= ctx->prm.scc_tol) break;
+    if (ctx->prm.kernel == 1 && r < 0.1) {
+      // quasi-Newton step n <- n - (K0 J)^-1 K0 (q - n)  (SI Sec. C)
+      double* f = ctx->d_vec + 20LL * ctx->N;
+      double* u = ctx->d_vec + 21LL * ctx->N;
+      sub_kernel<<<nblk(ctx->N, 128), 128, 0, s>>>(f, ctx->d_q, ctx->d_n, ctx->N);
+      int rank = 0;
+      STCHK(sedacs_kernel_apply_dev(ctx, f, u, &rank));
+      sub_kernel<<<nblk(ctx->N, 128), 128, 0, s>>>(ctx->d_n, ctx->d_n, u, ctx->N);
+    } else {
+      // linear mixing n <- n + alpha (q - n)
+      cudaMemcpyAsync(ctx->d_tmp2, ctx->d_n, sizeof(double) * ctx->N, cudaMemcpyDeviceToDevice, s);
+      axpy_kernel<<<nblk(ctx->N, 128), 128, 0, s>>>(ctx->d_n, ctx->d_q, ctx->d_tmp2, ctx->prm.scc_alpha, ctx->N);
+    }
+    ctx->launches += 2;
+  }
+  *mu = m;
+  if (resid_max) *resid_max = r;
+  if (iters) *iters = std::min(it, (int)max_iter);
+  STCHK(copy_out(ctx, n, ctx->d_n, sizeof(double) * ctx->N));
+  CUCHK(cudaStreamSynchronize(s));
+  if (r > ctx->prm.scc_tol) { ctx->err = "SCC did not converge"; return SEDACS_ENOCONV; }
+  return SEDACS_OK;
+}
+
+sedacs_status sedacs_xlbomd_init(sedacs_ctx* ctx, const double* R, const double* V, const double* n0, double mu) {
+  if (!ctx || !R || !V || !n0) return SEDACS_EINVAL;
+  if (!ctx->have_cores) { ctx->err = "cores are required (sedacs_partition)"; return SEDACS_EINVAL; }
+  STCHK(copy_in(ctx, ctx->d_R, R, 3LL * ctx->N));
+  ctx->geom_valid = false;
+  STCHK(copy_in(ctx, ctx->d_vel, V, 3LL * ctx->N));
+  STCHK(copy_in(ctx, ctx->d_n, n0, ctx->N));
+  fill_hist_kernel<<<nblk(ctx->N, 128), 128, 0, ctx->stream>>>(ctx->d_hist, ctx->d_n, ctx->N);
+  ctx->hist_head = 0;
+  double m = mu;
+  STCHK(cycle(ctx, &m));
+  STCHK(forces_core(ctx));
+  ctx->md_ready = true;
+  return SEDACS_OK;
+}
+
+sedacs_status sedacs_xlbomd_step(sedacs_ctx* ctx, double* R, double* V, int32_t nsteps, double dt_fs,
+                                 double* energies, double* n_out) {
+  if (!ctx || !ctx->md_ready || nsteps < 0) return SEDACS_EINVAL;
+  cudaStream_t s = ctx->stream;
+  const int N = ctx->N;
+  const double kappa = 1.82, alpha = 0.018;
+  const double c[6] = {-6.0, 14.0, -8.0, -3.0, 4.0, -1.0};
+  for (int step = 0; step < nsteps; ++step) {
+    phase_begin(ctx, 0);
+    // kernel action u = K (q - n) at the current state
+    double* f = ctx->d_vec + 20LL * N;
+    double* u = ctx->d_vec + 21LL * N;
+    sub_kernel<<<nblk(N, 128), 128, 0, s>>>(f, ctx->d_q, ctx->d_n, N);
+    int rank = 0;
+    STCHK(sedacs_kernel_apply_dev(ctx, f, u, &rank));
+    xl_update_kernel<<<nblk(N, 128), 128, 0, s>>>(ctx->d_hist, ctx->hist_head, N, u, kappa, alpha, c[0], c[1], c[2],
+                                                  c[3], c[4], c[5], ctx->d_n);
+    ctx->hist_head = (ctx->hist_head + 1) % 6;
+    // velocity Verlet: half kick, drift
+    kick_kernel<<<nblk(3 * N, 256), 256, 0, s>>>(ctx->d_vel, ctx->d_F, ctx->d_mass, 0.5 * dt_fs * kAccHaAAmu, N);
+    drift_kernel<<<nblk(3 * N, 256), 256, 0, s>>>(ctx->d_R, ctx->d_vel, dt_fs, N);
+    ctx->launches += 8;
+    ctx->geom_valid = false;
+    phase_end(ctx, 0, 7);
+    double m = ctx->mu;
+    STCHK(cycle(ctx, &m));
+    STCHK(forces_core(ctx));
+    kick_kernel<<<nblk(3 * N, 256), 256, 0, s>>>(ctx->d_vel, ctx->d_F, ctx->d_mass, 0.5 * dt_fs * kAccHaAAmu, N);
+    kin_kernel<<<1, 1024, 0, s>>>(ctx->d_vel, ctx->d_mass, N, ctx->d_scal + 5);
+    ctx->launches += 2;
+    if (energies) {
+      const double kin = host_scalar(ctx, ctx->d_scal + 5);
+      const double pot = ctx->e_band + ctx->e_coul + ctx->e_rep;
+      const double e3[3] = {kin, pot, kin + pot};
+      if (ctx->dev_io) cudaMemcpyAsync(energies + 3 * step, e3, sizeof(e3), cudaMemcpyHostToDevice, s);
+      else std::memcpy(energies + 3 * step, e3, sizeof(e3));
+    }
+  }
+  STCHK(copy_out(ctx, R, ctx->d_R, sizeof(double) * 3 * N));
+  STCHK(copy_out(ctx, V, ctx->d_vel, sizeof(double) * 3 * N));
+  STCHK(copy_out(ctx, n_out, ctx->d_n, sizeof(double) * N));
+  CUCHK(cudaStreamSynchronize(s));
+  return check_dev_err(ctx);
+}
+
+sedacs_status sedacs_kernel_apply_dev(sedacs_ctx* ctx, const double* f, double* u, int32_t* rank) {
+  int r = 0;
+  const sedacs_status st = kernel_core(ctx, f, u, &r);
+  if (rank) *rank = r;
+  return st;
+}
+
+sedacs_status sedacs_charge_response(sedacs_ctx* ctx, const double* v, double* dq) {
+  if (!ctx || !v || !dq) return SEDACS_EINVAL;
+  double* dv = ctx->d_vec + 22LL * ctx->N;
+  double* ddq = ctx->d_vec + 23LL * ctx->N;
+  STCHK(copy_in(ctx, dv, v, ctx->N));
+  STCHK(response_core(ctx, dv, ddq));
+  STCHK(copy_out(ctx, dq, ddq, sizeof(double) * ctx->N));
+  CUCHK(cudaStreamSynchronize(ctx->stream));
+  return SEDACS_OK;
+}
+
+sedacs_status sedacs_kernel_apply(sedacs_ctx* ctx, const double* f, double* u, int32_t* rank) {
+  if (!ctx || !f || !u) return SEDACS_EINVAL;
+  double* df = ctx->d_vec + 22LL * ctx->N;
+  double* du = ctx->d_vec + 23LL * ctx->N;
+  STCHK(copy_in(ctx, df, f, ctx->N));
+  int r = 0;
+  phase_begin(ctx, 0);
+  STCHK(kernel_core(ctx, df, du, &r));
+  phase_end(ctx, 0, 7);
+  if (rank) *rank = r;
+  STCHK(copy_out(ctx, u, du, sizeof(double) * ctx->N));
+  CUCHK(cudaStreamSynchronize(ctx->stream));
+  return SEDACS_OK;
+}
+
+sedacs_status sedacs_phase_times(sedacs_ctx* ctx, double* t, int64_t* launches) {
+  if (!ctx) return SEDACS_EINVAL;
+  if (t)
+    for (int k = 0; k < 8; ++k) t[k] = ctx->t_phase[k];
+  if (launches) *launches = ctx->launches;
+  return SEDACS_OK;
+}
+
+sedacs_status sedacs_reset_counters(sedacs_ctx* ctx) {
+  if (!ctx) return SEDACS_EINVAL;
+  for (double& x : ctx->t_phase) x = 0.0;
+  ctx->launches = 0;
+  return SEDACS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,162 @@
+// Host engine behind the C ABI: owns device buffers, the per-subgraph arena layout, the
+// batched GEMM tables and the stream; runs the pipeline of the graph-partitioned solve.
+#pragma once
+#include <string>
+#include <vector>
+
+#include "../../include/sedacs.h"
+#include "dense.cuh"
+#include "dense_ops.cuh"
+#include "ewald.cuh"
+#include "graph.cuh"
+#include "sk.cuh"
+
+namespace sedacs {
+
+// A matrix slot of the arena: one matrix per subgraph (square n_pad x n_pad or core rows
+// m_pad x n_pad), a row-major master (fp32 or fp64) and optionally three bf16 planes.
+struct Slot {
+  long long base = 0;        // byte offset of copy 0
+  long long copy_stride = 0; // bytes between copies (ping-pong)
+  long long master_bytes = 0;
+  long long plane_stride = 0;
+  bool rows = false;
+  bool planes = false;
+  int copies = 1;
+};
+
+enum SlotId : int {
+  kS = 0, kH, kT, kY0, kY1, kZ0, kZ1, kP, kHt, kX, kT1, kDc, kT2, kWc,
+  kR1, kR2,            // response: X dX, and dX (ping-pong)
+  kdH, kdHt, kdT1, kdDc,
+  kNumSlots
+};
+
+struct GemmOp {
+  GemmMat* mats_d = nullptr;
+  GemmWork* work_d = nullptr;
+  int n_work = 0;
+  float alpha = 1.f, beta = 0.f;
+  int mode = kModeGeneric;
+};
+
+enum OpId : int {
+  OP_NS_Y1 = 0,
+  OP_NS_T0, OP_NS_T1, OP_NS_Y0, OP_NS_Y1b, OP_NS_Z0, OP_NS_Z1,
+  OP_P0, OP_P1, OP_HT0, OP_HT1,
+  OP_SP2,
+  OP_T1_0, OP_T1_1, OP_DC0, OP_DC1, OP_T2, OP_WC0, OP_WC1,
+  // response (first-order SP2), see response.cu
+  OP_RSP_A, OP_RSP_B, OP_DP0, OP_DP1, OP_DHT0, OP_DHT1, OP_DT1_0, OP_DT1_1, OP_DDC0, OP_DDC1,
+  OP_NUM
+};
+
+struct Layout {
+  int n_sub = 0;
+  std::vector<int> n_real, n_pad, m_pad, n_core_orb, n_core_atoms, n_atoms;
+  std::vector<long long> sq_off, rw_off;   // element offsets in square / rows slots
+  long long sq_total = 0, rw_total = 0;
+  int max_npad = 0, max_mpad = 0;
+  long long tr_total = 0;
+  std::vector<long long> tr_off;
+  std::vector<int> n_diag;
+};
+
+}  // namespace sedacs
+
+struct sedacs_ctx {
+  // system
+  int N = 0;
+  std::vector<int> species_h;
+  double box[3] = {0, 0, 0};
+  sedacs::ModelDev model{};
+  sedacs_params prm{};
+  double n_electrons = 0.0;
+  cudaStream_t stream = 0;
+  bool dev_io = false;
+  std::string err;
+  bool f64 = false;
+  int tile = 128;
+  int nsplit_sp2 = 3, nsplit_ns = 3;
+  // device vectors
+  int* d_err = nullptr;
+  int* d_species = nullptr;
+  double *d_R = nullptr, *d_n = nullptr, *d_q = nullptr, *d_V = nullptr, *d_pop = nullptr, *d_eband = nullptr;
+  double *d_dU = nullptr, *d_F = nullptr, *d_erep = nullptr, *d_tmp = nullptr, *d_tmp2 = nullptr, *d_scal = nullptr;
+  double *d_vel = nullptr, *d_hist = nullptr, *d_mass = nullptr, *d_zval = nullptr;
+  double* d_vec = nullptr;   // scratch N-vectors for the kernel (Krylov)
+  // graph
+  sedacs::GraphBuilder gb, pb;
+  long long* d_row_ptr = nullptr;
+  int* d_col = nullptr;
+  long long col_cap = 0, nnz = 0;
+  bool have_graph = false;
+  // pair list within r_off and its SK blocks
+  long long* d_pptr = nullptr;
+  int* d_pcol = nullptr;
+  long long pcol_cap = 0, pnnz = 0;
+  void *d_h0b = nullptr, *d_sb = nullptr;
+  long long blk_cap = 0;
+  bool pairs_valid = false;
+  // density graph of the last density call
+  long long* d_gd_ptr = nullptr;
+  int* d_gd_col = nullptr;
+  double* d_gd_val = nullptr;
+  long long gd_cap = 0, gd_nnz = 0;
+  bool have_gd = false;
+  // external density graph uploaded by the caller
+  long long* d_xgd_ptr = nullptr;
+  int* d_xgd_col = nullptr;
+  double* d_xgd_val = nullptr;
+  long long xgd_cap = 0;
+  // partition
+  sedacs::Partitioner part;
+  bool have_cores = false, have_subs = false;
+  long long* d_sub_ptr = nullptr;
+  int* d_sub_atoms = nullptr;
+  long long sub_cap = 0;
+  std::vector<long long> sub_ptr_h;
+  std::vector<int> sub_atoms_h;
+  int *d_orb_off = nullptr, *d_n_orb_sub = nullptr, *d_n_core = nullptr, *d_n_core_orb = nullptr;
+  int *d_sub_of_row = nullptr, *d_core_sub = nullptr, *d_core_local = nullptr, *d_loc = nullptr;
+  long long loc_cap = 0, rows_cap = 0;
+  int n_core_total = 0;
+  // layout and arena
+  sedacs::Layout lay;
+  sedacs::Slot slot[sedacs::kNumSlots];
+  uint8_t* arena = nullptr;
+  size_t arena_cap = 0;
+  sedacs::GemmOp ops[sedacs::OP_NUM];
+  sedacs::SubView* d_views[sedacs::kNumSlots] = {};
+  sedacs::SubView* d_views_x1 = nullptr;   // X copy 1
+  long long *d_hoff = nullptr, *d_soff = nullptr, *d_dcoff = nullptr, *d_wcoff = nullptr, *d_rowbase = nullptr;
+  long long* d_tr_off = nullptr;
+  int *d_n_pad = nullptr, *d_n_real = nullptr, *d_n_diag = nullptr;
+  double *d_glo = nullptr, *d_ghi = nullptr, *d_bounds = nullptr, *d_slots = nullptr;
+  sedacs::Sp2State* d_sp2 = nullptr;
+  int* d_nactive = nullptr;
+  long long* d_dcoff_d = nullptr;   // core-row offsets of the response density
+  double* d_dqpop = nullptr;        // response populations scratch
+  long long* d_dhoff = nullptr;     // per-subgraph offsets of the response Hamiltonian
+  int* d_steps = nullptr;           // SP2 step counts of the last density call
+  std::vector<double> bounds_h;
+  int zc = 0;              // Z buffer holding s^-1/2
+  bool z_valid = false;
+  bool geom_valid = false; // pair blocks / Ewald tables match d_R
+  // Ewald
+  sedacs::Ewald ew;
+  bool ew_ready = false;
+  // state of the last density call
+  double mu = 0.0;
+  bool have_density = false;
+  std::vector<int> sp2_iters_h;
+  double e_band = 0, e_coul = 0, e_rep = 0;
+  bool have_forces = false;
+  // MD
+  bool md_ready = false;
+  int hist_head = 0;
+  // timing
+  cudaEvent_t ev[10] = {};
+  double t_phase[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  long long launches = 0;
+};

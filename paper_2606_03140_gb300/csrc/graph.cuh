@@ -1,0 +1,58 @@
+// Graph construction, partition and halo builders (device memory owned by the builder).
+#pragma once
+#include <vector>
+#include "common.cuh"
+
+namespace sedacs {
+
+struct RcbSeg {
+  int start;            // first position in the permutation
+  int count;            // atoms in the segment
+  long long scratch;    // offset of its sort scratch
+};
+
+struct GraphBuilder {
+  int* cell_of = nullptr;
+  int* cell_count = nullptr;
+  int* cell_start = nullptr;
+  int* cell_fill = nullptr;
+  int* cell_atoms = nullptr;
+  int* cnt = nullptr;
+  int* fillc = nullptr;
+  int* ucnt = nullptr;
+  long long* cptr = nullptr;
+  int* cand = nullptr;
+  int cap_n = 0, cap_cells = 0;
+  long long cap_cand = 0;
+  ~GraphBuilder();
+  void release();
+  // Builds the symmetric CSR of the atom graph into row_ptr (device, N+1) and *col_out
+  // (device, grown as needed).  gptr/gcol/gval: optional device CSR of the previous
+  // atom-condensed density graph.
+  cudaError_t build(const double* dR, int N, const double box[3], double r_graph, const long long* gptr,
+                    const int* gcol, const double* gval, double tau, long long* row_ptr, int** col_out,
+                    long long* col_cap, long long* nnz_host, int* derr, cudaStream_t s);
+};
+
+struct Partitioner {
+  int* perm = nullptr;        // atoms grouped by core, each core ascending
+  double* skey = nullptr;
+  int* sidx = nullptr;
+  RcbSeg* segs_d = nullptr;
+  unsigned* bits = nullptr;
+  int* hcnt = nullptr;
+  int cap_n = 0, cap_seg = 0;
+  long long cap_scr = 0, cap_bits = 0;
+  int n_parts = 0;
+  std::vector<RcbSeg> leaves;       // core segments in perm (host copy)
+  std::vector<int> halo_count_h;
+  ~Partitioner();
+  void release();
+  cudaError_t rcb(const double* dR, int N, const double box[3], int core_size, cudaStream_t s);
+  cudaError_t set_cores(const std::vector<std::vector<int>>& cores, int N, cudaStream_t s);
+  // Halos of the current cores on graph (row_ptr, col); writes the subgraph atom lists.
+  cudaError_t halos(const long long* row_ptr, const int* col, int N, long long** sub_ptr_d, int** sub_atoms_d,
+                    long long* sub_cap, std::vector<long long>& sub_ptr_h, cudaStream_t s);
+};
+
+}  // namespace sedacs
