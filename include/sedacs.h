@@ -179,6 +179,12 @@ sedacs_status sedacs_xlbomd_step(sedacs_ctx* ctx, double* R, double* V, int32_t 
  * sedacs_reset_counters() in *launches. */
 sedacs_status sedacs_phase_times(sedacs_ctx* ctx, double* t, int64_t* launches);
 sedacs_status sedacs_reset_counters(sedacs_ctx* ctx);
+/* Per-launch timing of the SP2 square kernel: on != 0 records CUDA events around every launch
+ * on the context stream.  Returns the accumulated kernel time (ms), number of launches and
+ * the algorithmic work of those launches (sum over subgraphs of steps * n^3 multiply-add
+ * pairs, n the orbital count: one symmetric square per step) since the last reset. */
+sedacs_status sedacs_kernel_stats(sedacs_ctx* ctx, int32_t on, double* sp2_ms, int64_t* sp2_launches,
+                                  double* sp2_flops);
 
 #ifdef __cplusplus
 }

@@ -59,21 +59,26 @@ def sp2_mu_occupations(x: np.ndarray, y: float, n_real: int, tol: float = 1e-9, 
     Matrix Evaluation on Partitioned Graphs", refs. Niklasson 2002 / Finkelstein 2021)
     with the branch set by the image y of the chemical potential: y >= 1/2 -> x <- x^2,
     y <- y^2; else x <- 2x - x^2, y <- 2y - y^2.  At step k the idempotency error
-    t_k = sum x(1-x) of the current iterate is taken, the update is applied, and the
-    recursion stops after the first step with t_k < tol * n_real (or after kmax).
+    t_k = sum x(1-x) of the current iterate is taken and the update is applied.  The
+    recursion stops after the first step with t_k < tol * n_real, or -- the parameterless
+    rule of Kruchinina, Rudberg and Rubensson (2016) for finite precision -- after the
+    first step k >= 4 with t_{k-2} < 1e-4 n_real and t_k >= t_{k-2}, or after kmax steps.
     Returns (occupations, number of steps).
     """
     x = np.array(x, dtype=np.float64)
     it = 0
+    hist = []
     for it in range(1, kmax + 1):
         t = float(np.sum(x - x * x))
+        hist.append(t)
         if y >= 0.5:
             x = x * x
             y = y * y
         else:
             x = 2.0 * x - x * x
             y = 2.0 * y - y * y
-        if t < tol * n_real:
+        floor_hit = it >= 4 and hist[-3] < 1e-4 * n_real and t >= hist[-3]
+        if t < tol * n_real or floor_hit:
             break
     return x, it
 

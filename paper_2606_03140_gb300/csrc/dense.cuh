@@ -36,7 +36,9 @@ struct GemmWork {
 struct Sp2State {
   double y;          // image of mu under the polynomial so far
   double t;          // last idempotency error Tr(X - X^2)
+  double t1, t2;     // the two errors before it
   double tol;        // stop when t < tol
+  double floor_guard;// noise-floor stop applies once t_{k-2} < floor_guard
   int active;        // 1 while iterating
   int iters;         // completed steps
   int cur;           // buffer holding the current iterate

@@ -136,8 +136,9 @@ __global__ void sp2_replay_init_kernel(Sp2State* st, const double* bounds, const
   const double emin = bounds[2 * i], emax = bounds[2 * i + 1];
   Sp2State s;
   s.y = (emax - mu) / (emax - emin);
-  s.t = 0.0;
+  s.t = s.t1 = s.t2 = 0.0;
   s.tol = -1.0;
+  s.floor_guard = -1.0;
   s.iters = 0;
   s.cur = 0;
   s.kmax = steps[i];
@@ -152,8 +153,9 @@ __global__ void sp2_init_kernel(Sp2State* st, const double* bounds, const int* n
   const double emin = bounds[2 * i], emax = bounds[2 * i + 1];
   Sp2State s;
   s.y = (emax - mu) / (emax - emin);
-  s.t = 0.0;
+  s.t = s.t1 = s.t2 = 0.0;
   s.tol = tol * (double)n_real[i];
+  s.floor_guard = 1e-4 * (double)n_real[i];
   s.active = n_real[i] > 0 ? 1 : 0;
   s.iters = 0;
   s.cur = 0;
@@ -174,11 +176,16 @@ __global__ void sp2_advance_kernel(Sp2State* st, const double* slots, const long
     a += slots[tr_off[i] + 2 * q];
     b += slots[tr_off[i] + 2 * q + 1];
   }
+  s.t2 = s.t1;
+  s.t1 = s.t;
   s.t = a - b;
   s.y = (s.y >= 0.5) ? s.y * s.y : 2.0 * s.y - s.y * s.y;
   s.cur ^= 1;
   s.iters += 1;
-  if (s.t < s.tol || s.iters >= s.kmax) s.active = 0;
+  // stop on the tolerance, or once the error no longer falls over two steps in the
+  // asymptotic regime (rounding noise floor of the arithmetic in use)
+  const bool floor_hit = s.iters >= 4 && s.t2 < s.floor_guard && s.t >= s.t2;
+  if (s.t < s.tol || floor_hit || s.iters >= s.kmax) s.active = 0;
   else atomicAdd(n_active, 1);
   st[i] = s;
 }

@@ -623,8 +623,15 @@ sedacs_status run_sp2(sedacs_ctx* ctx, double mu, int kmax) {
   launch_sp2_init(ctx->d_sp2, ctx->d_bounds, ctx->d_n_real, mu, ctx->prm.sp2_tol, kmax, L.n_sub, s);
   ctx->launches += ctx->f64 ? 2 : 3;
   if (!ctx->d_nactive) CUCHK(cudaMalloc(&ctx->d_nactive, sizeof(int)));
+  const int ev0 = ctx->kev_used;
   for (int k = 0; k < kmax; ++k) {
+    const bool rec = ctx->kstats && ctx->kev_used + 2 <= (int)ctx->kev.size();
+    if (rec) cudaEventRecord(ctx->kev[ctx->kev_used], s);
     run_op(ctx, OP_SP2, ctx->nsplit_sp2, ctx->nsplit_sp2);
+    if (rec) {
+      cudaEventRecord(ctx->kev[ctx->kev_used + 1], s);
+      ctx->kev_used += 2;
+    }
     cudaMemsetAsync(ctx->d_nactive, 0, sizeof(int), s);
     launch_sp2_advance(ctx->d_sp2, ctx->d_slots, ctx->d_tr_off, ctx->d_n_diag, ctx->d_nactive, L.n_sub, s);
     ctx->launches += 1;
@@ -633,6 +640,23 @@ sedacs_status run_sp2(sedacs_ctx* ctx, double mu, int kmax) {
       CUCHK(cudaMemcpyAsync(&na, ctx->d_nactive, sizeof(int), cudaMemcpyDeviceToHost, s));
       CUCHK(cudaStreamSynchronize(s));
       if (na == 0) break;
+    }
+  }
+  if (ctx->kstats) {
+    CUCHK(cudaStreamSynchronize(s));
+    for (int e = ev0; e + 1 < ctx->kev_used; e += 2) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ctx->kev[e], ctx->kev[e + 1]);
+      ctx->k_ms += ms;
+      ctx->k_launches += 1;
+    }
+    ctx->kev_used = ev0;
+    // algorithmic work of these launches: one symmetric square = n^3 multiply-adds pairs
+    std::vector<Sp2State> st(ctx->lay.n_sub);
+    CUCHK(cudaMemcpy(st.data(), ctx->d_sp2, sizeof(Sp2State) * ctx->lay.n_sub, cudaMemcpyDeviceToHost));
+    for (int i = 0; i < ctx->lay.n_sub; ++i) {
+      const double nr = ctx->lay.n_real[i];
+      ctx->k_flops += (double)st[i].iters * nr * nr * nr;
     }
   }
   return SEDACS_OK;
@@ -962,8 +986,6 @@ sedacs_status kernel_core(sedacs_ctx* ctx, const double* f, double* u, int* rank
 // ===============================================================================================
 extern "C" {
 
-sedacs_status sedacs_kernel_apply_dev(sedacs_ctx* ctx, const double* f, double* u, int32_t* rank);
-
 void sedacs_default_params(sedacs_params* p) {
   if (!p) return;
   std::memset(p, 0, sizeof(*p));
@@ -1079,6 +1101,8 @@ void sedacs_destroy(sedacs_ctx* ctx) {
     if (op.work_d) cudaFree(op.work_d);
   }
   for (auto& e : ctx->ev)
+    if (e) cudaEventDestroy(e);
+  for (auto& e : ctx->kev)
     if (e) cudaEventDestroy(e);
   delete ctx;
 }
@@ -1312,7 +1336,7 @@ sedacs_status sedacs_scc_step(sedacs_ctx* ctx, const double* R, double* n, int32
       double* u = ctx->d_vec + 21LL * ctx->N;
       sub_kernel<<<nblk(ctx->N, 128), 128, 0, s>>>(f, ctx->d_q, ctx->d_n, ctx->N);
       int rank = 0;
-      STCHK(sedacs_kernel_apply_dev(ctx, f, u, &rank));
+      STCHK(kernel_core(ctx, f, u, &rank));
       sub_kernel<<<nblk(ctx->N, 128), 128, 0, s>>>(ctx->d_n, ctx->d_n, u, ctx->N);
     } else {
       // linear mixing n <- n + alpha (q - n)
@@ -1360,7 +1384,7 @@ sedacs_status sedacs_xlbomd_step(sedacs_ctx* ctx, double* R, double* V, int32_t 
     double* u = ctx->d_vec + 21LL * N;
     sub_kernel<<<nblk(N, 128), 128, 0, s>>>(f, ctx->d_q, ctx->d_n, N);
     int rank = 0;
-    STCHK(sedacs_kernel_apply_dev(ctx, f, u, &rank));
+    STCHK(kernel_core(ctx, f, u, &rank));
     xl_update_kernel<<<nblk(N, 128), 128, 0, s>>>(ctx->d_hist, ctx->hist_head, N, u, kappa, alpha, c[0], c[1], c[2],
                                                   c[3], c[4], c[5], ctx->d_n);
     ctx->hist_head = (ctx->hist_head + 1) % 6;
@@ -1389,13 +1413,6 @@ sedacs_status sedacs_xlbomd_step(sedacs_ctx* ctx, double* R, double* V, int32_t 
   STCHK(copy_out(ctx, n_out, ctx->d_n, sizeof(double) * N));
   CUCHK(cudaStreamSynchronize(s));
   return check_dev_err(ctx);
-}
-
-sedacs_status sedacs_kernel_apply_dev(sedacs_ctx* ctx, const double* f, double* u, int32_t* rank) {
-  int r = 0;
-  const sedacs_status st = kernel_core(ctx, f, u, &r);
-  if (rank) *rank = r;
-  return st;
 }
 
 sedacs_status sedacs_charge_response(sedacs_ctx* ctx, const double* v, double* dq) {
@@ -1432,8 +1449,25 @@ sedacs_status sedacs_phase_times(sedacs_ctx* ctx, double* t, int64_t* launches) 
   return SEDACS_OK;
 }
 
+sedacs_status sedacs_kernel_stats(sedacs_ctx* ctx, int32_t on, double* sp2_ms, int64_t* sp2_launches,
+                                  double* sp2_flops) {
+  if (!ctx) return SEDACS_EINVAL;
+  if (on && ctx->kev.empty()) {
+    ctx->kev.resize(512);
+    for (auto& e : ctx->kev) cudaEventCreate(&e);
+  }
+  ctx->kstats = on != 0;
+  if (sp2_ms) *sp2_ms = ctx->k_ms;
+  if (sp2_launches) *sp2_launches = ctx->k_launches;
+  if (sp2_flops) *sp2_flops = ctx->k_flops;
+  return SEDACS_OK;
+}
+
 sedacs_status sedacs_reset_counters(sedacs_ctx* ctx) {
   if (!ctx) return SEDACS_EINVAL;
+  ctx->k_ms = 0.0;
+  ctx->k_flops = 0.0;
+  ctx->k_launches = 0;
   for (double& x : ctx->t_phase) x = 0.0;
   ctx->launches = 0;
   return SEDACS_OK;

@@ -155,6 +155,12 @@ struct sedacs_ctx {
   // MD
   bool md_ready = false;
   int hist_head = 0;
+  // timing of the SP2 square kernel (per launch, events on the context stream)
+  bool kstats = false;
+  std::vector<cudaEvent_t> kev;
+  int kev_used = 0;
+  double k_ms = 0.0, k_flops = 0.0;
+  long long k_launches = 0;
   // timing
   cudaEvent_t ev[10] = {};
   double t_phase[8] = {0, 0, 0, 0, 0, 0, 0, 0};

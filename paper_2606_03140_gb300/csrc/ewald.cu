@@ -132,7 +132,11 @@ __global__ void sf_reduce_kernel(const double* part, int nchunk, int nv, long lo
 template <typename T, int MODE>
 __global__ void recip_atom_kernel(const KRow* rows, int nrows, const typename C2<T>::t* tab, const typename C2<T>::t* ws,
                                   long long nk, int N, int nmax_all, int m3max, EwaldGeom g, const double* av,
-                                  const double* bv, double* out) {
+                                  const double* bv, double* out_part) {
+  // block (atom chunk, row chunk): rows [r0, r1) of the k list, partial sums per row chunk
+  const int rchunk = (nrows + gridDim.y - 1) / gridDim.y;
+  const int r0 = blockIdx.y * rchunk, r1 = min(nrows, r0 + rchunk);
+  double* out = out_part + (long long)blockIdx.y * (MODE == 0 ? N : 3 * N);
   using CT = typename C2<T>::t;
   extern __shared__ unsigned char sm[];
   CT* zt = reinterpret_cast<CT*>(sm);          // [blockDim][2*m3max+1]
@@ -152,7 +156,7 @@ __global__ void recip_atom_kernel(const KRow* rows, int nrows, const typename C2
   double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
   const double tpx = 2.0 * M_PI / g.box_b[0], tpy = 2.0 * M_PI / g.box_b[1], tpz = 2.0 * M_PI / g.box_b[2];
   if (I < N) {
-    for (int r = 0; r < nrows; ++r) {
+    for (int r = r0; r < r1; ++r) {
       const KRow kr = rows[r];
       CT x = tab[(0LL * N + I) * (nmax_all + 1) + kr.m1];
       CT y = tab[(1LL * N + I) * (nmax_all + 1) + abs(kr.m2)];
@@ -171,8 +175,7 @@ __global__ void recip_atom_kernel(const KRow* rows, int nrows, const typename C2
         acc0 += (double)re;
       } else {
         // Im(S e^{-ikR}) for S_b (vector 0) and S_a (vector 1)
-        T i1 = 0, i2 = 0, i3 = 0;   // sum over m3 of Im-combination weighted by 1, m3
-        T j1 = 0, j3 = 0;
+        T i1 = 0, i3 = 0;   // sums over m3 of the Im-combination weighted by 1 and by m3
         for (int t = 0; t < nm3; ++t) {
           const int m3 = kr.m3lo + t;
           const CT sb = ws[kr.koff + t];
@@ -184,7 +187,6 @@ __global__ void recip_atom_kernel(const KRow* rows, int nrows, const typename C2
           const T comb = (T)av[I] * imb + (T)bv[I] * ima;
           i1 += comb;
           i3 += comb * (T)m3;
-          (void)i2; (void)j1; (void)j3;
         }
         acc0 += (double)i1 * (tpx * kr.m1);
         acc1 += (double)i1 * (tpy * kr.m2);
@@ -200,48 +202,56 @@ __global__ void recip_atom_kernel(const KRow* rows, int nrows, const typename C2
   }
 }
 
-// Real-space part, per atom I, over images within rc.  mode 0: V_I += sum_J phi b_J;
-// mode 1: dE/dR_I += -sum_J (a_I b_J + a_J b_I) phi'(d) d_hat.
+// Real-space part, one warp per atom I over images within rc.  mode 0: V_I += sum_J phi b_J;
+// mode 1: dE/dR_I += -sum_J (a_I b_J + a_J b_I) phi'(d) d_hat.  Differences of positions are
+// taken in FP64, the rest in T; lane sums are combined by a fixed shuffle tree.
 template <typename T, int MODE>
 __global__ void real_space_kernel(const double* R, const int* species, int N, EwaldGeom g, const int* cell_start,
                                   const int* cell_count, const int* cell_atoms, const int* cell_of, const double* av,
                                   const double* bv, double* out) {
-  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int I = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (I >= N) return;
-  const double rc2 = g.rc_b * g.rc_b;
+  const T rc2 = (T)(g.rc_b * g.rc_b);
   const T eta = (T)g.eta;
   const T sq = (T)1.1283791670955126;    // 2 / sqrt(pi)
+  const T inv_b = (T)(1.0 / kBohrA);
+  const T bx = (T)g.box_b[0], by = (T)g.box_b[1], bz = (T)g.box_b[2];
   const int si = species[I];
   double acc = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
-  auto visit = [&](int J, double dx, double dy, double dz) {
-    const double d2 = dx * dx + dy * dy + dz * dz;
-    if (d2 >= rc2 || d2 == 0.0) return;
-    const T d = (T)sqrt(d2);
+  const double xi = R[3 * I], yi = R[3 * I + 1], zi = R[3 * I + 2];
+  auto visit = [&](int J, T dx, T dy, T dz) {
+    const T d2 = dx * dx + dy * dy + dz * dz;
+    if (d2 >= rc2 || d2 == (T)0) return;
+    const T d = sqrt(d2);
     const T aij = (T)g.a[si][species[J]];
-    const T e1 = (T)erfc(eta * d), e2 = (T)erfc(aij * d);
+    const T e1 = erfc(eta * d), e2 = erfc(aij * d);
     const T phi = (e1 - e2) / d;
     if (MODE == 0) {
       acc += (double)phi * bv[J];
     } else {
-      const T dphi = (-sq * eta * (T)exp(-(eta * d) * (eta * d)) + sq * aij * (T)exp(-(aij * d) * (aij * d))) / d -
-                     phi / d;
+      const T dphi = (-sq * eta * exp(-(eta * d) * (eta * d)) + sq * aij * exp(-(aij * d) * (aij * d))) / d - phi / d;
       const double coef = (av[I] * bv[J] + av[J] * bv[I]) * (double)(dphi / d);
-      gx -= coef * dx;
-      gy -= coef * dy;
-      gz -= coef * dz;
+      gx -= coef * (double)dx;
+      gy -= coef * (double)dy;
+      gz -= coef * (double)dz;
     }
   };
-  const double xi = R[3 * I] / kBohrA, yi = R[3 * I + 1] / kBohrA, zi = R[3 * I + 2] / kBohrA;
+  auto rel = [&](int J, T& dx, T& dy, T& dz) {
+    dx = (T)(R[3 * J] - xi) * inv_b;
+    dy = (T)(R[3 * J + 1] - yi) * inv_b;
+    dz = (T)(R[3 * J + 2] - zi) * inv_b;
+    dx -= bx * rint(dx / bx);
+    dy -= by * rint(dy / by);
+    dz -= bz * rint(dz / bz);
+  };
   if (g.brute) {
-    for (int J = 0; J < N; ++J) {
-      double dx = R[3 * J] / kBohrA - xi, dy = R[3 * J + 1] / kBohrA - yi, dz = R[3 * J + 2] / kBohrA - zi;
-      dx -= g.box_b[0] * rint(dx / g.box_b[0]);
-      dy -= g.box_b[1] * rint(dy / g.box_b[1]);
-      dz -= g.box_b[2] * rint(dz / g.box_b[2]);
+    for (int J = lane; J < N; J += 32) {
+      T dx, dy, dz;
+      rel(J, dx, dy, dz);
       for (int ix = -g.nimg[0]; ix <= g.nimg[0]; ++ix)
         for (int iy = -g.nimg[1]; iy <= g.nimg[1]; ++iy)
-          for (int iz = -g.nimg[2]; iz <= g.nimg[2]; ++iz)
-            visit(J, dx + ix * g.box_b[0], dy + iy * g.box_b[1], dz + iz * g.box_b[2]);
+          for (int iz = -g.nimg[2]; iz <= g.nimg[2]; ++iz) visit(J, dx + ix * bx, dy + iy * by, dz + iz * bz);
     }
   } else {
     const int cid = cell_of[I];
@@ -253,22 +263,35 @@ __global__ void real_space_kernel(const double* R, const int* species, int N, Ew
           const int y = (cy + ddy + g.nc[1]) % g.nc[1];
           const int z = (cz + ddz + g.nc[2]) % g.nc[2];
           const int c = (x * g.nc[1] + y) * g.nc[2] + z;
-          for (int q = 0; q < cell_count[c]; ++q) {
+          for (int q = lane; q < cell_count[c]; q += 32) {
             const int J = cell_atoms[cell_start[c] + q];
-            double dx = R[3 * J] / kBohrA - xi, dy = R[3 * J + 1] / kBohrA - yi, dz = R[3 * J + 2] / kBohrA - zi;
-            dx -= g.box_b[0] * rint(dx / g.box_b[0]);
-            dy -= g.box_b[1] * rint(dy / g.box_b[1]);
-            dz -= g.box_b[2] * rint(dz / g.box_b[2]);
+            T dx, dy, dz;
+            rel(J, dx, dy, dz);
             visit(J, dx, dy, dz);
           }
         }
   }
-  if (MODE == 0) out[I] = acc;
-  else {
-    out[3 * I] = gx;
-    out[3 * I + 1] = gy;
-    out[3 * I + 2] = gz;
+  if (MODE == 0) {
+    acc = warp_sum(acc);
+    if (lane == 0) out[I] = acc;
+  } else {
+    gx = warp_sum(gx);
+    gy = warp_sum(gy);
+    gz = warp_sum(gz);
+    if (lane == 0) {
+      out[3 * I] = gx;
+      out[3 * I + 1] = gy;
+      out[3 * I + 2] = gz;
+    }
   }
+}
+
+__global__ void chunk_reduce_kernel(const double* part, int nchunk, long long len, double* out) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= len) return;
+  double s = 0.0;
+  for (int c = 0; c < nchunk; ++c) s += part[c * len + t];
+  out[t] = s;
 }
 
 __global__ void ewald_cell_assign(const double* R, int N, EwaldGeom g, int* cell_of, int* cell_count) {
@@ -328,10 +351,10 @@ Ewald::~Ewald() { release(); }
 void Ewald::release() {
   for (void* p : {(void*)rows_d, (void*)wk_d, (void*)tab, (void*)part, (void*)ws, (void*)real_buf, (void*)recip_buf,
                   (void*)cell_of, (void*)cell_count, (void*)cell_start, (void*)cell_fill, (void*)cell_atoms,
-                  (void*)scal})
+                  (void*)scal, (void*)rpart})
     if (p) cudaFree(p);
   rows_d = nullptr; wk_d = nullptr; tab = nullptr; part = nullptr; ws = nullptr; real_buf = nullptr;
-  recip_buf = nullptr; cell_of = cell_count = cell_start = cell_fill = cell_atoms = nullptr; scal = nullptr;
+  recip_buf = nullptr; rpart = nullptr; cell_of = cell_count = cell_start = cell_fill = cell_atoms = nullptr; scal = nullptr;
   N_ = 0;
 }
 
@@ -402,6 +425,7 @@ cudaError_t Ewald::setup(int N, const double box_A[3], const double hubbard_u[3]
   if ((e = cudaMalloc(&ws, csz * 2 * (size_t)nk_))) return e;
   if ((e = cudaMalloc(&real_buf, sizeof(double) * 3 * N))) return e;
   if ((e = cudaMalloc(&recip_buf, sizeof(double) * 3 * N))) return e;
+  if ((e = cudaMalloc(&rpart, sizeof(double) * 3 * (size_t)N * kRowChunks))) return e;
   if ((e = cudaMalloc(&scal, sizeof(double) * 4))) return e;
   const int ncell = g.nc[0] * g.nc[1] * g.nc[2];
   if ((e = cudaMalloc(&cell_of, sizeof(int) * N))) return e;
@@ -459,20 +483,22 @@ cudaError_t Ewald::potential(const double* b, double* V, cudaStream_t s) {
   const int W = 2 * m3max_ + 1;
   if (fp64_) {
     run_sf<double>(*this, b, nullptr, 1, s);
-    real_space_kernel<double, 0><<<nb, TB, 0, s>>>(dR_, dspecies_, N_, g, cell_start, cell_count, cell_atoms, cell_of,
-                                                   nullptr, b, real_buf);
+    real_space_kernel<double, 0><<<(32 * N_ + 127) / 128, 128, 0, s>>>(dR_, dspecies_, N_, g, cell_start, cell_count,
+                                                                      cell_atoms, cell_of, nullptr, b, real_buf);
     const int tpb = 64;
-    recip_atom_kernel<double, 0><<<(N_ + tpb - 1) / tpb, tpb, sizeof(double2) * tpb * W, s>>>(
+    recip_atom_kernel<double, 0><<<dim3((N_ + tpb - 1) / tpb, kRowChunks), tpb, sizeof(double2) * tpb * W, s>>>(
         rows_d, nrows_, reinterpret_cast<const double2*>(tab), reinterpret_cast<const double2*>(ws), nk_, N_,
-        g.nmax_all, m3max_, g, nullptr, nullptr, recip_buf);
+        g.nmax_all, m3max_, g, nullptr, nullptr, rpart);
+    chunk_reduce_kernel<<<(N_ + 255) / 256, 256, 0, s>>>(rpart, kRowChunks, N_, recip_buf);
   } else {
     run_sf<float>(*this, b, nullptr, 1, s);
-    real_space_kernel<float, 0><<<nb, TB, 0, s>>>(dR_, dspecies_, N_, g, cell_start, cell_count, cell_atoms, cell_of,
-                                                  nullptr, b, real_buf);
+    real_space_kernel<float, 0><<<(32 * N_ + 127) / 128, 128, 0, s>>>(dR_, dspecies_, N_, g, cell_start, cell_count,
+                                                                     cell_atoms, cell_of, nullptr, b, real_buf);
     const int tpb = 128;
-    recip_atom_kernel<float, 0><<<(N_ + tpb - 1) / tpb, tpb, sizeof(float2) * tpb * W, s>>>(
+    recip_atom_kernel<float, 0><<<dim3((N_ + tpb - 1) / tpb, kRowChunks), tpb, sizeof(float2) * tpb * W, s>>>(
         rows_d, nrows_, reinterpret_cast<const float2*>(tab), reinterpret_cast<const float2*>(ws), nk_, N_,
-        g.nmax_all, m3max_, g, nullptr, nullptr, recip_buf);
+        g.nmax_all, m3max_, g, nullptr, nullptr, rpart);
+    chunk_reduce_kernel<<<(N_ + 255) / 256, 256, 0, s>>>(rpart, kRowChunks, N_, recip_buf);
   }
   sum_kernel<<<1, 1024, 0, s>>>(b, N_, scal);
   combine_pot_kernel<<<nb, TB, 0, s>>>(real_buf, recip_buf, b, dspecies_, g, scal, V, N_);
@@ -485,20 +511,22 @@ cudaError_t Ewald::gradient(const double* a, const double* b, double* G, cudaStr
   // vector 0 = b (S_b), vector 1 = a (S_a)
   if (fp64_) {
     run_sf<double>(*this, b, a, 2, s);
-    real_space_kernel<double, 1><<<nb, TB, 0, s>>>(dR_, dspecies_, N_, g, cell_start, cell_count, cell_atoms, cell_of,
-                                                   a, b, real_buf);
+    real_space_kernel<double, 1><<<(32 * N_ + 127) / 128, 128, 0, s>>>(dR_, dspecies_, N_, g, cell_start, cell_count,
+                                                                      cell_atoms, cell_of, a, b, real_buf);
     const int tpb = 64;
-    recip_atom_kernel<double, 1><<<(N_ + tpb - 1) / tpb, tpb, sizeof(double2) * tpb * W, s>>>(
+    recip_atom_kernel<double, 1><<<dim3((N_ + tpb - 1) / tpb, kRowChunks), tpb, sizeof(double2) * tpb * W, s>>>(
         rows_d, nrows_, reinterpret_cast<const double2*>(tab), reinterpret_cast<const double2*>(ws), nk_, N_,
-        g.nmax_all, m3max_, g, a, b, recip_buf);
+        g.nmax_all, m3max_, g, a, b, rpart);
+    chunk_reduce_kernel<<<(3 * N_ + 255) / 256, 256, 0, s>>>(rpart, kRowChunks, 3LL * N_, recip_buf);
   } else {
     run_sf<float>(*this, b, a, 2, s);
-    real_space_kernel<float, 1><<<nb, TB, 0, s>>>(dR_, dspecies_, N_, g, cell_start, cell_count, cell_atoms, cell_of,
-                                                  a, b, real_buf);
+    real_space_kernel<float, 1><<<(32 * N_ + 127) / 128, 128, 0, s>>>(dR_, dspecies_, N_, g, cell_start, cell_count,
+                                                                     cell_atoms, cell_of, a, b, real_buf);
     const int tpb = 128;
-    recip_atom_kernel<float, 1><<<(N_ + tpb - 1) / tpb, tpb, sizeof(float2) * tpb * W, s>>>(
+    recip_atom_kernel<float, 1><<<dim3((N_ + tpb - 1) / tpb, kRowChunks), tpb, sizeof(float2) * tpb * W, s>>>(
         rows_d, nrows_, reinterpret_cast<const float2*>(tab), reinterpret_cast<const float2*>(ws), nk_, N_,
-        g.nmax_all, m3max_, g, a, b, recip_buf);
+        g.nmax_all, m3max_, g, a, b, rpart);
+    chunk_reduce_kernel<<<(3 * N_ + 255) / 256, 256, 0, s>>>(rpart, kRowChunks, 3LL * N_, recip_buf);
   }
   combine_grad_kernel<<<(3 * N_ + 255) / 256, 256, 0, s>>>(real_buf, recip_buf, G, N_, 1.0 / kBohrA);
   return cudaGetLastError();

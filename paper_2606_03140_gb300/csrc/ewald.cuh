@@ -25,6 +25,7 @@ struct KRow {           // reciprocal vectors with fixed (m1, m2), m3 in [m3lo, 
 
 struct Ewald {
   static constexpr int kChunk = 1024;
+  static constexpr int kRowChunks = 24;    // k-row chunks of the per-atom reciprocal sums
   EwaldGeom g{};
   int N_ = 0;
   bool fp64_ = true;
@@ -37,6 +38,7 @@ struct Ewald {
   void* ws = nullptr;        // w(k) S(k)
   double* real_buf = nullptr;
   double* recip_buf = nullptr;
+  double* rpart = nullptr;   // per-row-chunk partial sums
   double* scal = nullptr;
   int *cell_of = nullptr, *cell_count = nullptr, *cell_start = nullptr, *cell_fill = nullptr, *cell_atoms = nullptr;
   const double* dR_ = nullptr;

@@ -210,16 +210,18 @@ __global__ void gather_kernel(const ModelDev m, const long long* sub_ptr, const 
   }
 }
 
-// Collected observables for every core atom; one thread per core atom.
+// Collected observables, one warp per core atom (lanes split its neighbour list; sums are
+// combined by a fixed shuffle tree, the reaction on B by FP64 atomics).
 template <typename T>
 __global__ void observables_kernel(const ModelDev m, const double* R, const int* species, SkGeom g,
                                    const long long* sub_ptr, const int* sub_atoms, const int* orb_off,
                                    const int* core_list, const int* core_sub, const int* core_local, int n_core_total,
                                    const long long* pptr, const int* pcol, const T* h0b, const T* sb, const int* loc,
                                    int N, const double* V, const float* Dc32, const double* Dc64, const float* Wc32,
-                                   const double* Wc64, const long long* dc_off, const long long* wc_off, const int* n_pad, double* pop,
-                                   double* eband, double* dU, int with_forces) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+                                   const double* Wc64, const long long* dc_off, const long long* wc_off, const int* n_pad,
+                                   double* pop, double* eband, double* dU, int with_forces) {
+  const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (t >= n_core_total) return;
   const int A = core_list[t], i = core_sub[t], a = core_local[t];
   const long long qa = sub_ptr[i] + a;
@@ -238,15 +240,15 @@ __global__ void observables_kernel(const ModelDev m, const double* R, const int*
   const int* L = loc + (long long)i * N;
   double p_acc = 0.0, e_acc = 0.0;
   double fa[3] = {0.0, 0.0, 0.0};
-  // on-site block
-  for (int u = 0; u < na; ++u) {
-    const double d = Dv(oa + u, oa + u);
-    p_acc += d;
-    e_acc += d * (u == 0 ? m.eps_s[sa] : m.eps_p[sa]);
-  }
+  if (lane == 0)
+    for (int u = 0; u < na; ++u) {      // on-site block
+      const double d = Dv(oa + u, oa + u);
+      p_acc += d;
+      e_acc += d * (u == 0 ? m.eps_s[sa] : m.eps_p[sa]);
+    }
   const double va = V[A];
   const double roff2 = m.r_off * m.r_off;
-  for (long long p = pptr[A]; p < pptr[A + 1]; ++p) {
+  for (long long p = pptr[A] + lane; p < pptr[A + 1]; p += 32) {
     const int B = pcol[p];
     const int b = L[B];
     if (b < 0) continue;
@@ -257,7 +259,7 @@ __global__ void observables_kernel(const ModelDev m, const double* R, const int*
       for (int v = 0; v < nb; ++v) {
         const double d = Dv(oa + u, ob + v);
         Dm[u][v] = (T)d;
-        Wm[u][v] = (T)Wv(oa + u, ob + v);
+        if (with_forces) Wm[u][v] = (T)Wv(oa + u, ob + v);
         p_acc += d * (double)sb[p * 16 + u * 4 + v];
         e_acc += d * (double)h0b[p * 16 + u * 4 + v];
       }
@@ -290,11 +292,16 @@ __global__ void observables_kernel(const ModelDev m, const double* R, const int*
       atomicAdd(&dU[3 * B + c], gab[c]);
     }
   }
-  pop[A] = p_acc;
-  eband[A] = e_acc;
+  p_acc = warp_sum(p_acc);
+  e_acc = warp_sum(e_acc);
   if (with_forces)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) atomicAdd(&dU[3 * A + c], fa[c]);
+    for (int c = 0; c < 3; ++c) fa[c] = warp_sum(fa[c]);
+  if (lane == 0) {
+    pop[A] = p_acc;
+    eband[A] = e_acc;
+    if (with_forces)
+      for (int c = 0; c < 3; ++c) atomicAdd(&dU[3 * A + c], fa[c]);
+  }
 }
 
 // Atom-condensed density graph rows: for core atom A, G^D_AB = max |D_AB| over all subgraph atoms B.
@@ -401,7 +408,7 @@ void launch_observables(const ModelDev& m, const double* R, const int* species, 
                         const void* Dc, const void* Wc, const long long* dc_off, const long long* wc_off,
                         const int* n_pad, double* pop, double* eband, double* dU, int with_forces, bool f64,
                         cudaStream_t s) {
-  const int TB = 64, nb = (n_core_total + TB - 1) / TB;
+  const int TB = 128, nb = (int)((32LL * n_core_total + TB - 1) / TB);
   if (f64)
     observables_kernel<double><<<nb, TB, 0, s>>>(m, R, species, g, sub_ptr, sub_atoms, orb_off, core_list, core_sub,
                                                  core_local, n_core_total, pptr, pcol, (const double*)h0b,

@@ -72,6 +72,7 @@ def _load():
         "sedacs_xlbomd_step": (I32, [P, P, P, I32, D, P, P]),
         "sedacs_phase_times": (I32, [P, P, P]),
         "sedacs_reset_counters": (I32, [P]),
+        "sedacs_kernel_stats": (I32, [P, I32, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -88,6 +89,7 @@ EXPORTED = (
     "sedacs_energy", "sedacs_forces", "sedacs_density_graph_size", "sedacs_density_graph_get",
     "sedacs_subgraph_matrix", "sedacs_charge_response", "sedacs_kernel_apply", "sedacs_scc_step",
     "sedacs_xlbomd_init", "sedacs_xlbomd_step", "sedacs_phase_times", "sedacs_reset_counters",
+    "sedacs_kernel_stats",
 )
 
 
@@ -293,3 +295,12 @@ def sedacs_phase_times(ctx):
 
 def sedacs_reset_counters(ctx):
     _check(ctx, _lib.sedacs_reset_counters(ctx))
+
+
+def sedacs_kernel_stats(ctx, on: bool = True):
+    """(SP2 kernel ms, launches, algorithmic multiply-add pairs) since the last reset."""
+    ms = C.c_double()
+    nl = C.c_int64()
+    fl = C.c_double()
+    _check(ctx, _lib.sedacs_kernel_stats(ctx, 1 if on else 0, C.byref(ms), C.byref(nl), C.byref(fl)))
+    return ms.value, nl.value, fl.value
