@@ -95,6 +95,10 @@ sedacs_status sedacs_create(int32_t n_atoms, const int32_t* species, const doubl
 void sedacs_destroy(sedacs_ctx* ctx);
 const char* sedacs_last_error(const sedacs_ctx* ctx);
 
+/* Replace the run parameters of a context (kernel, tolerances, graph cutoff, ...);
+ * precision, core_size and ewald_tol must keep their creation values. */
+sedacs_status sedacs_set_params(sedacs_ctx* ctx, const sedacs_params* params);
+
 /* Device I/O: on != 0 makes every array argument a device pointer used on `stream`
  * (a cudaStream_t, may be 0 for the legacy default stream).  on = 0 restores host I/O. */
 sedacs_status sedacs_set_device_io(sedacs_ctx* ctx, int32_t on, void* stream);
@@ -132,8 +136,8 @@ sedacs_status sedacs_coulomb_potential(sedacs_ctx* ctx, const double* R, const d
  * graph and subgraphs.  Per subgraph: gather h = H0 + 1/2 (S V + V S) and s, Z = s^-1/2
  * (Newton-Schulz), h~ = Z h Z, the mu-branch SP2 recursion for the T -> 0 Fermi operator,
  * core rows D_c = 2 Z_c X Z and W_c = 2 Z_c X h~ Z; then Mulliken charges, band energy and
- * the density graph.  mu: in = chemical potential (Hartree) or NaN to place it at the middle
- * of the collected gap; out = the value used.  q [N] out, e_band out (Hartree),
+ * the density graph.  mu: in = chemical potential (Hartree), used as given, or NaN to place
+ * it at the middle of the collected gap; out = the value used.  q [N] out, e_band out (Hartree),
  * sp2_iters [n_parts] out (nullable). */
 sedacs_status sedacs_subgraph_density(sedacs_ctx* ctx, const double* R, const double* n, double* mu, double* q,
                                       double* e_band, int32_t* sp2_iters);

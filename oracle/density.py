@@ -164,16 +164,28 @@ def solve_mu_bisection(eps_list, w_list, n_e: float, beta: float) -> float:
     return mid
 
 
-def solve_mu(eps_list, w_list, n_e: float, kappa: float = 0.5) -> tuple[float, float, float]:
+def count_window(n_e: float) -> float:
+    """Half-width kappa of the electron-count window around N_e used to locate the gap edges.
+
+    The graph truncation leaves the collected count at mid-gap off N_e by an amount that
+    grows with the system (about 2.5e-5 e per atom in the water boxes); kappa = 1/2 + 1e-4 N_e
+    keeps that excess inside the window while staying far below the weight of a band."""
+    return 0.5 + 1e-4 * n_e
+
+
+def solve_mu(eps_list, w_list, n_e: float, kappa: float | None = None) -> tuple[float, float, float]:
     """Global chemical potential at the middle of the collected gap (T -> 0 reading of Eq. 2).
 
     The T -> 0 count N0(mu) = 2 sum_ik w_ik theta(mu - eps_ik) is a staircase in mu.
     The highest occupied level eps_H is the state whose inclusion first brings the
     count to >= N_e - kappa; the lowest unoccupied level eps_L is the first state whose
-    inclusion takes it above N_e + kappa.  mu = (eps_H + eps_L) / 2.  States between
-    them carry less than 2 kappa electrons in total (in-gap halo states).
+    inclusion takes it above N_e + kappa (kappa = ``count_window(N_e)``).
+    mu = (eps_H + eps_L) / 2.  States between them carry less than 2 kappa electrons in
+    total (in-gap halo states).
     Returns (mu, eps_H, eps_L).
     """
+    if kappa is None:
+        kappa = count_window(n_e)
     e = np.concatenate([np.asarray(x, dtype=np.float64) for x in eps_list])
     w = np.concatenate([np.asarray(x, dtype=np.float64) for x in w_list])
     order = np.argsort(e, kind="stable")

@@ -5,8 +5,10 @@
 
 namespace sedacs {
 
-// One matrix problem of a batched GEMM  C = alpha * A * B^T + beta * I  (B^T: B is read by
-// rows, so for the symmetric operands of the method B^T = B).  Offsets are bytes from
+// One matrix problem of a batched GEMM
+//   C = alpha * A * B^T + beta * I + g1 * C1 + g2 * C2      (generic mode)
+// (B^T: B is read by rows, so for the symmetric operands of the method B^T = B; C1, C2 are
+// masters added in the epilogue, so a product with I + E is formed as C + C E exactly).  Offsets are bytes from
 // the arena base.  For the tensor-core path A and B are blocked split-bf16 planes and the
 // master output is fp32 row-major; for the FP64 path every matrix is fp64 row-major.
 struct GemmMat {
@@ -18,14 +20,16 @@ struct GemmMat {
   long long x_off;               // SP2: master of the current iterate
   long long buf_stride;          // SP2 ping/pong distance (bytes) for a, b, x and the outputs
   long long tr_off;              // SP2: trace partial slots (doubles from the slot base)
-  long long c_off;               // response mode: master of X dX (added to the product)
+  long long c_off;               // response mode: master of X dX; generic mode: C1 (-1: none)
+  long long c2_off;              // generic mode: C2 (-1: none)
   int n_pad;                     // row stride of every operand (multiple of 128)
   int m_real;                    // valid output rows
   int n_real;                    // valid output columns
   int k_real;                    // valid inner dimension
   int b_from_sp2;                // generic mode: B taken from the SP2 result buffer
   int a_from_sp2;
-  int pad0, pad1;
+  int c_from_sp2;                // generic mode: C1 taken from the SP2 result buffer
+  int pad1;
 };
 
 struct GemmWork {
@@ -60,6 +64,7 @@ struct GemmParams {
   int mode;
   int nsplit_out;     // tensor path: number of bf16 planes written (0..3)
   float alpha, beta;
+  float g1, g2;
 };
 
 // Host launchers (dense.cu)

@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const GemmParams p) {
     if (!st.active) return;
     cur = st.cur;
     branch_sq = st.y >= 0.5;
-  } else if (m.b_from_sp2 || m.a_from_sp2) {
+  } else if (m.b_from_sp2 || m.a_from_sp2 || m.c_from_sp2) {
     cur = p.sp2[w.mat].cur;
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -85,8 +85,13 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const GemmParams p) {
     mbar_init(accb, 1);
     fence_mbar_init();
   }
+  // TMEM: the leading hi*hi products go to three accumulators by k-block (columns [0,384)),
+  // the split-correction products to a fourth ([384,512)): each accumulator takes few adds
+  // and the small corrections are not summed against the large partial sums; the epilogue
+  // adds the four in FP32.
+  constexpr uint32_t kTmemCols = NSPLIT > 1 ? 512 : 128;
   if (warp == 0) {
-    tmem_alloc(tmem_slot, 128);
+    tmem_alloc(tmem_slot, kTmemCols);
     tmem_relinquish();
   }
   tc_fence_before();
@@ -134,7 +139,14 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const GemmParams p) {
           prod_planes(pr, pa, pb);
           const uint64_t ad = smem_desc_sw128(st + pa * kBlkBytes + kk * 32);
           const uint64_t bd = smem_desc_sw128(st + (NSPLIT + pb) * kBlkBytes + kk * 32);
-          tc_mma_bf16(tmem, ad, bd, idesc, (kb | kk | pr) != 0 ? 1u : 0u);
+          const int hsel = kb % 3;
+          const uint32_t acc_col = (NSPLIT == 1) ? 0u : (pr == 0 ? 128u * hsel : 384u);
+          // the first product into each accumulator starts it
+          uint32_t accum;
+          if (NSPLIT == 1) accum = (kb | kk) != 0 ? 1u : 0u;
+          else if (pr == 0) accum = (kb >= 3 || kk != 0) ? 1u : 0u;
+          else accum = (pr == 1 && (kb | kk) == 0) ? 0u : 1u;
+          tc_mma_bf16(tmem + acc_col, ad, bd, idesc, accum);
         }
       }
       tc_commit(&empty[s]);
@@ -159,6 +171,25 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const GemmParams p) {
   for (int c = 0; c < 4; ++c) {
     float v[32];
     tmem_ld32(t_row + c * 32, v);
+    if (NSPLIT > 1) {
+      // accumulators 1, 2 hold hi*hi of k-blocks 1, 2 mod 3 (empty when fewer k-blocks)
+      if (kb_end > 1) {
+        float v2[32];
+        tmem_ld32(t_row + 128 + c * 32, v2);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] += v2[j];
+      }
+      if (kb_end > 2) {
+        float v2[32];
+        tmem_ld32(t_row + 256 + c * 32, v2);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] += v2[j];
+      }
+      float v3[32];
+      tmem_ld32(t_row + 384 + c * 32, v3);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) v[j] += v3[j];
+    }
     const int col0 = w.tn * 128 + c * 32;
     if (p.mode == kModeRsp) {
       const float4* sx = reinterpret_cast<const float4*>(xm + (long long)row * m.n_pad + col0);
@@ -195,11 +226,31 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const GemmParams p) {
         v[j] = ok_ij ? nv : 0.f;
       }
     } else {
+      float c1[32], c2[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) { c1[j] = 0.f; c2[j] = 0.f; }
+      if (m.c_off >= 0) {
+        const float4* s1 = reinterpret_cast<const float4*>(
+            p.arena + m.c_off + (m.c_from_sp2 ? cur * m.buf_stride : 0) + ((long long)row * m.n_pad + col0) * 4);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const float4 t = s1[q];
+          c1[4 * q] = t.x; c1[4 * q + 1] = t.y; c1[4 * q + 2] = t.z; c1[4 * q + 3] = t.w;
+        }
+      }
+      if (m.c2_off >= 0) {
+        const float4* s2 = reinterpret_cast<const float4*>(p.arena + m.c2_off + ((long long)row * m.n_pad + col0) * 4);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const float4 t = s2[q];
+          c2[4 * q] = t.x; c2[4 * q + 1] = t.y; c2[4 * q + 2] = t.z; c2[4 * q + 3] = t.w;
+        }
+      }
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
         const int col = col0 + j;
         const bool ok_ij = row_ok && col < m.n_real;
-        v[j] = ok_ij ? (p.alpha * v[j] + (row == col ? p.beta : 0.f)) : 0.f;
+        v[j] = ok_ij ? (p.alpha * v[j] + (row == col ? p.beta : 0.f) + p.g1 * c1[j] + p.g2 * c2[j]) : 0.f;
       }
     }
     if (outm) {
@@ -229,7 +280,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const GemmParams p) {
   }
   if (warp == 0) {
     tc_fence_after();
-    tmem_dealloc(tmem, 128);
+    tmem_dealloc(tmem, kTmemCols);
   }
   if (!ok) atomicOr(p.err, kErrTimeout);
 }
@@ -250,7 +301,7 @@ __global__ void __launch_bounds__(256) f64_gemm_kernel(const GemmParams p) {
     if (!st.active) return;
     cur = st.cur;
     branch_sq = st.y >= 0.5;
-  } else if (m.b_from_sp2 || m.a_from_sp2) {
+  } else if (m.b_from_sp2 || m.a_from_sp2 || m.c_from_sp2) {
     cur = p.sp2[w.mat].cur;
   }
   const long long in_shift = stepping ? cur * m.buf_stride : 0;
@@ -305,6 +356,10 @@ __global__ void __launch_bounds__(256) f64_gemm_kernel(const GemmParams p) {
         v = branch_sq ? sum : 2.0 * x - sum;
       } else {
         v = (double)p.alpha * acc[i][j] + (row == col ? (double)p.beta : 0.0);
+        if (m.c_off >= 0)
+          v += (double)p.g1 * reinterpret_cast<const double*>(
+                   p.arena + m.c_off + (m.c_from_sp2 ? cur * m.buf_stride : 0))[(long long)row * ld + col];
+        if (m.c2_off >= 0) v += (double)p.g2 * reinterpret_cast<const double*>(p.arena + m.c2_off)[(long long)row * ld + col];
       }
       if (outm) outm[(long long)row * ld + col] = ok ? v : 0.0;
     }

@@ -133,12 +133,13 @@ __global__ void fill_hist_kernel(double* hist, const double* n, int N) {
 }
 
 __global__ void matrix_to_f64_kernel(const uint8_t* arena, long long off, bool f64, int rows, int cols, int ld,
-                                     double* out) {
+                                     double diag, double* out) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= (long long)rows * cols) return;
   const int r = (int)(t / cols), c = (int)(t % cols);
-  out[t] = f64 ? reinterpret_cast<const double*>(arena + off)[(long long)r * ld + c]
-               : (double)reinterpret_cast<const float*>(arena + off)[(long long)r * ld + c];
+  out[t] = (f64 ? reinterpret_cast<const double*>(arena + off)[(long long)r * ld + c]
+                : (double)reinterpret_cast<const float*>(arena + off)[(long long)r * ld + c]) +
+           (r == c ? diag : 0.0);
 }
 
 }  // namespace
@@ -276,8 +277,10 @@ long long pptr_(const sedacs_ctx* ctx, int sl, int i, int copy = 0) {
   return S.base + copy * S.copy_stride + S.master_bytes + el * 2;
 }
 
+// C = alpha A B^T + beta I + g1 C1 + g2 C2 over every subgraph (slots a, b, out, c1, c2; -1: none).
 sedacs_status build_op(sedacs_ctx* ctx, int id, int a, int b, int out, int mode, float alpha, float beta,
-                       bool b_from_sp2, bool a_from_sp2 = false) {
+                       bool b_from_sp2, bool a_from_sp2 = false, int c1 = -1, float g1 = 0.f, int c2 = -1,
+                       float g2 = 0.f, bool c_from_sp2 = false) {
   const Layout& L = ctx->lay;
   std::vector<GemmMat> mats(L.n_sub);
   std::vector<GemmWork> work;
@@ -292,7 +295,9 @@ sedacs_status build_op(sedacs_ctx* ctx, int id, int a, int b, int out, int mode,
     m.outp_off = ctx->f64 ? -1 : pptr_(ctx, out, i);
     m.outp_plane = ctx->slot[out].plane_stride;
     m.x_off = (mode == kModeRsp) ? mptr(ctx, kR2, i) : mptr(ctx, kX, i);
-    m.c_off = mptr(ctx, kR1, i);
+    m.c_off = (mode == kModeRsp) ? mptr(ctx, kR1, i) : (c1 >= 0 ? mptr(ctx, c1, i) : -1);
+    m.c2_off = (c2 >= 0) ? mptr(ctx, c2, i) : -1;
+    m.c_from_sp2 = c_from_sp2 ? 1 : 0;
     m.buf_stride = ctx->slot[kX].copy_stride;
     m.tr_off = L.tr_off[i];
     m.n_pad = L.n_pad[i];
@@ -322,6 +327,8 @@ sedacs_status build_op(sedacs_ctx* ctx, int id, int a, int b, int out, int mode,
   op.n_work = (int)work.size();
   op.alpha = alpha;
   op.beta = beta;
+  op.g1 = g1;
+  op.g2 = g2;
   op.mode = mode;
   CUCHK(cudaStreamSynchronize(ctx->stream));
   return SEDACS_OK;
@@ -340,6 +347,8 @@ void run_op(sedacs_ctx* ctx, int id, int nsplit_in, int nsplit_out) {
   p.nsplit_out = nsplit_out;
   p.alpha = op.alpha;
   p.beta = op.beta;
+  p.g1 = op.g1;
+  p.g2 = op.g2;
   if (ctx->f64) launch_gemm_f64(p, op.n_work, ctx->stream);
   else launch_gemm_tc(p, op.n_work, nsplit_in, ctx->stream);
   ctx->launches += op.n_work > 0 ? 1 : 0;
@@ -519,36 +528,40 @@ sedacs_status rebuild_layout(sedacs_ctx* ctx) {
   // GEMM tables
   const bool f = ctx->f64;
   (void)f;
-  STCHK(build_op(ctx, OP_NS_Y1, kS, kT, kY1, kModeGeneric, 1.f, 0.f, false));
-  STCHK(build_op(ctx, OP_NS_T0, kZ0, kY0, kT, kModeGeneric, -0.5f, 1.5f, false));
-  STCHK(build_op(ctx, OP_NS_T1, kZ1, kY1, kT, kModeGeneric, -0.5f, 1.5f, false));
-  STCHK(build_op(ctx, OP_NS_Y0, kY0, kT, kY1, kModeGeneric, 1.f, 0.f, false));
-  STCHK(build_op(ctx, OP_NS_Y1b, kY1, kT, kY0, kModeGeneric, 1.f, 0.f, false));
-  STCHK(build_op(ctx, OP_NS_Z0, kT, kZ0, kZ1, kModeGeneric, 1.f, 0.f, false));
-  STCHK(build_op(ctx, OP_NS_Z1, kT, kZ1, kZ0, kModeGeneric, 1.f, 0.f, false));
-  STCHK(build_op(ctx, OP_P0, kZ0, kH, kP, kModeGeneric, 1.f, 0.f, false));
-  STCHK(build_op(ctx, OP_P1, kZ1, kH, kP, kModeGeneric, 1.f, 0.f, false));
-  STCHK(build_op(ctx, OP_HT0, kP, kZ0, kHt, kModeGeneric, 1.f, 0.f, false));
-  STCHK(build_op(ctx, OP_HT1, kP, kZ1, kHt, kModeGeneric, 1.f, 0.f, false));
+  // S^-1/2 in deviation form: Y = I + E_y (kY*), Z = I + E_z (kZ*), T = I + E_t (kT);
+  // only products of the small deviations go through the tensor cores.
+  STCHK(build_op(ctx, OP_NS_Y1, kY0, kT, kY1, kModeGeneric, 1.f, 0.f, false, false, kY0, 1.f, kT, 1.f));
+  STCHK(build_op(ctx, OP_NS_T0, kZ0, kY0, kT, kModeGeneric, -0.5f, 0.f, false, false, kZ0, -0.5f, kY0, -0.5f));
+  STCHK(build_op(ctx, OP_NS_T1, kZ1, kY1, kT, kModeGeneric, -0.5f, 0.f, false, false, kZ1, -0.5f, kY1, -0.5f));
+  STCHK(build_op(ctx, OP_NS_Y0, kY0, kT, kY1, kModeGeneric, 1.f, 0.f, false, false, kY0, 1.f, kT, 1.f));
+  STCHK(build_op(ctx, OP_NS_Y1b, kY1, kT, kY0, kModeGeneric, 1.f, 0.f, false, false, kY1, 1.f, kT, 1.f));
+  STCHK(build_op(ctx, OP_NS_Z0, kT, kZ0, kZ1, kModeGeneric, 1.f, 0.f, false, false, kT, 1.f, kZ0, 1.f));
+  STCHK(build_op(ctx, OP_NS_Z1, kT, kZ1, kZ0, kModeGeneric, 1.f, 0.f, false, false, kT, 1.f, kZ1, 1.f));
+  // h~ = Z h Z = P + P E_z with P = h + E_z h
+  STCHK(build_op(ctx, OP_P0, kZ0, kH, kP, kModeGeneric, 1.f, 0.f, false, false, kH, 1.f));
+  STCHK(build_op(ctx, OP_P1, kZ1, kH, kP, kModeGeneric, 1.f, 0.f, false, false, kH, 1.f));
+  STCHK(build_op(ctx, OP_HT0, kP, kZ0, kHt, kModeGeneric, 1.f, 0.f, false, false, kP, 1.f));
+  STCHK(build_op(ctx, OP_HT1, kP, kZ1, kHt, kModeGeneric, 1.f, 0.f, false, false, kP, 1.f));
   STCHK(build_op(ctx, OP_SP2, kX, kX, kX, kModeSp2, 1.f, 0.f, false));
-  STCHK(build_op(ctx, OP_T1_0, kZ0, kX, kT1, kModeGeneric, 1.f, 0.f, true));
-  STCHK(build_op(ctx, OP_T1_1, kZ1, kX, kT1, kModeGeneric, 1.f, 0.f, true));
-  STCHK(build_op(ctx, OP_DC0, kT1, kZ0, kDc, kModeGeneric, 2.f, 0.f, false));
-  STCHK(build_op(ctx, OP_DC1, kT1, kZ1, kDc, kModeGeneric, 2.f, 0.f, false));
+  // core rows: T1 = Z_c X = X_c + E_z,c X ; D_c = 2 T1 Z = 2 (T1 + T1 E_z); W_c = 2 (T1 h~) Z
+  STCHK(build_op(ctx, OP_T1_0, kZ0, kX, kT1, kModeGeneric, 1.f, 0.f, true, false, kX, 1.f, -1, 0.f, true));
+  STCHK(build_op(ctx, OP_T1_1, kZ1, kX, kT1, kModeGeneric, 1.f, 0.f, true, false, kX, 1.f, -1, 0.f, true));
+  STCHK(build_op(ctx, OP_DC0, kT1, kZ0, kDc, kModeGeneric, 2.f, 0.f, false, false, kT1, 2.f));
+  STCHK(build_op(ctx, OP_DC1, kT1, kZ1, kDc, kModeGeneric, 2.f, 0.f, false, false, kT1, 2.f));
   STCHK(build_op(ctx, OP_T2, kT1, kHt, kT2, kModeGeneric, 1.f, 0.f, false));
-  STCHK(build_op(ctx, OP_WC0, kT2, kZ0, kWc, kModeGeneric, 2.f, 0.f, false));
-  STCHK(build_op(ctx, OP_WC1, kT2, kZ1, kWc, kModeGeneric, 2.f, 0.f, false));
+  STCHK(build_op(ctx, OP_WC0, kT2, kZ0, kWc, kModeGeneric, 2.f, 0.f, false, false, kT2, 2.f));
+  STCHK(build_op(ctx, OP_WC1, kT2, kZ1, kWc, kModeGeneric, 2.f, 0.f, false, false, kT2, 2.f));
   // response tables
   STCHK(build_op(ctx, OP_RSP_A, kX, kR2, kR1, kModeGeneric, 1.f, 0.f, true, true));
   STCHK(build_op(ctx, OP_RSP_B, kR2, kX, kR2, kModeRsp, 1.f, 0.f, false));
-  STCHK(build_op(ctx, OP_DP0, kZ0, kdH, kP, kModeGeneric, 1.f, 0.f, false));
-  STCHK(build_op(ctx, OP_DP1, kZ1, kdH, kP, kModeGeneric, 1.f, 0.f, false));
-  STCHK(build_op(ctx, OP_DHT0, kP, kZ0, kdHt, kModeGeneric, 1.f, 0.f, false));
-  STCHK(build_op(ctx, OP_DHT1, kP, kZ1, kdHt, kModeGeneric, 1.f, 0.f, false));
-  STCHK(build_op(ctx, OP_DT1_0, kZ0, kR2, kdT1, kModeGeneric, 1.f, 0.f, true));
-  STCHK(build_op(ctx, OP_DT1_1, kZ1, kR2, kdT1, kModeGeneric, 1.f, 0.f, true));
-  STCHK(build_op(ctx, OP_DDC0, kdT1, kZ0, kdDc, kModeGeneric, 2.f, 0.f, false));
-  STCHK(build_op(ctx, OP_DDC1, kdT1, kZ1, kdDc, kModeGeneric, 2.f, 0.f, false));
+  STCHK(build_op(ctx, OP_DP0, kZ0, kdH, kP, kModeGeneric, 1.f, 0.f, false, false, kdH, 1.f));
+  STCHK(build_op(ctx, OP_DP1, kZ1, kdH, kP, kModeGeneric, 1.f, 0.f, false, false, kdH, 1.f));
+  STCHK(build_op(ctx, OP_DHT0, kP, kZ0, kdHt, kModeGeneric, 1.f, 0.f, false, false, kP, 1.f));
+  STCHK(build_op(ctx, OP_DHT1, kP, kZ1, kdHt, kModeGeneric, 1.f, 0.f, false, false, kP, 1.f));
+  STCHK(build_op(ctx, OP_DT1_0, kZ0, kR2, kdT1, kModeGeneric, 1.f, 0.f, true, false, kR2, 1.f, -1, 0.f, true));
+  STCHK(build_op(ctx, OP_DT1_1, kZ1, kR2, kdT1, kModeGeneric, 1.f, 0.f, true, false, kR2, 1.f, -1, 0.f, true));
+  STCHK(build_op(ctx, OP_DDC0, kdT1, kZ0, kdDc, kModeGeneric, 2.f, 0.f, false, false, kdT1, 2.f));
+  STCHK(build_op(ctx, OP_DDC1, kdT1, kZ1, kdDc, kModeGeneric, 2.f, 0.f, false, false, kdT1, 2.f));
   ctx->have_subs = true;
   ctx->z_valid = false;
   ctx->sp2_iters_h.assign(P, 0);
@@ -576,25 +589,32 @@ void gather_hs(sedacs_ctx* ctx) {
 }
 
 // Z = s^-1/2 by the coupled Newton-Schulz iteration Y0 = s, Z0 = I, T = (3I - Z Y)/2,
-// Y <- Y T, Z <- T Z (quadratic convergence for ||I - s|| < 1).
+// Y <- Y T, Z <- T Z (quadratic convergence for ||I - s|| < 1), carried in deviation form
+// Y = I + E_y, Z = I + E_z, T = I + E_t:
+//   E_t = -(E_z + E_y + E_z E_y)/2,  E_y <- E_y + E_t + E_y E_t,  E_z <- E_t + E_z + E_t E_z.
+// The overlap of the model is close to I, so the deviations are small and the tensor-core
+// products carry a small absolute error.  The result Z = I + E_z is held as E_z.
 void compute_z(sedacs_ctx* ctx) {
   cudaStream_t s = ctx->stream;
   const Layout& L = ctx->lay;
   const int mr = max_rows(ctx);
   const int ns = ctx->nsplit_ns;
-  if (!ctx->f64) launch_split_planes(ctx->d_views[kS], L.n_sub, mr, ctx->arena, ns, false, s);
-  launch_affine(ctx->d_views[kS], ctx->d_views[kT], L.n_sub, mr, ctx->arena, -0.5, 1.5, ctx->f64, s);
-  if (!ctx->f64) launch_split_planes(ctx->d_views[kT], L.n_sub, mr, ctx->arena, ns, false, s);
-  run_op(ctx, OP_NS_Y1, ns, ns);                       // Y1 = s T0
-  launch_affine(ctx->d_views[kT], ctx->d_views[kZ1], L.n_sub, mr, ctx->arena, 1.0, 0.0, ctx->f64, s);   // Z1 = T0
+  launch_affine(ctx->d_views[kS], ctx->d_views[kY0], L.n_sub, mr, ctx->arena, 1.0, -1.0, ctx->f64, s);   // E_y0 = s - I
+  launch_affine(ctx->d_views[kY0], ctx->d_views[kT], L.n_sub, mr, ctx->arena, -0.5, 0.0, ctx->f64, s);   // E_t = -E_y0/2
+  if (!ctx->f64) {
+    launch_split_planes(ctx->d_views[kY0], L.n_sub, mr, ctx->arena, ns, false, s);
+    launch_split_planes(ctx->d_views[kT], L.n_sub, mr, ctx->arena, ns, false, s);
+  }
+  run_op(ctx, OP_NS_Y1, ns, ns);                       // E_y1
+  launch_affine(ctx->d_views[kT], ctx->d_views[kZ1], L.n_sub, mr, ctx->arena, 1.0, 0.0, ctx->f64, s);    // E_z1 = E_t
   if (!ctx->f64) launch_split_planes(ctx->d_views[kZ1], L.n_sub, mr, ctx->arena, ns, false, s);
-  ctx->launches += ctx->f64 ? 2 : 5;
+  ctx->launches += ctx->f64 ? 3 : 6;
   int c = 1;
   const int K = std::max(2, ctx->prm.ns_iters);
   for (int k = 2; k <= K; ++k) {
-    run_op(ctx, c == 0 ? OP_NS_T0 : OP_NS_T1, ns, ns);      // T = 1.5 I - 0.5 Z[c] Y[c]
-    if (k < K) run_op(ctx, c == 0 ? OP_NS_Y0 : OP_NS_Y1b, ns, ns);   // Y[1-c] = Y[c] T
-    run_op(ctx, c == 0 ? OP_NS_Z0 : OP_NS_Z1, ns, ns);      // Z[1-c] = T Z[c]
+    run_op(ctx, c == 0 ? OP_NS_T0 : OP_NS_T1, ns, ns);
+    if (k < K) run_op(ctx, c == 0 ? OP_NS_Y0 : OP_NS_Y1b, ns, ns);
+    run_op(ctx, c == 0 ? OP_NS_Z0 : OP_NS_Z1, ns, ns);
     c = 1 - c;
   }
   ctx->zc = c;
@@ -696,8 +716,13 @@ sedacs_status count_at(sedacs_ctx* ctx, double mu, int kmax, double* nel) {
   return observe(ctx, false, nel);
 }
 
-// mu at the middle of the collected gap: the smallest mu with N0 >= N_e - 1/2 (top of the
-// occupied levels) and the smallest mu with N0 > N_e + 1/2 (bottom of the empty ones).
+// Half-width of the electron-count window that locates the gap edges: the graph truncation
+// leaves the mid-gap count off N_e by an amount growing with the system (~2.5e-5 e/atom in
+// water), kept inside kappa = 1/2 + 1e-4 N_e.
+double count_window(double ne) { return 0.5 + 1e-4 * ne; }
+
+// mu at the middle of the collected gap: the smallest mu with N0 >= N_e - kappa (top of the
+// occupied levels) and the smallest mu with N0 > N_e + kappa (bottom of the empty ones).
 sedacs_status solve_mu(sedacs_ctx* ctx, double* mu_out) {
   double lo = 1e300, hi = -1e300;
   for (int i = 0; i < ctx->lay.n_sub; ++i) {
@@ -705,7 +730,7 @@ sedacs_status solve_mu(sedacs_ctx* ctx, double* mu_out) {
     lo = std::min(lo, ctx->bounds_h[2 * i]);
     hi = std::max(hi, ctx->bounds_h[2 * i + 1]);
   }
-  const double ne = ctx->n_electrons, kap = 0.5, delta = 1e-3;
+  const double ne = ctx->n_electrons, kap = count_window(ne), delta = 1e-3;
   const int kt = 40;
   double a = lo, b = hi, nel = 0.0;
   while (b - a > delta) {
@@ -726,7 +751,9 @@ sedacs_status solve_mu(sedacs_ctx* ctx, double* mu_out) {
   return SEDACS_OK;
 }
 
-sedacs_status density_core(sedacs_ctx* ctx, double* mu_io) {
+// allow_resolve: place mu again when the count leaves the window (internal SCC / MD loops,
+// or a caller that asked for mu = NaN); a mu given by the caller is used as given.
+sedacs_status density_core(sedacs_ctx* ctx, double* mu_io, bool allow_resolve = true) {
   if (!ctx->have_subs) { ctx->err = "no subgraphs: call sedacs_graph_build and sedacs_partition first"; return SEDACS_EINVAL; }
   cudaStream_t s = ctx->stream;
   STCHK(prepare_geometry(ctx));
@@ -752,7 +779,7 @@ sedacs_status density_core(sedacs_ctx* ctx, double* mu_io) {
   phase_begin(ctx, 0);
   back_transform(ctx, true);
   STCHK(observe(ctx, false, &nel));
-  if (std::fabs(nel - ctx->n_electrons) > 0.5) {
+  if (allow_resolve && std::fabs(nel - ctx->n_electrons) > count_window(ctx->n_electrons)) {
     // mu left the gap (the levels moved): place it again
     STCHK(solve_mu(ctx, &mu));
     STCHK(run_sp2(ctx, mu, ctx->prm.sp2_kmax));
@@ -1109,6 +1136,17 @@ void sedacs_destroy(sedacs_ctx* ctx) {
 
 const char* sedacs_last_error(const sedacs_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
+sedacs_status sedacs_set_params(sedacs_ctx* ctx, const sedacs_params* p) {
+  if (!ctx || !p) return SEDACS_EINVAL;
+  if (p->precision != ctx->prm.precision || p->core_size != ctx->prm.core_size || p->ewald_tol != ctx->prm.ewald_tol) {
+    ctx->err = "precision, core_size and ewald_tol are fixed at creation";
+    return SEDACS_EINVAL;
+  }
+  if (p->ns_iters != ctx->prm.ns_iters) ctx->z_valid = false;
+  ctx->prm = *p;
+  return SEDACS_OK;
+}
+
 sedacs_status sedacs_set_device_io(sedacs_ctx* ctx, int32_t on, void* stream) {
   if (!ctx) return SEDACS_EINVAL;
   ctx->dev_io = on != 0;
@@ -1241,7 +1279,7 @@ sedacs_status sedacs_subgraph_density(sedacs_ctx* ctx, const double* R, const do
   }
   STCHK(copy_in(ctx, ctx->d_n, n, ctx->N));
   double m = *mu;
-  STCHK(density_core(ctx, &m));
+  STCHK(density_core(ctx, &m, std::isnan(*mu)));
   *mu = m;
   STCHK(copy_out(ctx, q, ctx->d_q, sizeof(double) * ctx->N));
   if (e_band) *e_band = ctx->e_band;
@@ -1306,8 +1344,8 @@ sedacs_status sedacs_subgraph_matrix(sedacs_ctx* ctx, int32_t part, int32_t whic
   const long long off = mptr(ctx, sl, part);
   double* tmp = nullptr;
   CUCHK(cudaMalloc(&tmp, sizeof(double) * std::max(1, rows * nr)));
-  matrix_to_f64_kernel<<<nblk((long long)rows * nr, 256), 256, 0, ctx->stream>>>(ctx->arena, off, ctx->f64, rows, nr,
-                                                                                 ctx->lay.n_pad[part], tmp);
+  matrix_to_f64_kernel<<<nblk((long long)rows * nr, 256), 256, 0, ctx->stream>>>(
+      ctx->arena, off, ctx->f64, rows, nr, ctx->lay.n_pad[part], which == 2 ? 1.0 : 0.0, tmp);
   cudaError_t e = cudaMemcpyAsync(out, tmp, sizeof(double) * rows * nr, cudaMemcpyDefault, ctx->stream);
   cudaStreamSynchronize(ctx->stream);
   cudaFree(tmp);

@@ -36,7 +36,7 @@ struct GemmOp {
   GemmMat* mats_d = nullptr;
   GemmWork* work_d = nullptr;
   int n_work = 0;
-  float alpha = 1.f, beta = 0.f;
+  float alpha = 1.f, beta = 0.f, g1 = 0.f, g2 = 0.f;
   int mode = kModeGeneric;
 };
 

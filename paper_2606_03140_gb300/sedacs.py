@@ -73,6 +73,7 @@ def _load():
         "sedacs_phase_times": (I32, [P, P, P]),
         "sedacs_reset_counters": (I32, [P]),
         "sedacs_kernel_stats": (I32, [P, I32, P, P, P]),
+        "sedacs_set_params": (I32, [P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -89,7 +90,7 @@ EXPORTED = (
     "sedacs_energy", "sedacs_forces", "sedacs_density_graph_size", "sedacs_density_graph_get",
     "sedacs_subgraph_matrix", "sedacs_charge_response", "sedacs_kernel_apply", "sedacs_scc_step",
     "sedacs_xlbomd_init", "sedacs_xlbomd_step", "sedacs_phase_times", "sedacs_reset_counters",
-    "sedacs_kernel_stats",
+    "sedacs_kernel_stats", "sedacs_set_params",
 )
 
 
@@ -149,6 +150,10 @@ def sedacs_create(species, box, model, params) -> C.c_void_p:
 
 def sedacs_destroy(ctx):
     _lib.sedacs_destroy(ctx)
+
+
+def sedacs_set_params(ctx, params):
+    _check(ctx, _lib.sedacs_set_params(ctx, C.byref(params)))
 
 
 def sedacs_set_device_io(ctx, on: bool, stream: int = 0):
