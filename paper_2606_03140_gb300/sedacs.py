@@ -74,6 +74,7 @@ def _load():
         "sedacs_reset_counters": (I32, [P]),
         "sedacs_kernel_stats": (I32, [P, I32, P, P, P]),
         "sedacs_set_params": (I32, [P, P]),
+        "sedacs_graph_build_noalloc": (I32, [P, I32, P, D, P, P, I64, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -90,7 +91,7 @@ EXPORTED = (
     "sedacs_energy", "sedacs_forces", "sedacs_density_graph_size", "sedacs_density_graph_get",
     "sedacs_subgraph_matrix", "sedacs_charge_response", "sedacs_kernel_apply", "sedacs_scc_step",
     "sedacs_xlbomd_init", "sedacs_xlbomd_step", "sedacs_phase_times", "sedacs_reset_counters",
-    "sedacs_kernel_stats", "sedacs_set_params",
+    "sedacs_kernel_stats", "sedacs_set_params", "sedacs_graph_build_noalloc",
 )
 
 
@@ -309,3 +310,19 @@ def sedacs_kernel_stats(ctx, on: bool = True):
     fl = C.c_double()
     _check(ctx, _lib.sedacs_kernel_stats(ctx, 1 if on else 0, C.byref(ms), C.byref(nl), C.byref(fl)))
     return ms.value, nl.value, fl.value
+
+
+def sedacs_graph_build_noalloc(R_dev, box, r_graph: float, row_ptr_dev, col_dev, stream: int = 0) -> tuple[int, int]:
+    """Distance graph into caller-owned device tensors, without any device allocation.
+
+    R_dev float64 [N, 3], row_ptr_dev int64 [N+1], col_dev int32 [capacity] (torch CUDA tensors).
+    Returns (status, nnz); status SEDACS_ECAPACITY (8) means col_dev is too small for nnz edges.
+    """
+    bx = np.ascontiguousarray(box, dtype=np.float64)
+    nnz = C.c_int64()
+    st = _lib.sedacs_graph_build_noalloc(_ptr(R_dev), int(R_dev.shape[0]), _ptr(bx), float(r_graph),
+                                         _ptr(row_ptr_dev), _ptr(col_dev), int(col_dev.numel()), C.byref(nnz),
+                                         C.c_void_p(stream))
+    if st not in (0, 8):
+        _check(None, st)
+    return st, nnz.value
