@@ -85,7 +85,7 @@ typedef struct {
 
 /* Fill p with the defaults (r_graph 3.0, tau 1e-3, core_size 32, precision 1, kernel 0,
  * krylov_rank 4, krylov_tol 1e-2, c_k0 0.5, scc_tol 1e-8, scc_alpha 0.2, sp2_tol 1e-9,
- * sp2_kmax 60, ns_iters 6, ewald_tol 0). */
+ * sp2_kmax 60, ns_iters 4, ewald_tol 0). */
 void sedacs_default_params(sedacs_params* p);
 
 /* Create a context for N atoms of the given species in an orthorhombic periodic box

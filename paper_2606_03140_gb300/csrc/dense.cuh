@@ -29,7 +29,8 @@ struct GemmMat {
   int b_from_sp2;                // generic mode: B taken from the SP2 result buffer
   int a_from_sp2;
   int c_from_sp2;                // generic mode: C1 taken from the SP2 result buffer
-  int pad1;
+  int sym_out;                   // result is symmetric: only tiles tn >= tm are run, each
+                                 // off-diagonal tile is also written transposed
 };
 
 struct GemmWork {

@@ -153,6 +153,22 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const GemmParams p) {
     }
     tc_commit(accb);
   }
+  // while the tensor cores run, pull this thread's epilogue input rows (X / C1 / C2 masters)
+  // towards L2 so the epilogue does not wait on DRAM
+  {
+    const int prow = w.tm * 128 + warp * 32 + lane;
+    const long long roff = ((long long)prow * m.n_pad + w.tn * 128) * 4;
+    const uint8_t* pre[3] = {nullptr, nullptr, nullptr};
+    if (stepping) pre[0] = p.arena + m.x_off + in_shift + roff;
+    if (p.mode == kModeRsp) pre[1] = p.arena + m.c_off + roff;
+    if (p.mode == kModeGeneric && m.c_off >= 0) pre[1] = p.arena + m.c_off + (m.c_from_sp2 ? cur * m.buf_stride : 0) + roff;
+    if (p.mode == kModeGeneric && m.c2_off >= 0) pre[2] = p.arena + m.c2_off + roff;
+    if (prow < m.m_real)
+      for (int u = 0; u < 3; ++u)
+        if (pre[u])
+#pragma unroll
+          for (int q = 0; q < 4; ++q) asm volatile("prefetch.global.L2 [%0];" ::"l"(pre[u] + q * 128));
+  }
   __syncwarp();
   if (!mbar_wait(accb, 0)) ok = false;
   tc_fence_after();
@@ -264,6 +280,32 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const GemmParams p) {
         store_planes8(p.arena, m.outp_off + out_shift, m.outp_plane, p.nsplit_out, m.n_pad, row, col0 + 8 * q,
                       v + 8 * q);
     }
+    if (m.sym_out && !diag_tile) {
+      // mirrored tile through shared memory (the operand ring is idle now): the warp's
+      // 32 x 32 block is transposed so that lane l then holds output row (col0 + l) and
+      // writes it with the same vector stores as the direct tile.
+      float* tb = reinterpret_cast<float*>(smem) + warp * (32 * 33);
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < 32; ++j) tb[lane * 33 + j] = v[j];
+      __syncwarp();
+      float tv[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) tv[j] = tb[j * 33 + lane];
+      const int trow = col0 + lane;                      // output row of the mirrored element
+      const int tcol0 = w.tm * 128 + warp * 32;          // its first column
+      if (outm) {
+        float4* dst = reinterpret_cast<float4*>(outm + (long long)trow * m.n_pad + tcol0);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) dst[q] = make_float4(tv[4 * q], tv[4 * q + 1], tv[4 * q + 2], tv[4 * q + 3]);
+      }
+      if (m.outp_off >= 0 && p.nsplit_out > 0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          store_planes8(p.arena, m.outp_off + out_shift, m.outp_plane, p.nsplit_out, m.n_pad, trow, tcol0 + 8 * q,
+                        tv + 8 * q);
+      }
+    }
   }
   if (p.mode == kModeSp2 && diag_tile) {
     // fixed-order CTA reduction of the trace partials -> one slot per diagonal tile
@@ -361,7 +403,10 @@ __global__ void __launch_bounds__(256) f64_gemm_kernel(const GemmParams p) {
                    p.arena + m.c_off + (m.c_from_sp2 ? cur * m.buf_stride : 0))[(long long)row * ld + col];
         if (m.c2_off >= 0) v += (double)p.g2 * reinterpret_cast<const double*>(p.arena + m.c2_off)[(long long)row * ld + col];
       }
-      if (outm) outm[(long long)row * ld + col] = ok ? v : 0.0;
+      if (outm) {
+        outm[(long long)row * ld + col] = ok ? v : 0.0;
+        if (m.sym_out && w.tm != w.tn) outm[(long long)col * ld + row] = ok ? v : 0.0;
+      }
     }
   }
   if (p.mode == kModeSp2 && w.tm == w.tn) {

@@ -280,7 +280,7 @@ long long pptr_(const sedacs_ctx* ctx, int sl, int i, int copy = 0) {
 // C = alpha A B^T + beta I + g1 C1 + g2 C2 over every subgraph (slots a, b, out, c1, c2; -1: none).
 sedacs_status build_op(sedacs_ctx* ctx, int id, int a, int b, int out, int mode, float alpha, float beta,
                        bool b_from_sp2, bool a_from_sp2 = false, int c1 = -1, float g1 = 0.f, int c2 = -1,
-                       float g2 = 0.f, bool c_from_sp2 = false) {
+                       float g2 = 0.f, bool c_from_sp2 = false, bool sym = false) {
   const Layout& L = ctx->lay;
   std::vector<GemmMat> mats(L.n_sub);
   std::vector<GemmWork> work;
@@ -298,6 +298,7 @@ sedacs_status build_op(sedacs_ctx* ctx, int id, int a, int b, int out, int mode,
     m.c_off = (mode == kModeRsp) ? mptr(ctx, kR1, i) : (c1 >= 0 ? mptr(ctx, c1, i) : -1);
     m.c2_off = (c2 >= 0) ? mptr(ctx, c2, i) : -1;
     m.c_from_sp2 = c_from_sp2 ? 1 : 0;
+    m.sym_out = sym && !rows_out ? 1 : 0;
     m.buf_stride = ctx->slot[kX].copy_stride;
     m.tr_off = L.tr_off[i];
     m.n_pad = L.n_pad[i];
@@ -311,7 +312,7 @@ sedacs_status build_op(sedacs_ctx* ctx, int id, int a, int b, int out, int mode,
     const int tiles_n = L.n_pad[i] / ctx->tile;
     const int tiles_m = (rows_out ? L.m_pad[i] : L.n_pad[i]) / ctx->tile;
     for (int tm = 0; tm < tiles_m; ++tm)
-      for (int tn = 0; tn < tiles_n; ++tn) work.push_back({i, tm, tn, 0});
+      for (int tn = (m.sym_out ? tm : 0); tn < tiles_n; ++tn) work.push_back({i, tm, tn, 0});
   }
   GemmOp& op = ctx->ops[id];
   if (op.mats_d) cudaFree(op.mats_d);
@@ -530,19 +531,19 @@ sedacs_status rebuild_layout(sedacs_ctx* ctx) {
   (void)f;
   // S^-1/2 in deviation form: Y = I + E_y (kY*), Z = I + E_z (kZ*), T = I + E_t (kT);
   // only products of the small deviations go through the tensor cores.
-  STCHK(build_op(ctx, OP_NS_Y1, kY0, kT, kY1, kModeGeneric, 1.f, 0.f, false, false, kY0, 1.f, kT, 1.f));
-  STCHK(build_op(ctx, OP_NS_T0, kZ0, kY0, kT, kModeGeneric, -0.5f, 0.f, false, false, kZ0, -0.5f, kY0, -0.5f));
-  STCHK(build_op(ctx, OP_NS_T1, kZ1, kY1, kT, kModeGeneric, -0.5f, 0.f, false, false, kZ1, -0.5f, kY1, -0.5f));
-  STCHK(build_op(ctx, OP_NS_Y0, kY0, kT, kY1, kModeGeneric, 1.f, 0.f, false, false, kY0, 1.f, kT, 1.f));
-  STCHK(build_op(ctx, OP_NS_Y1b, kY1, kT, kY0, kModeGeneric, 1.f, 0.f, false, false, kY1, 1.f, kT, 1.f));
-  STCHK(build_op(ctx, OP_NS_Z0, kT, kZ0, kZ1, kModeGeneric, 1.f, 0.f, false, false, kT, 1.f, kZ0, 1.f));
-  STCHK(build_op(ctx, OP_NS_Z1, kT, kZ1, kZ0, kModeGeneric, 1.f, 0.f, false, false, kT, 1.f, kZ1, 1.f));
+  STCHK(build_op(ctx, OP_NS_Y1, kY0, kT, kY1, kModeGeneric, 1.f, 0.f, false, false, kY0, 1.f, kT, 1.f, false, true));
+  STCHK(build_op(ctx, OP_NS_T0, kZ0, kY0, kT, kModeGeneric, -0.5f, 0.f, false, false, kZ0, -0.5f, kY0, -0.5f, false, true));
+  STCHK(build_op(ctx, OP_NS_T1, kZ1, kY1, kT, kModeGeneric, -0.5f, 0.f, false, false, kZ1, -0.5f, kY1, -0.5f, false, true));
+  STCHK(build_op(ctx, OP_NS_Y0, kY0, kT, kY1, kModeGeneric, 1.f, 0.f, false, false, kY0, 1.f, kT, 1.f, false, true));
+  STCHK(build_op(ctx, OP_NS_Y1b, kY1, kT, kY0, kModeGeneric, 1.f, 0.f, false, false, kY1, 1.f, kT, 1.f, false, true));
+  STCHK(build_op(ctx, OP_NS_Z0, kT, kZ0, kZ1, kModeGeneric, 1.f, 0.f, false, false, kT, 1.f, kZ0, 1.f, false, true));
+  STCHK(build_op(ctx, OP_NS_Z1, kT, kZ1, kZ0, kModeGeneric, 1.f, 0.f, false, false, kT, 1.f, kZ1, 1.f, false, true));
   // h~ = Z h Z = P + P E_z with P = h + E_z h
   STCHK(build_op(ctx, OP_P0, kZ0, kH, kP, kModeGeneric, 1.f, 0.f, false, false, kH, 1.f));
   STCHK(build_op(ctx, OP_P1, kZ1, kH, kP, kModeGeneric, 1.f, 0.f, false, false, kH, 1.f));
-  STCHK(build_op(ctx, OP_HT0, kP, kZ0, kHt, kModeGeneric, 1.f, 0.f, false, false, kP, 1.f));
-  STCHK(build_op(ctx, OP_HT1, kP, kZ1, kHt, kModeGeneric, 1.f, 0.f, false, false, kP, 1.f));
-  STCHK(build_op(ctx, OP_SP2, kX, kX, kX, kModeSp2, 1.f, 0.f, false));
+  STCHK(build_op(ctx, OP_HT0, kP, kZ0, kHt, kModeGeneric, 1.f, 0.f, false, false, kP, 1.f, -1, 0.f, false, true));
+  STCHK(build_op(ctx, OP_HT1, kP, kZ1, kHt, kModeGeneric, 1.f, 0.f, false, false, kP, 1.f, -1, 0.f, false, true));
+  STCHK(build_op(ctx, OP_SP2, kX, kX, kX, kModeSp2, 1.f, 0.f, false, false, -1, 0.f, -1, 0.f, false, true));
   // core rows: T1 = Z_c X = X_c + E_z,c X ; D_c = 2 T1 Z = 2 (T1 + T1 E_z); W_c = 2 (T1 h~) Z
   STCHK(build_op(ctx, OP_T1_0, kZ0, kX, kT1, kModeGeneric, 1.f, 0.f, true, false, kX, 1.f, -1, 0.f, true));
   STCHK(build_op(ctx, OP_T1_1, kZ1, kX, kT1, kModeGeneric, 1.f, 0.f, true, false, kX, 1.f, -1, 0.f, true));
@@ -556,8 +557,8 @@ sedacs_status rebuild_layout(sedacs_ctx* ctx) {
   STCHK(build_op(ctx, OP_RSP_B, kR2, kX, kR2, kModeRsp, 1.f, 0.f, false));
   STCHK(build_op(ctx, OP_DP0, kZ0, kdH, kP, kModeGeneric, 1.f, 0.f, false, false, kdH, 1.f));
   STCHK(build_op(ctx, OP_DP1, kZ1, kdH, kP, kModeGeneric, 1.f, 0.f, false, false, kdH, 1.f));
-  STCHK(build_op(ctx, OP_DHT0, kP, kZ0, kdHt, kModeGeneric, 1.f, 0.f, false, false, kP, 1.f));
-  STCHK(build_op(ctx, OP_DHT1, kP, kZ1, kdHt, kModeGeneric, 1.f, 0.f, false, false, kP, 1.f));
+  STCHK(build_op(ctx, OP_DHT0, kP, kZ0, kdHt, kModeGeneric, 1.f, 0.f, false, false, kP, 1.f, -1, 0.f, false, true));
+  STCHK(build_op(ctx, OP_DHT1, kP, kZ1, kdHt, kModeGeneric, 1.f, 0.f, false, false, kP, 1.f, -1, 0.f, false, true));
   STCHK(build_op(ctx, OP_DT1_0, kZ0, kR2, kdT1, kModeGeneric, 1.f, 0.f, true, false, kR2, 1.f, -1, 0.f, true));
   STCHK(build_op(ctx, OP_DT1_1, kZ1, kR2, kdT1, kModeGeneric, 1.f, 0.f, true, false, kR2, 1.f, -1, 0.f, true));
   STCHK(build_op(ctx, OP_DDC0, kdT1, kZ0, kdDc, kModeGeneric, 2.f, 0.f, false, false, kdT1, 2.f));
@@ -1028,7 +1029,7 @@ void sedacs_default_params(sedacs_params* p) {
   p->scc_alpha = 0.2;
   p->sp2_tol = 1e-9;
   p->sp2_kmax = 60;
-  p->ns_iters = 6;
+  p->ns_iters = 4;
   p->ewald_tol = 0.0;
 }
 
