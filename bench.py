@@ -173,9 +173,11 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
     e0.record(stream)
     S.sedacs_xlbomd_step(ctx, Rd, Vd, args.steps, args.dt, Ed)
     e1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     barrier(world)
     clocks = clk.stop()

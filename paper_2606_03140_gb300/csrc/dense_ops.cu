@@ -31,39 +31,35 @@ template <typename T>
 __global__ void affine_kernel(const SubView* in_v, const SubView* out_v, uint8_t* arena, double a, double b) {
   const SubView vi = in_v[blockIdx.y];
   const SubView vo = out_v[blockIdx.y];
-  const int row = blockIdx.x;
+  const int row = blockIdx.x * 8 + (threadIdx.x >> 5);     // one warp per row
   if (row >= vo.rows_pad) return;
   const T* src = reinterpret_cast<const T*>(arena + vi.master) + (long long)row * vi.n_pad;
   T* dst = reinterpret_cast<T*>(arena + vo.master) + (long long)row * vo.n_pad;
-  for (int c = threadIdx.x; c < vo.n_pad; c += blockDim.x) {
+  for (int c = threadIdx.x & 31; c < vo.n_pad; c += 32) {
     const bool ok = row < vo.n_real && c < vo.n_real;
     dst[c] = ok ? (T)(a * (double)src[c] + (row == c ? b : 0.0)) : (T)0;
   }
 }
 
-// Gershgorin: per row, d - r and d + r of the valid block.
+// Gershgorin: per row (one warp), d - r and d + r of the valid block.
 template <typename T>
 __global__ void gersh_rows_kernel(const SubView* views, const uint8_t* arena, double* lo, double* hi,
                                   const long long* row_base) {
   const SubView v = views[blockIdx.y];
-  const int row = blockIdx.x;
+  const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
   if (row >= v.n_real) return;
   const T* src = reinterpret_cast<const T*>(arena + v.master) + (long long)row * v.n_pad;
   double s = 0.0, d = 0.0;
-  for (int c = threadIdx.x; c < v.n_real; c += blockDim.x) {
+  for (int c = lane; c < v.n_real; c += 32) {
     const double x = (double)src[c];
     if (c == row) d = x; else s += fabs(x);
   }
-  __shared__ double rs[8], rd[8];
   s = warp_sum(s);
   d = warp_sum(d);
-  if ((threadIdx.x & 31) == 0) { rs[threadIdx.x >> 5] = s; rd[threadIdx.x >> 5] = d; }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double ss = 0.0, dd = 0.0;
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { ss += rs[q]; dd += rd[q]; }
-    lo[row_base[blockIdx.y] + row] = dd - ss;
-    hi[row_base[blockIdx.y] + row] = dd + ss;
+  if (lane == 0) {
+    lo[row_base[blockIdx.y] + row] = d - s;
+    hi[row_base[blockIdx.y] + row] = d + s;
   }
 }
 
@@ -89,41 +85,38 @@ __global__ void gersh_reduce_kernel(const SubView* views, const double* lo, cons
   if (threadIdx.x == 0) { bounds[2 * blockIdx.x] = smn[0]; bounds[2 * blockIdx.x + 1] = smx[0]; }
 }
 
-// X0 = (emax I - (h~ + h~^T)/2) / (emax - emin) on the valid block.
+// X0 = (emax I - h~) / (emax - emin) on the valid block (h~ is stored exactly symmetric:
+// its GEMM writes each off-diagonal tile and its transpose from the same values).
 template <typename T>
 __global__ void sp2_x0_kernel(const SubView* hv, const SubView* xv, uint8_t* arena, const double* bounds) {
   const SubView vh = hv[blockIdx.y];
   const SubView vx = xv[blockIdx.y];
-  const int row = blockIdx.x;
+  const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (row >= vx.rows_pad) return;
   const double emin = bounds[2 * blockIdx.y], emax = bounds[2 * blockIdx.y + 1];
   const double inv = 1.0 / (emax - emin);
-  const T* h = reinterpret_cast<const T*>(arena + vh.master);
+  const T* h = reinterpret_cast<const T*>(arena + vh.master) + (long long)row * vh.n_pad;
   T* x = reinterpret_cast<T*>(arena + vx.master) + (long long)row * vx.n_pad;
-  for (int c = threadIdx.x; c < vx.n_pad; c += blockDim.x) {
+  for (int c = threadIdx.x & 31; c < vx.n_pad; c += 32) {
     T out = (T)0;
-    if (row < vx.n_real && c < vx.n_real) {
-      const double hs = 0.5 * ((double)h[(long long)row * vh.n_pad + c] + (double)h[(long long)c * vh.n_pad + row]);
-      out = (T)(((row == c ? emax : 0.0) - hs) * inv);
-    }
+    if (row < vx.n_real && c < vx.n_real) out = (T)(((row == c ? emax : 0.0) - (double)h[c]) * inv);
     x[c] = out;
   }
 }
 
-// dX0 = -(dh~ + dh~^T)/2 / (emax - emin): first-order change of the SP2 start matrix.
+// dX0 = -dh~ / (emax - emin): first-order change of the SP2 start matrix.
 template <typename T>
 __global__ void sp2_dx0_kernel(const SubView* hv, const SubView* xv, uint8_t* arena, const double* bounds) {
   const SubView vh = hv[blockIdx.y];
   const SubView vx = xv[blockIdx.y];
-  const int row = blockIdx.x;
+  const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (row >= vx.rows_pad) return;
   const double inv = 1.0 / (bounds[2 * blockIdx.y + 1] - bounds[2 * blockIdx.y]);
-  const T* h = reinterpret_cast<const T*>(arena + vh.master);
+  const T* h = reinterpret_cast<const T*>(arena + vh.master) + (long long)row * vh.n_pad;
   T* x = reinterpret_cast<T*>(arena + vx.master) + (long long)row * vx.n_pad;
-  for (int c = threadIdx.x; c < vx.n_pad; c += blockDim.x) {
+  for (int c = threadIdx.x & 31; c < vx.n_pad; c += 32) {
     T out = (T)0;
-    if (row < vx.n_real && c < vx.n_real)
-      out = (T)(-0.5 * ((double)h[(long long)row * vh.n_pad + c] + (double)h[(long long)c * vh.n_pad + row]) * inv);
+    if (row < vx.n_real && c < vx.n_real) out = (T)(-(double)h[c] * inv);
     x[c] = out;
   }
 }
@@ -203,7 +196,7 @@ void launch_split_planes(const SubView* views, int n_sub, int max_rows, uint8_t*
 void launch_affine(const SubView* in, const SubView* out, int n_sub, int max_rows, uint8_t* arena, double a,
                    double b, bool f64, cudaStream_t s) {
   if (n_sub <= 0 || max_rows <= 0) return;
-  dim3 g(max_rows, n_sub);
+  dim3 g((max_rows + 7) / 8, n_sub);
   if (f64) affine_kernel<double><<<g, 256, 0, s>>>(in, out, arena, a, b);
   else affine_kernel<float><<<g, 256, 0, s>>>(in, out, arena, a, b);
 }
@@ -211,7 +204,7 @@ void launch_affine(const SubView* in, const SubView* out, int n_sub, int max_row
 void launch_gershgorin(const SubView* views, int n_sub, int max_rows, const uint8_t* arena, double* lo, double* hi,
                        const long long* row_base, double* bounds, bool f64, cudaStream_t s) {
   if (n_sub <= 0) return;
-  dim3 g(max_rows, n_sub);
+  dim3 g((max_rows + 7) / 8, n_sub);
   if (f64) gersh_rows_kernel<double><<<g, 256, 0, s>>>(views, arena, lo, hi, row_base);
   else gersh_rows_kernel<float><<<g, 256, 0, s>>>(views, arena, lo, hi, row_base);
   gersh_reduce_kernel<<<n_sub, 256, 0, s>>>(views, lo, hi, row_base, bounds);
@@ -220,7 +213,7 @@ void launch_gershgorin(const SubView* views, int n_sub, int max_rows, const uint
 void launch_sp2_x0(const SubView* hv, const SubView* xv, int n_sub, int max_rows, uint8_t* arena,
                    const double* bounds, bool f64, cudaStream_t s) {
   if (n_sub <= 0) return;
-  dim3 g(max_rows, n_sub);
+  dim3 g((max_rows + 7) / 8, n_sub);
   if (f64) sp2_x0_kernel<double><<<g, 256, 0, s>>>(hv, xv, arena, bounds);
   else sp2_x0_kernel<float><<<g, 256, 0, s>>>(hv, xv, arena, bounds);
 }
@@ -228,7 +221,7 @@ void launch_sp2_x0(const SubView* hv, const SubView* xv, int n_sub, int max_rows
 void launch_sp2_dx0(const SubView* hv, const SubView* xv, int n_sub, int max_rows, uint8_t* arena,
                     const double* bounds, bool f64, cudaStream_t s) {
   if (n_sub <= 0) return;
-  dim3 g(max_rows, n_sub);
+  dim3 g((max_rows + 7) / 8, n_sub);
   if (f64) sp2_dx0_kernel<double><<<g, 256, 0, s>>>(hv, xv, arena, bounds);
   else sp2_dx0_kernel<float><<<g, 256, 0, s>>>(hv, xv, arena, bounds);
 }

@@ -229,8 +229,10 @@ sedacs_status prepare_geometry(sedacs_ctx* ctx) {
   cudaStream_t s = ctx->stream;
   CUCHK(grow(&ctx->d_pptr, &ctx->rows_cap, (long long)N + 1) == cudaSuccess ? cudaSuccess : cudaErrorMemoryAllocation);
   long long pn = 0;
+  // pair list of the Slater-Koster blocks: FP32 distance test (a pair at the cutoff carries a
+  // zero block, so the exact side of the boundary does not matter)
   CUCHK(ctx->pb.build(ctx->d_R, N, ctx->box, ctx->model.r_off, nullptr, nullptr, nullptr, 0.0, ctx->d_pptr,
-                      &ctx->d_pcol, &ctx->pcol_cap, &pn, ctx->d_err, s));
+                      &ctx->d_pcol, &ctx->pcol_cap, &pn, ctx->d_err, s, false));
   ctx->pnnz = pn;
   const size_t esz = ctx->f64 ? 8 : 4;
   if (pn * 16 > ctx->blk_cap) {

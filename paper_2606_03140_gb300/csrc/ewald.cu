@@ -83,29 +83,50 @@ __global__ void structure_factor_kernel(const KRow* rows, const typename C2<T>::
     }
   }
   __syncthreads();
+  // 4 groups of 64 threads: lane = m3 slot, group = every 4th atom of the chunk; the group
+  // partials are added in a fixed order through shared memory.
   const int nm3 = kr.m3hi - kr.m3lo + 1;
-  for (int t = threadIdx.x; t < nm3; t += blockDim.x) {
-    const int m3 = kr.m3lo + t;
-    const int am3 = abs(m3);
+  const int grp = threadIdx.x >> 6, ln = threadIdx.x & 63;
+  T* red = reinterpret_cast<T*>(c12 + (size_t)chunk * NV);   // [4][64][NV][2] after the products
+  for (int base = 0; base < nm3; base += 64) {      // block-uniform loop over 64 m3 slots at a time
     T sr[NV], si[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) { sr[v] = 0; si[v] = 0; }
-    for (int J = a0; J < a1; ++J) {
-      CT z = tab[(2LL * N + J) * (nmax_all + 1) + am3];
-      if (m3 < 0) z.y = -z.y;
+    const int t = base + ln;
+    const int m3 = kr.m3lo + t;
+    const int am3 = abs(m3);
+    if (t < nm3) {
+      for (int J = a0 + grp; J < a1; J += 4) {
+        CT z = tab[(2LL * N + J) * (nmax_all + 1) + am3];
+        if (m3 < 0) z.y = -z.y;
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        const CT c = c12[(J - a0) * NV + v];
-        sr[v] += c.x * z.x - c.y * z.y;
-        si[v] += c.x * z.y + c.y * z.x;
+        for (int v = 0; v < NV; ++v) {
+          const CT c = c12[(J - a0) * NV + v];
+          sr[v] += c.x * z.x - c.y * z.y;
+          si[v] += c.x * z.y + c.y * z.x;
+        }
       }
     }
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      const long long o = ((long long)blockIdx.y * NV + v) * nk_total + kr.koff + t;
-      part[2 * o] = (double)sr[v];
-      part[2 * o + 1] = (double)si[v];
+      red[((grp * 64 + ln) * NV + v) * 2] = sr[v];
+      red[((grp * 64 + ln) * NV + v) * 2 + 1] = si[v];
     }
+    __syncthreads();
+    if (grp == 0 && t < nm3) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        double re = 0.0, im = 0.0;
+        for (int g2 = 0; g2 < 4; ++g2) {
+          re += (double)red[((g2 * 64 + ln) * NV + v) * 2];
+          im += (double)red[((g2 * 64 + ln) * NV + v) * 2 + 1];
+        }
+        const long long o = ((long long)blockIdx.y * NV + v) * nk_total + kr.koff + t;
+        part[2 * o] = re;
+        part[2 * o + 1] = im;
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -467,12 +488,12 @@ template <typename T>
 static void run_sf(Ewald& E, const double* b0, const double* b1, int nv, cudaStream_t s) {
   using CT = typename C2<T>::t;
   dim3 grid(E.nrows_, E.nchunk_);
-  const size_t shm = sizeof(CT) * Ewald::kChunk * nv;
+  const size_t shm = sizeof(CT) * Ewald::kChunk * nv + sizeof(T) * 4 * 64 * nv * 2;
   if (nv == 1)
-    structure_factor_kernel<T, 1><<<grid, 64, shm, s>>>(E.rows_d, reinterpret_cast<const CT*>(E.tab), b0, b1, E.N_,
+    structure_factor_kernel<T, 1><<<grid, 256, shm, s>>>(E.rows_d, reinterpret_cast<const CT*>(E.tab), b0, b1, E.N_,
                                                         E.g.nmax_all, Ewald::kChunk, E.part, E.nk_);
   else
-    structure_factor_kernel<T, 2><<<grid, 64, shm, s>>>(E.rows_d, reinterpret_cast<const CT*>(E.tab), b0, b1, E.N_,
+    structure_factor_kernel<T, 2><<<grid, 256, shm, s>>>(E.rows_d, reinterpret_cast<const CT*>(E.tab), b0, b1, E.N_,
                                                         E.g.nmax_all, Ewald::kChunk, E.part, E.nk_);
   sf_reduce_kernel<T><<<(int)((E.nk_ + 255) / 256), 256, 0, s>>>(E.part, E.nchunk_, nv, E.nk_, E.wk_d,
                                                                  reinterpret_cast<CT*>(E.ws));

@@ -42,7 +42,20 @@ struct CellGrid {
   double cw[3];
   double box[3];
   int brute;   // 1: fewer than 3 cells on an axis, test every atom
+  int exact;   // 1: separately rounded FP64 test (bit-reproducible); 0: FP32 test (pair lists)
 };
+
+__device__ __forceinline__ float min_image_r2_f(const double* R, int i, int j, const double* box) {
+  float d[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float dx = (float)(R[3 * j + a] - R[3 * i + a]);
+    const float L = (float)box[a];
+    dx -= L * rintf(dx / L);
+    d[a] = dx;
+  }
+  return d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+}
 
 __global__ void cell_assign_kernel(const double* R, int N, CellGrid g, int* cell_of, int* cell_count) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -74,9 +87,13 @@ __device__ __forceinline__ void for_each_distance_neighbour(const double* R, int
                                                             const int* cell_count, const int* cell_atoms,
                                                             double rg2, F f) {
   const double box[3] = {g.box[0], g.box[1], g.box[2]};
+  const float rg2f = (float)rg2;
+  auto within = [&](int j) {
+    return g.exact ? (min_image_r2(R, i, j, box) < rg2) : (min_image_r2_f(R, i, j, box) < rg2f);
+  };
   if (g.brute) {
     for (int j = 0; j < N; ++j)
-      if (j != i && min_image_r2(R, i, j, box) < rg2) f(j);
+      if (j != i && within(j)) f(j);
     return;
   }
   const int cid = cell_of[i];
@@ -91,7 +108,7 @@ __device__ __forceinline__ void for_each_distance_neighbour(const double* R, int
         const int s = cell_start[c], n = cell_count[c];
         for (int q = 0; q < n; ++q) {
           const int j = cell_atoms[s + q];
-          if (j != i && min_image_r2(R, i, j, box) < rg2) f(j);
+          if (j != i && within(j)) f(j);
         }
       }
 }
@@ -366,9 +383,10 @@ void GraphBuilder::release() {
   cap_cand = 0;
 }
 
-static CellGrid make_grid(const double box[3], double rc) {
+static CellGrid make_grid(const double box[3], double rc, int exact = 1) {
   CellGrid g;
   g.brute = 0;
+  g.exact = exact;
   for (int a = 0; a < 3; ++a) {
     g.box[a] = box[a];
     g.nc[a] = (int)floor(box[a] / (rc * (1.0 + 1e-9) + 1e-9));
@@ -381,9 +399,9 @@ static CellGrid make_grid(const double box[3], double rc) {
 
 cudaError_t GraphBuilder::build(const double* dR, int N, const double box[3], double r_graph, const long long* gptr,
                                 const int* gcol, const double* gval, double tau, long long* row_ptr, int** col_out,
-                                long long* col_cap, long long* nnz_host, int* derr, cudaStream_t s) {
+                                long long* col_cap, long long* nnz_host, int* derr, cudaStream_t s, bool exact) {
   cudaError_t e;
-  CellGrid g = make_grid(box, r_graph);
+  CellGrid g = make_grid(box, r_graph, exact ? 1 : 0);
   const int ncell = g.nc[0] * g.nc[1] * g.nc[2];
   if (N > cap_n) {
     for (int** p : {&cell_of, &cnt, &fillc, &ucnt}) { if (*p) cudaFree(*p); *p = nullptr; }

@@ -31,7 +31,7 @@ struct GraphBuilder {
   // atom-condensed density graph.
   cudaError_t build(const double* dR, int N, const double box[3], double r_graph, const long long* gptr,
                     const int* gcol, const double* gval, double tau, long long* row_ptr, int** col_out,
-                    long long* col_cap, long long* nnz_host, int* derr, cudaStream_t s);
+                    long long* col_cap, long long* nnz_host, int* derr, cudaStream_t s, bool exact = true);
 };
 
 struct Partitioner {
