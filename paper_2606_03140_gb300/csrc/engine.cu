@@ -168,6 +168,18 @@ inline int nblk(long long n, int tb) { return (int)((n + tb - 1) / tb); }
 
 namespace {
 
+// Grow-only device buffer: reallocates only when `bytes` exceeds the recorded capacity.
+cudaError_t ensure(sedacs_ctx* ctx, void** p, size_t bytes) {
+  size_t& cap = ctx->caps[p];
+  if (*p && bytes <= cap) return cudaSuccess;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  const size_t n = std::max<size_t>(bytes + bytes / 2, 256);
+  cudaError_t e = cudaMalloc(p, n);
+  cap = (e == cudaSuccess) ? n : 0;
+  return e;
+}
+
 template <typename T>
 cudaError_t grow(T** p, long long* cap, long long need) {
   if (need <= *cap && *p) return cudaSuccess;
@@ -317,12 +329,8 @@ sedacs_status build_op(sedacs_ctx* ctx, int id, int a, int b, int out, int mode,
       for (int tn = (m.sym_out ? tm : 0); tn < tiles_n; ++tn) work.push_back({i, tm, tn, 0});
   }
   GemmOp& op = ctx->ops[id];
-  if (op.mats_d) cudaFree(op.mats_d);
-  if (op.work_d) cudaFree(op.work_d);
-  op.mats_d = nullptr;
-  op.work_d = nullptr;
-  CUCHK(cudaMalloc(&op.mats_d, sizeof(GemmMat) * std::max(1, L.n_sub)));
-  CUCHK(cudaMalloc(&op.work_d, sizeof(GemmWork) * std::max<size_t>(1, work.size())));
+  CUCHK(ensure(ctx, reinterpret_cast<void**>(&op.mats_d), sizeof(GemmMat) * std::max(1, L.n_sub)));
+  CUCHK(ensure(ctx, reinterpret_cast<void**>(&op.work_d), sizeof(GemmWork) * std::max<size_t>(1, work.size())));
   CUCHK(cudaMemcpyAsync(op.mats_d, mats.data(), sizeof(GemmMat) * L.n_sub, cudaMemcpyHostToDevice, ctx->stream));
   if (!work.empty())
     CUCHK(cudaMemcpyAsync(op.work_d, work.data(), sizeof(GemmWork) * work.size(), cudaMemcpyHostToDevice,
@@ -333,7 +341,6 @@ sedacs_status build_op(sedacs_ctx* ctx, int id, int a, int b, int out, int mode,
   op.g1 = g1;
   op.g2 = g2;
   op.mode = mode;
-  CUCHK(cudaStreamSynchronize(ctx->stream));
   return SEDACS_OK;
 }
 
@@ -371,20 +378,17 @@ sedacs_status upload_views(sedacs_ctx* ctx, int sl, int copy, SubView** dst) {
     s.pad = 0;
     v[i] = s;
   }
-  if (*dst) cudaFree(*dst);
-  *dst = nullptr;
-  CUCHK(cudaMalloc(dst, sizeof(SubView) * std::max(1, L.n_sub)));
+  CUCHK(ensure(ctx, reinterpret_cast<void**>(dst), sizeof(SubView) * std::max(1, L.n_sub)));
   CUCHK(cudaMemcpyAsync(*dst, v.data(), sizeof(SubView) * L.n_sub, cudaMemcpyHostToDevice, ctx->stream));
-  CUCHK(cudaStreamSynchronize(ctx->stream));
+  CUCHK(cudaStreamSynchronize(ctx->stream));   // v is a local
   return SEDACS_OK;
 }
 
 template <typename T>
 sedacs_status upload_vec(sedacs_ctx* ctx, T** dst, const std::vector<T>& v) {
-  if (*dst) cudaFree(*dst);
-  *dst = nullptr;
-  CUCHK(cudaMalloc(dst, sizeof(T) * std::max<size_t>(1, v.size())));
+  CUCHK(ensure(ctx, reinterpret_cast<void**>(dst), sizeof(T) * std::max<size_t>(1, v.size())));
   if (!v.empty()) CUCHK(cudaMemcpyAsync(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, ctx->stream));
+  CUCHK(cudaStreamSynchronize(ctx->stream));   // v may be a temporary
   return SEDACS_OK;
 }
 
@@ -402,10 +406,8 @@ sedacs_status rebuild_layout(sedacs_ctx* ctx) {
   for (int i = 0; i < P; ++i) ncore[i] = ctx->part.leaves[i].count;
   STCHK(upload_vec(ctx, &ctx->d_n_core, ncore));
   CUCHK(grow(&ctx->d_orb_off, &ctx->loc_cap, tot_rows) == cudaSuccess ? cudaSuccess : cudaErrorMemoryAllocation);
-  if (ctx->d_n_orb_sub) cudaFree(ctx->d_n_orb_sub);
-  if (ctx->d_n_core_orb) cudaFree(ctx->d_n_core_orb);
-  CUCHK(cudaMalloc(&ctx->d_n_orb_sub, sizeof(int) * std::max(1, P)));
-  CUCHK(cudaMalloc(&ctx->d_n_core_orb, sizeof(int) * std::max(1, P)));
+  CUCHK(ensure(ctx, reinterpret_cast<void**>(&ctx->d_n_orb_sub), sizeof(int) * std::max(1, P)));
+  CUCHK(ensure(ctx, reinterpret_cast<void**>(&ctx->d_n_core_orb), sizeof(int) * std::max(1, P)));
   launch_orb_offsets(ctx->d_sub_ptr, ctx->d_sub_atoms, ctx->d_species, ctx->model, ctx->d_orb_off, ctx->d_n_orb_sub,
                      ctx->d_n_core, ctx->d_n_core_orb, P, s);
   L.n_real.resize(P);
@@ -491,16 +493,11 @@ sedacs_status rebuild_layout(sedacs_ctx* ctx) {
   STCHK(upload_vec(ctx, &ctx->d_n_pad, npad));
   STCHK(upload_vec(ctx, &ctx->d_n_real, nreal));
   STCHK(upload_vec(ctx, &ctx->d_n_diag, ndiag));
-  if (ctx->d_glo) cudaFree(ctx->d_glo);
-  if (ctx->d_ghi) cudaFree(ctx->d_ghi);
-  if (ctx->d_bounds) cudaFree(ctx->d_bounds);
-  if (ctx->d_slots) cudaFree(ctx->d_slots);
-  if (ctx->d_sp2) cudaFree(ctx->d_sp2);
-  CUCHK(cudaMalloc(&ctx->d_glo, sizeof(double) * std::max(1LL, rb)));
-  CUCHK(cudaMalloc(&ctx->d_ghi, sizeof(double) * std::max(1LL, rb)));
-  CUCHK(cudaMalloc(&ctx->d_bounds, sizeof(double) * 2 * std::max(1, P)));
-  CUCHK(cudaMalloc(&ctx->d_slots, sizeof(double) * std::max(1LL, L.tr_total)));
-  CUCHK(cudaMalloc(&ctx->d_sp2, sizeof(Sp2State) * std::max(1, P)));
+  CUCHK(ensure(ctx, reinterpret_cast<void**>(&ctx->d_glo), sizeof(double) * std::max(1LL, rb)));
+  CUCHK(ensure(ctx, reinterpret_cast<void**>(&ctx->d_ghi), sizeof(double) * std::max(1LL, rb)));
+  CUCHK(ensure(ctx, reinterpret_cast<void**>(&ctx->d_bounds), sizeof(double) * 2 * std::max(1, P)));
+  CUCHK(ensure(ctx, reinterpret_cast<void**>(&ctx->d_slots), sizeof(double) * std::max(1LL, L.tr_total)));
+  CUCHK(ensure(ctx, reinterpret_cast<void**>(&ctx->d_sp2), sizeof(Sp2State) * std::max(1, P)));
   // subgraph-of-row, core lists, local index table, density-graph row pointers
   std::vector<int> sor(tot_rows), csub, cloc;
   std::vector<long long> gdp(N + 1, 0);
@@ -518,19 +515,13 @@ sedacs_status rebuild_layout(sedacs_ctx* ctx) {
   STCHK(upload_vec(ctx, &ctx->d_sub_of_row, sor));
   STCHK(upload_vec(ctx, &ctx->d_core_sub, csub));
   STCHK(upload_vec(ctx, &ctx->d_core_local, cloc));
-  if (ctx->d_gd_ptr) cudaFree(ctx->d_gd_ptr);
-  ctx->d_gd_ptr = nullptr;
   STCHK(upload_vec(ctx, &ctx->d_gd_ptr, gdp));
   ctx->gd_nnz = gdp[N];
   CUCHK(grow(&ctx->d_gd_col, &ctx->gd_cap, ctx->gd_nnz + 1) == cudaSuccess ? cudaSuccess : cudaErrorMemoryAllocation);
-  if (ctx->d_gd_val) cudaFree(ctx->d_gd_val);
-  CUCHK(cudaMalloc(&ctx->d_gd_val, sizeof(double) * ctx->gd_cap));
-  if (ctx->d_loc) cudaFree(ctx->d_loc);
-  CUCHK(cudaMalloc(&ctx->d_loc, sizeof(int) * (size_t)N * std::max(1, P)));
+  CUCHK(ensure(ctx, reinterpret_cast<void**>(&ctx->d_gd_val), sizeof(double) * ctx->gd_cap));
+  CUCHK(ensure(ctx, reinterpret_cast<void**>(&ctx->d_loc), sizeof(int) * (size_t)N * std::max(1, P)));
   launch_loc_fill(ctx->d_sub_ptr, ctx->d_sub_atoms, ctx->d_loc, N, P, s);
   // GEMM tables
-  const bool f = ctx->f64;
-  (void)f;
   // S^-1/2 in deviation form: Y = I + E_y (kY*), Z = I + E_z (kZ*), T = I + E_t (kT);
   // only products of the small deviations go through the tensor cores.
   STCHK(build_op(ctx, OP_NS_Y1, kY0, kT, kY1, kModeGeneric, 1.f, 0.f, false, false, kY0, 1.f, kT, 1.f, false, true));

@@ -64,7 +64,11 @@ struct Layout {
 
 }  // namespace sedacs
 
+#include <unordered_map>
+
 struct sedacs_ctx {
+  // capacities of grow-only device buffers, keyed by the address of their pointer
+  std::unordered_map<void**, size_t> caps;
   // system
   int N = 0;
   std::vector<int> species_h;

@@ -474,6 +474,7 @@ void Partitioner::release() {
     if (p) cudaFree(p);
   perm = nullptr; skey = nullptr; sidx = nullptr; segs_d = nullptr; bits = nullptr; hcnt = nullptr;
   cap_n = cap_scr = cap_seg = 0;
+  cap_hcnt = cap_subptr = 0;
   cap_bits = 0;
 }
 
@@ -580,8 +581,12 @@ cudaError_t Partitioner::halos(const long long* row_ptr, const int* col, int N, 
     if ((e = cudaMalloc(&bits, sizeof(unsigned) * need))) return e;
     cap_bits = need;
   }
-  if (hcnt) cudaFree(hcnt);
-  if ((e = cudaMalloc(&hcnt, sizeof(int) * n_parts))) return e;
+  if (n_parts > cap_hcnt) {
+    if (hcnt) cudaFree(hcnt);
+    hcnt = nullptr;
+    if ((e = cudaMalloc(&hcnt, sizeof(int) * n_parts))) return e;
+    cap_hcnt = n_parts;
+  }
   cudaMemcpyAsync(segs_d, leaves.data(), sizeof(RcbSeg) * leaves.size(), cudaMemcpyHostToDevice, s);
   halo_mark_kernel<<<n_parts, 256, 0, s>>>(row_ptr, col, perm, segs_d, bits, words);
   halo_count_kernel<<<n_parts, 256, 0, s>>>(bits, words, hcnt);
@@ -597,8 +602,12 @@ cudaError_t Partitioner::halos(const long long* row_ptr, const int* col, int N, 
     *sub_cap = tot + tot / 4 + 1024;
     if ((e = cudaMalloc(sub_atoms_d, sizeof(int) * (*sub_cap)))) return e;
   }
-  if (*sub_ptr_d) cudaFree(*sub_ptr_d);
-  if ((e = cudaMalloc(sub_ptr_d, sizeof(long long) * (n_parts + 1)))) return e;
+  if (n_parts + 1 > cap_subptr) {
+    if (*sub_ptr_d) cudaFree(*sub_ptr_d);
+    *sub_ptr_d = nullptr;
+    if ((e = cudaMalloc(sub_ptr_d, sizeof(long long) * (n_parts + 1)))) return e;
+    cap_subptr = n_parts + 1;
+  }
   cudaMemcpyAsync(*sub_ptr_d, sub_ptr_h.data(), sizeof(long long) * (n_parts + 1), cudaMemcpyHostToDevice, s);
   sub_fill_kernel<<<n_parts, 128, 0, s>>>(bits, words, perm, segs_d, *sub_ptr_d, *sub_atoms_d);
   return cudaStreamSynchronize(s);

@@ -41,7 +41,7 @@ struct Partitioner {
   RcbSeg* segs_d = nullptr;
   unsigned* bits = nullptr;
   int* hcnt = nullptr;
-  int cap_n = 0, cap_seg = 0;
+  int cap_n = 0, cap_seg = 0, cap_hcnt = 0, cap_subptr = 0;
   long long cap_scr = 0, cap_bits = 0;
   int n_parts = 0;
   std::vector<RcbSeg> leaves;       // core segments in perm (host copy)
