@@ -65,7 +65,8 @@ typedef struct {
  * 2 = mixed BF16 (SP2 squares with two-way bf16 splitting; S^-1/2 and the core-row
  * back-transform three-way); 3 = pure bf16 SP2 squares (diagnostic).  In 1-3 the Ewald sums
  * run in FP32 with FP64 reductions; electron counts, energies and forces are summed in FP64.
- * kernel: 0 = K0 = -c_k0 I (SI Sec. B); 1 = preconditioned rank-m Krylov (SI Sec. B). */
+ * kernel: 0 = K0 = -c_k0 I (SI Sec. B); 1 = preconditioned rank-m Krylov (SI Sec. B);
+ * 2 = learned preconditioner (message-passing network, see sedacs_gnn_*), judged against 1. */
 typedef struct {
   double r_graph;       /* distance-graph cutoff, Angstrom */
   double tau;           /* |D| threshold of the density graph */
@@ -81,11 +82,13 @@ typedef struct {
   int32_t sp2_kmax;     /* maximum SP2 steps */
   int32_t ns_iters;     /* Newton-Schulz steps for S^-1/2 */
   double ewald_tol;     /* relative accuracy of the Ewald sums (0: 1e-12 FP64, 1e-8 mixed) */
+  int32_t judge_every;  /* kernel 2: every judge_every MD steps compare with the Krylov kernel */
+  double judge_tol;     /* kernel 2: relative error above which the Krylov kernel takes over */
 } sedacs_params;
 
 /* Fill p with the defaults (r_graph 3.0, tau 1e-3, core_size 32, precision 1, kernel 0,
  * krylov_rank 4, krylov_tol 1e-2, c_k0 0.5, scc_tol 1e-8, scc_alpha 0.2, sp2_tol 1e-9,
- * sp2_kmax 60, ns_iters 4, ewald_tol 0). */
+ * sp2_kmax 60, ns_iters 4, ewald_tol 0, judge_every 20, judge_tol 0.1). */
 void sedacs_default_params(sedacs_params* p);
 
 /* Create a context for N atoms of the given species in an orthorhombic periodic box
@@ -176,6 +179,34 @@ sedacs_status sedacs_scc_step(sedacs_ctx* ctx, const double* R, double* n, int32
 sedacs_status sedacs_xlbomd_init(sedacs_ctx* ctx, const double* R, const double* V, const double* n0, double mu);
 sedacs_status sedacs_xlbomd_step(sedacs_ctx* ctx, double* R, double* V, int32_t nsteps, double dt_fs,
                                  double* energies, double* n_out);
+
+/* ---- a13: learned charge-response preconditioner.  The paper names data-driven acceleration
+ * as an extension (Sec. "Summary and Conclusions"); the network is this library's reading:
+ * K_NN(y) = -c_k0 y + G(y), G a 3-layer, 64-wide message-passing network on the current atom
+ * graph that is linear in y (species embedding times y, radial edge filters of the minimum-image
+ * distance with a 6 A cosine cutoff, residual 64 x 64 mixes, linear read-out).  Parameters are a
+ * flat FP64 vector of sedacs_gnn_num_params() entries (device copy in FP32): e[3][64], then per
+ * layer C[8][64], A[64][64], B[64][64], then w[64].  Trained by Adam on pairs (x = J v, v) of the
+ * Krylov kernel's responses (SI Sec. B): with kernel 1 and collection on, every Krylov vector
+ * adds a pair to a ring of `capacity` pairs (device memory). */
+int32_t sedacs_gnn_num_params(void);
+sedacs_status sedacs_gnn_init(sedacs_ctx* ctx, uint64_t seed);
+sedacs_status sedacs_gnn_set_params(sedacs_ctx* ctx, const double* p);
+/* grad != 0: the gradient of the last sedacs_gnn_param_grad call instead of the parameters. */
+sedacs_status sedacs_gnn_get_params(sedacs_ctx* ctx, double* p, int32_t grad);
+/* u = K_NN(y) on the current graph and positions. */
+sedacs_status sedacs_gnn_apply(sedacs_ctx* ctx, const double* y, double* u);
+/* grad = d/dp sum_i gu_i K_NN(y)_i (host or device arrays as the I/O mode says). */
+sedacs_status sedacs_gnn_param_grad(sedacs_ctx* ctx, const double* y, const double* gu, double* grad);
+sedacs_status sedacs_gnn_collect(sedacs_ctx* ctx, int32_t on, int32_t capacity);
+/* Adam (lr) for `epochs` full-batch steps on the mean of |K_NN(x) - v|^2 over the given pairs
+ * (X, V: [n_pairs][N]) or, with X = NULL, over the collected pairs.  Losses of the first and
+ * the last step out. */
+sedacs_status sedacs_gnn_train(sedacs_ctx* ctx, const double* X, const double* V, int32_t n_pairs, int32_t epochs,
+                               double lr, double* loss_first, double* loss_last);
+/* Last judged relative error |K_NN f - K_m f| / |K_m f| and the number of fallbacks to the
+ * Krylov kernel during XL-BOMD with kernel 2. */
+sedacs_status sedacs_kernel_judge(sedacs_ctx* ctx, double* last_error, int32_t* fallbacks);
 
 /* Wall time (ms, CUDA events on the context stream) of the phases of the last call:
  * t[0] graph+halos, t[1] Coulomb, t[2] gather, t[3] S^-1/2 + h~, t[4] SP2, t[5] collect,

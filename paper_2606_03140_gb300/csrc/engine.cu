@@ -146,6 +146,22 @@ __global__ void matrix_to_f64_kernel(const uint8_t* arena, long long off, bool f
 
 inline int nblk(long long n, int tb) { return (int)((n + tb - 1) / tb); }
 
+// learned preconditioner (gnn.cu)
+cudaError_t gnn_prepare_params(sedacs_ctx* ctx);
+cudaError_t gnn_prepare(sedacs_ctx* ctx);
+void gnn_forward(sedacs_ctx* ctx, const double* y, double* u);
+void gnn_backward(sedacs_ctx* ctx, const double* y, const double* gu);
+void gnn_adam(sedacs_ctx* ctx, float lr);
+void gnn_zero_grad(sedacs_ctx* ctx);
+void gnn_set_params_f64(sedacs_ctx* ctx, const double* d_p);
+void gnn_get_params_f64(sedacs_ctx* ctx, double* d_p, bool grad);
+double gnn_train_step(sedacs_ctx* ctx, const double* X, const double* V, int n, float lr);
+
+void dev_dot_into(sedacs_ctx* ctx, const double* a, const double* b, double* out) {
+  dot_kernel<<<1, 1024, 0, ctx->stream>>>(a, b, ctx->N, out);
+  ctx->launches += 1;
+}
+
 }  // namespace sedacs
 
 // =============================================================================================
@@ -928,6 +944,13 @@ sedacs_status kernel_core(sedacs_ctx* ctx, const double* f, double* u, int* rank
   auto F_ = [&](int j) { return ctx->d_vec + (10LL + j) * N; };
   double* dq = ctx->d_vec + 18LL * N;
   double* r = ctx->d_vec + 19LL * N;
+  if (ctx->prm.kernel == 2) {
+    // learned preconditioner K_NN(f) = -c f + G(f) on the current graph
+    CUCHK(gnn_prepare(ctx));
+    gnn_forward(ctx, f, u);
+    *rank_out = 0;
+    return SEDACS_OK;
+  }
   scale_kernel<<<nblk(N, 128), 128, 0, s>>>(k0f, f, -c, N);
   ctx->launches += 1;
   int m_max = (ctx->prm.kernel == 1) ? std::min(8, std::max(0, ctx->prm.krylov_rank)) : 0;
@@ -956,6 +979,15 @@ sedacs_status kernel_core(sedacs_ctx* ctx, const double* f, double* u, int* rank
     STCHK(response_core(ctx, V_(j), dq));
     // f_vj = K0 (J v) = -c (dq - v)
     sub_kernel<<<nblk(N, 128), 128, 0, s>>>(F_(j), dq, V_(j), N);
+    GnnState& G = ctx->gnn;
+    if (G.collect && G.pair_cap > 0) {
+      // training pair of the learned preconditioner: x = J v, target v
+      const int slot = G.pair_head;
+      cudaMemcpyAsync(G.pX + (size_t)slot * N, F_(j), sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(G.pV + (size_t)slot * N, V_(j), sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
+      G.pair_head = (G.pair_head + 1) % G.pair_cap;
+      G.pairs = std::min(G.pairs + 1, G.pair_cap);
+    }
     scale_kernel<<<nblk(N, 128), 128, 0, s>>>(F_(j), F_(j), -c, N);
     ctx->launches += 3 + 2 * m;
     m = j + 1;
@@ -1010,6 +1042,8 @@ extern "C" {
 void sedacs_default_params(sedacs_params* p) {
   if (!p) return;
   std::memset(p, 0, sizeof(*p));
+  p->judge_every = 20;
+  p->judge_tol = 0.1;
   p->r_graph = 3.0;
   p->tau = 1e-3;
   p->core_size = 32;
@@ -1125,6 +1159,10 @@ void sedacs_destroy(sedacs_ctx* ctx) {
     if (e) cudaEventDestroy(e);
   for (auto& e : ctx->kev)
     if (e) cudaEventDestroy(e);
+  GnnState& G = ctx->gnn;
+  for (void* p : {(void*)G.P, (void*)G.grad, (void*)G.m, (void*)G.v, (void*)G.act, (void*)G.part, (void*)G.ebas,
+                  (void*)G.gu, (void*)G.u, (void*)G.pX, (void*)G.pV})
+    if (p) cudaFree(p);
   delete ctx;
 }
 
@@ -1417,6 +1455,24 @@ sedacs_status sedacs_xlbomd_step(sedacs_ctx* ctx, double* R, double* V, int32_t 
     sub_kernel<<<nblk(N, 128), 128, 0, s>>>(f, ctx->d_q, ctx->d_n, N);
     int rank = 0;
     STCHK(kernel_core(ctx, f, u, &rank));
+    if (ctx->prm.kernel == 2 && ctx->prm.judge_every > 0 && (ctx->md_step % ctx->prm.judge_every) == 0) {
+      // judge the learned kernel against the rank-m Krylov kernel; fall back when it drifts
+      double* um = ctx->d_vec + 22LL * N;
+      ctx->prm.kernel = 1;
+      int rk = 0;
+      STCHK(kernel_core(ctx, f, um, &rk));
+      sub_kernel<<<nblk(N, 128), 128, 0, s>>>(ctx->d_tmp2, u, um, N);
+      const double num = std::sqrt(dev_dot(ctx, ctx->d_tmp2, ctx->d_tmp2));
+      const double den = std::sqrt(dev_dot(ctx, um, um));
+      ctx->gnn.last_judge = den > 0 ? num / den : 0.0;
+      if (ctx->gnn.last_judge > ctx->prm.judge_tol) {
+        ctx->gnn.fallbacks += 1;
+        cudaMemcpyAsync(u, um, sizeof(double) * N, cudaMemcpyDeviceToDevice, s);   // keep Krylov from now on
+      } else {
+        ctx->prm.kernel = 2;
+      }
+    }
+    ctx->md_step += 1;
     xl_update_kernel<<<nblk(N, 128), 128, 0, s>>>(ctx->d_hist, ctx->hist_head, N, u, kappa, alpha, c[0], c[1], c[2],
                                                   c[3], c[4], c[5], ctx->d_n);
     ctx->hist_head = (ctx->hist_head + 1) % 6;
@@ -1470,6 +1526,155 @@ sedacs_status sedacs_kernel_apply(sedacs_ctx* ctx, const double* f, double* u, i
   if (rank) *rank = r;
   STCHK(copy_out(ctx, u, du, sizeof(double) * ctx->N));
   CUCHK(cudaStreamSynchronize(ctx->stream));
+  return SEDACS_OK;
+}
+
+// ---- learned preconditioner ---------------------------------------------------------------------
+int32_t sedacs_gnn_num_params(void) { return gnn_num_params(); }
+
+sedacs_status sedacs_gnn_set_params(sedacs_ctx* ctx, const double* p) {
+  if (!ctx || !p) return SEDACS_EINVAL;
+  CUCHK(gnn_prepare_params(ctx));
+  double* tmp = nullptr;
+  CUCHK(cudaMalloc(&tmp, sizeof(double) * gnn_num_params()));
+  cudaMemcpyAsync(tmp, p, sizeof(double) * gnn_num_params(), cudaMemcpyDefault, ctx->stream);
+  gnn_set_params_f64(ctx, tmp);
+  cudaStreamSynchronize(ctx->stream);
+  cudaFree(tmp);
+  ctx->gnn.t = 0;
+  cudaMemsetAsync(ctx->gnn.m, 0, sizeof(float) * gnn_num_params(), ctx->stream);
+  cudaMemsetAsync(ctx->gnn.v, 0, sizeof(float) * gnn_num_params(), ctx->stream);
+  return check_dev_err(ctx);
+}
+
+sedacs_status sedacs_gnn_get_params(sedacs_ctx* ctx, double* p, int32_t grad) {
+  if (!ctx || !p) return SEDACS_EINVAL;
+  CUCHK(gnn_prepare_params(ctx));
+  double* tmp = nullptr;
+  CUCHK(cudaMalloc(&tmp, sizeof(double) * gnn_num_params()));
+  gnn_get_params_f64(ctx, tmp, grad != 0);
+  cudaMemcpyAsync(p, tmp, sizeof(double) * gnn_num_params(), cudaMemcpyDefault, ctx->stream);
+  cudaStreamSynchronize(ctx->stream);
+  cudaFree(tmp);
+  return SEDACS_OK;
+}
+
+sedacs_status sedacs_gnn_init(sedacs_ctx* ctx, uint64_t seed) {
+  if (!ctx) return SEDACS_EINVAL;
+  // seeded normal weights (SplitMix64 + Box-Muller), 1/sqrt(fan-in) scaled, small output layer
+  const int n = gnn_num_params();
+  std::vector<double> p(n);
+  uint64_t st = seed;
+  auto next = [&]() {
+    uint64_t z = (st += 0x9E3779B97F4A7C15ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return (double)((z ^ (z >> 31)) >> 11) * (1.0 / 9007199254740992.0);
+  };
+  for (int k = 0; k < n; ++k) {
+    const double u1 = std::max(next(), 1e-300), u2 = next();
+    p[k] = std::sqrt(-2.0 * std::log(u1)) * std::cos(2.0 * M_PI * u2);
+  }
+  const int Wd = 64, NBs = 8;
+  for (int k = 0; k < 3 * Wd; ++k) p[k] *= 0.1;
+  int o = 3 * Wd;
+  for (int l = 0; l < 3; ++l) {
+    for (int k = 0; k < NBs * Wd; ++k) p[o + k] *= 0.1;
+    o += NBs * Wd;
+    for (int k = 0; k < 2 * Wd * Wd; ++k) p[o + k] *= 0.1 / 8.0;
+    o += 2 * Wd * Wd;
+  }
+  for (int k = 0; k < Wd; ++k) p[o + k] *= 0.01;
+  const bool io = ctx->dev_io;
+  ctx->dev_io = false;
+  const sedacs_status r = sedacs_gnn_set_params(ctx, p.data());
+  ctx->dev_io = io;
+  return r;
+}
+
+sedacs_status sedacs_gnn_apply(sedacs_ctx* ctx, const double* y, double* u) {
+  if (!ctx || !y || !u || !ctx->have_graph) return SEDACS_EINVAL;
+  double* dy = ctx->d_vec + 22LL * ctx->N;
+  double* du = ctx->d_vec + 23LL * ctx->N;
+  STCHK(copy_in(ctx, dy, y, ctx->N));
+  CUCHK(gnn_prepare(ctx));
+  gnn_forward(ctx, dy, du);
+  STCHK(copy_out(ctx, u, du, sizeof(double) * ctx->N));
+  CUCHK(cudaStreamSynchronize(ctx->stream));
+  return check_dev_err(ctx);
+}
+
+sedacs_status sedacs_gnn_param_grad(sedacs_ctx* ctx, const double* y, const double* gu, double* grad) {
+  if (!ctx || !y || !gu || !grad || !ctx->have_graph) return SEDACS_EINVAL;
+  double* dy = ctx->d_vec + 22LL * ctx->N;
+  double* dg = ctx->d_vec + 23LL * ctx->N;
+  STCHK(copy_in(ctx, dy, y, ctx->N));
+  STCHK(copy_in(ctx, dg, gu, ctx->N));
+  CUCHK(gnn_prepare(ctx));
+  gnn_zero_grad(ctx);
+  gnn_forward(ctx, dy, ctx->gnn.u);
+  gnn_backward(ctx, dy, dg);
+  CUCHK(cudaStreamSynchronize(ctx->stream));
+  const bool io = ctx->dev_io;
+  ctx->dev_io = false;
+  const sedacs_status r = sedacs_gnn_get_params(ctx, grad, 1);
+  ctx->dev_io = io;
+  return r;
+}
+
+sedacs_status sedacs_gnn_collect(sedacs_ctx* ctx, int32_t on, int32_t capacity) {
+  if (!ctx || capacity < 0) return SEDACS_EINVAL;
+  GnnState& G = ctx->gnn;
+  if (on && capacity > G.pair_cap) {
+    if (G.pX) cudaFree(G.pX);
+    if (G.pV) cudaFree(G.pV);
+    G.pX = G.pV = nullptr;
+    CUCHK(cudaMalloc(&G.pX, sizeof(double) * (size_t)capacity * ctx->N));
+    CUCHK(cudaMalloc(&G.pV, sizeof(double) * (size_t)capacity * ctx->N));
+    G.pair_cap = capacity;
+    G.pairs = G.pair_head = 0;
+  }
+  G.collect = on != 0;
+  return SEDACS_OK;
+}
+
+sedacs_status sedacs_gnn_train(sedacs_ctx* ctx, const double* X, const double* V, int32_t n_pairs, int32_t epochs,
+                               double lr, double* loss_first, double* loss_last) {
+  if (!ctx || epochs <= 0 || !ctx->have_graph) return SEDACS_EINVAL;
+  GnnState& G = ctx->gnn;
+  const int N = ctx->N;
+  const double* dX = G.pX;
+  const double* dV = G.pV;
+  int n = G.pairs;
+  double* own = nullptr;
+  if (X) {
+    if (!V || n_pairs <= 0) return SEDACS_EINVAL;
+    CUCHK(cudaMalloc(&own, sizeof(double) * 2 * (size_t)n_pairs * N));
+    cudaMemcpyAsync(own, X, sizeof(double) * (size_t)n_pairs * N, cudaMemcpyDefault, ctx->stream);
+    cudaMemcpyAsync(own + (size_t)n_pairs * N, V, sizeof(double) * (size_t)n_pairs * N, cudaMemcpyDefault, ctx->stream);
+    dX = own;
+    dV = own + (size_t)n_pairs * N;
+    n = n_pairs;
+  }
+  if (n <= 0) { ctx->err = "no training pairs"; return SEDACS_EINVAL; }
+  CUCHK(gnn_prepare(ctx));
+  double l0 = 0.0, l1 = 0.0;
+  for (int e = 0; e < epochs; ++e) {
+    const double l = gnn_train_step(ctx, dX, dV, n, (float)lr);
+    if (e == 0) l0 = l;
+    l1 = l;
+  }
+  CUCHK(cudaStreamSynchronize(ctx->stream));
+  if (own) cudaFree(own);
+  if (loss_first) *loss_first = l0;
+  if (loss_last) *loss_last = l1;
+  return check_dev_err(ctx);
+}
+
+sedacs_status sedacs_kernel_judge(sedacs_ctx* ctx, double* last_error, int32_t* fallbacks) {
+  if (!ctx) return SEDACS_EINVAL;
+  if (last_error) *last_error = ctx->gnn.last_judge;
+  if (fallbacks) *fallbacks = ctx->gnn.fallbacks;
   return SEDACS_OK;
 }
 

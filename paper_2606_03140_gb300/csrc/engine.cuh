@@ -51,6 +51,20 @@ enum OpId : int {
   OP_NUM
 };
 
+// Learned preconditioner (gnn.cu): parameters, Adam moments, activations, training pairs.
+struct GnnState {
+  float *P = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr, *act = nullptr, *part = nullptr, *ebas = nullptr;
+  long long ebas_cap = 0;
+  int nchunk = 0;
+  int t = 0;                 // Adam step count
+  double *gu = nullptr, *u = nullptr;
+  bool collect = false;      // store (J v, v) pairs produced by the Krylov kernel
+  double *pX = nullptr, *pV = nullptr;
+  int pairs = 0, pair_cap = 0, pair_head = 0;
+  int fallbacks = 0;         // judge decisions that returned to the Krylov kernel
+  double last_judge = -1.0;  // last relative error |K_NN f - K_m f| / |K_m f|
+};
+
 struct Layout {
   int n_sub = 0;
   std::vector<int> n_real, n_pad, m_pad, n_core_orb, n_core_atoms, n_atoms;
@@ -62,6 +76,7 @@ struct Layout {
   std::vector<int> n_diag;
 };
 
+int gnn_num_params();
 }  // namespace sedacs
 
 #include <unordered_map>
@@ -156,8 +171,11 @@ struct sedacs_ctx {
   std::vector<int> sp2_iters_h;
   double e_band = 0, e_coul = 0, e_rep = 0;
   bool have_forces = false;
+  // learned preconditioner
+  sedacs::GnnState gnn;
   // MD
   bool md_ready = false;
+  long long md_step = 0;
   int hist_head = 0;
   // timing of the SP2 square kernel (per launch, events on the context stream)
   bool kstats = false;

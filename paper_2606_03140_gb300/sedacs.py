@@ -37,7 +37,7 @@ class sedacs_params(C.Structure):
                 ("kernel", C.c_int32), ("krylov_rank", C.c_int32), ("krylov_tol", C.c_double),
                 ("c_k0", C.c_double), ("scc_tol", C.c_double), ("scc_alpha", C.c_double),
                 ("sp2_tol", C.c_double), ("sp2_kmax", C.c_int32), ("ns_iters", C.c_int32),
-                ("ewald_tol", C.c_double)]
+                ("ewald_tol", C.c_double), ("judge_every", C.c_int32), ("judge_tol", C.c_double)]
 
 
 def _load():
@@ -75,6 +75,15 @@ def _load():
         "sedacs_kernel_stats": (I32, [P, I32, P, P, P]),
         "sedacs_set_params": (I32, [P, P]),
         "sedacs_graph_build_noalloc": (I32, [P, I32, P, D, P, P, I64, P, P]),
+        "sedacs_gnn_num_params": (I32, []),
+        "sedacs_gnn_init": (I32, [P, C.c_uint64]),
+        "sedacs_gnn_set_params": (I32, [P, P]),
+        "sedacs_gnn_get_params": (I32, [P, P, I32]),
+        "sedacs_gnn_apply": (I32, [P, P, P]),
+        "sedacs_gnn_param_grad": (I32, [P, P, P, P]),
+        "sedacs_gnn_collect": (I32, [P, I32, I32]),
+        "sedacs_gnn_train": (I32, [P, P, P, I32, I32, D, P, P]),
+        "sedacs_kernel_judge": (I32, [P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -91,7 +100,9 @@ EXPORTED = (
     "sedacs_energy", "sedacs_forces", "sedacs_density_graph_size", "sedacs_density_graph_get",
     "sedacs_subgraph_matrix", "sedacs_charge_response", "sedacs_kernel_apply", "sedacs_scc_step",
     "sedacs_xlbomd_init", "sedacs_xlbomd_step", "sedacs_phase_times", "sedacs_reset_counters",
-    "sedacs_kernel_stats", "sedacs_set_params", "sedacs_graph_build_noalloc",
+    "sedacs_kernel_stats", "sedacs_set_params", "sedacs_graph_build_noalloc", "sedacs_gnn_num_params",
+    "sedacs_gnn_init", "sedacs_gnn_set_params", "sedacs_gnn_get_params", "sedacs_gnn_apply", "sedacs_gnn_param_grad",
+    "sedacs_gnn_collect", "sedacs_gnn_train", "sedacs_kernel_judge",
 )
 
 
@@ -326,3 +337,60 @@ def sedacs_graph_build_noalloc(R_dev, box, r_graph: float, row_ptr_dev, col_dev,
     if st not in (0, 8):
         _check(None, st)
     return st, nnz.value
+
+
+def sedacs_gnn_num_params() -> int:
+    return int(_lib.sedacs_gnn_num_params())
+
+
+def sedacs_gnn_init(ctx, seed: int):
+    _check(ctx, _lib.sedacs_gnn_init(ctx, C.c_uint64(seed)))
+
+
+def sedacs_gnn_set_params(ctx, p):
+    p = np.ascontiguousarray(p, dtype=np.float64)
+    _check(ctx, _lib.sedacs_gnn_set_params(ctx, _ptr(p)))
+
+
+def sedacs_gnn_get_params(ctx, grad: bool = False):
+    out = np.zeros(sedacs_gnn_num_params())
+    _check(ctx, _lib.sedacs_gnn_get_params(ctx, _ptr(out), 1 if grad else 0))
+    return out
+
+
+def sedacs_gnn_apply(ctx, y):
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    u = np.zeros_like(y)
+    _check(ctx, _lib.sedacs_gnn_apply(ctx, _ptr(y), _ptr(u)))
+    return u
+
+
+def sedacs_gnn_param_grad(ctx, y, gu):
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    gu = np.ascontiguousarray(gu, dtype=np.float64)
+    g = np.zeros(sedacs_gnn_num_params())
+    _check(ctx, _lib.sedacs_gnn_param_grad(ctx, _ptr(y), _ptr(gu), _ptr(g)))
+    return g
+
+
+def sedacs_gnn_collect(ctx, on: bool, capacity: int = 256):
+    _check(ctx, _lib.sedacs_gnn_collect(ctx, 1 if on else 0, capacity))
+
+
+def sedacs_gnn_train(ctx, X=None, V=None, epochs: int = 100, lr: float = 1e-3):
+    l0 = C.c_double()
+    l1 = C.c_double()
+    if X is not None:
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        V = np.ascontiguousarray(V, dtype=np.float64)
+        _check(ctx, _lib.sedacs_gnn_train(ctx, _ptr(X), _ptr(V), X.shape[0], epochs, lr, C.byref(l0), C.byref(l1)))
+    else:
+        _check(ctx, _lib.sedacs_gnn_train(ctx, None, None, 0, epochs, lr, C.byref(l0), C.byref(l1)))
+    return l0.value, l1.value
+
+
+def sedacs_kernel_judge(ctx):
+    e = C.c_double()
+    n = C.c_int32()
+    _check(ctx, _lib.sedacs_kernel_judge(ctx, C.byref(e), C.byref(n)))
+    return e.value, n.value
