@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--workload", default="water9000")
     ap.add_argument("--dt", type=float, default=0.25)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="small ncu case: 3,000-atom water box, two densities, the second inside NVTX range 'second'")
     ap.add_argument("--quick-setup", action="store_true",
                     help="start the dynamics from zero charges instead of the SCC ground state "
                          "(same per-step work; used to time the slow plain FP64 form)")
@@ -341,8 +343,35 @@ def run_reference(args, world, rank):
             "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def profile_case(args):
+    """Small case for kernel captures: 3,000-atom water box (1,000 H2O, 31 A), distance graph,
+    RCB cores, one density, graph rebuilt from it, a second density inside NVTX range 'second'."""
+    import torch
+
+    from paper_2606_03140_gb300 import inputs as I
+    from paper_2606_03140_gb300 import sedacs as S
+
+    s = I.small_water_box(1000, 31.0, seed=33)
+    R = np.ascontiguousarray(s.R)
+    ctx = S.sedacs_create(s.species, s.box, I.default_model(),
+                          S.sedacs_default_params(core_size=32, precision=args.precision))
+    S.sedacs_graph_build(ctx, R)
+    P = S.sedacs_partition(ctx, R)
+    n = np.zeros(s.n_atoms)
+    S.sedacs_subgraph_density(ctx, R, n, mu=-0.13, n_parts=P)
+    S.sedacs_graph_build(ctx, R, use_prev_D=True)
+    torch.cuda.nvtx.range_push("second")
+    _, q, _, it = S.sedacs_subgraph_density(ctx, R, n, mu=-0.13, n_parts=P)
+    torch.cuda.nvtx.range_pop()
+    S.sedacs_destroy(ctx)
+    print(json.dumps({"profile_case": "water3000", "subgraphs": P, "sp2_steps_mean": float(it.mean())}))
+
+
 def main():
     args = parse()
+    if args.profile_case:
+        profile_case(args)
+        return
     world, rank, local = dist_init()
     if args.impl == "reference":
         out = run_reference(args, world, rank)
