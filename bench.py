@@ -235,7 +235,7 @@ def run_ours(args, world, rank, local):
     nsplit_products = {1: 6, 2: 3, 3: 1}.get(args.precision, 6)
     achieved = (2.0 * k_pairs / max(k_launch, 1)) / (k_ms / max(k_launch, 1) / 1e3) / 1e12 if k_ms > 0 else None
     peak = bf16 / nsplit_products
-    roof = {"kernel": "tc_gemm_kernel (SP2 square, split-bf16 tcgen05)", "bound": "tensor",
+    roof = {"kernel": "tc_gemm_persistent (SP2 square, split-bf16 tcgen05)", "bound": "tensor",
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": (achieved / peak) if achieved else None, "traffic": None,
             "peak_note": f"measured sustained bf16 {bf16} TF/s / {nsplit_products} split products (of measured)",

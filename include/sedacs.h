@@ -80,7 +80,7 @@ typedef struct {
   double scc_alpha;     /* linear mixing coefficient */
   double sp2_tol;       /* SP2 stop: Tr(X - X^2) < sp2_tol * n_orbitals */
   int32_t sp2_kmax;     /* maximum SP2 steps */
-  int32_t ns_iters;     /* Newton-Schulz steps for S^-1/2 */
+  int32_t ns_iters;     /* Newton-Schulz steps for S^-1/2 (0: 3 in the mixed forms, 4 in FP64) */
   double ewald_tol;     /* relative accuracy of the Ewald sums (0: 1e-12 FP64, 1e-8 mixed) */
   int32_t judge_every;  /* kernel 2: every judge_every MD steps compare with the Krylov kernel */
   double judge_tol;     /* kernel 2: relative error above which the Krylov kernel takes over */
@@ -88,7 +88,7 @@ typedef struct {
 
 /* Fill p with the defaults (r_graph 3.0, tau 1e-3, core_size 32, precision 1, kernel 0,
  * krylov_rank 4, krylov_tol 1e-2, c_k0 0.5, scc_tol 1e-8, scc_alpha 0.2, sp2_tol 1e-9,
- * sp2_kmax 60, ns_iters 4, ewald_tol 0, judge_every 20, judge_tol 0.1). */
+ * sp2_kmax 60, ns_iters 0, ewald_tol 0, judge_every 20, judge_tol 0.1). */
 void sedacs_default_params(sedacs_params* p);
 
 /* Create a context for N atoms of the given species in an orthorhombic periodic box

@@ -1,14 +1,15 @@
 // Batched GEMMs over the per-subgraph matrices.
 //
-//  * tc_gemm<NSPLIT>: 5th-generation tensor cores.  One CTA per 128x128 output tile, four
-//    warps.  Thread 0 streams 16 KB operand blocks (already in the swizzled shared-memory
-//    image, see blocked_offset) with bulk copies into a 2-3 stage ring guarded by
-//    mbarriers; thread 32 issues tcgen05.mma (M=128, N=128, K=16, bf16 in, fp32 in TMEM)
-//    over the split products hi*hi (+ hi*mid + mid*hi (+ hi*lo + mid*mid + lo*hi)) and
-//    commits to the ring's "empty" barriers; all four warps then drain TMEM with
-//    tcgen05.ld and run the epilogue (generic alpha*AB^T + beta*I, or one step of the
-//    mu-branch SP2 recursion with its trace partials) writing the fp32 master and the
-//    split planes of the result.
+//  * tc_gemm_persistent<NSPLIT>: 5th-generation tensor cores, one persistent CTA per SM,
+//    six warps.  A producer lane streams 16 KB operand blocks (already in the swizzled
+//    shared-memory image, see blocked_offset) with bulk copies into a 2-3 stage ring guarded
+//    by mbarriers, across tile boundaries; an MMA lane issues tcgen05.mma (M=128, N=128,
+//    K=16, bf16 in, fp32 in TMEM) over the split products hi*hi (+ hi*mid + mid*hi (+ hi*lo
+//    + mid*mid + lo*hi)) and commits to the ring's "empty" barriers; four epilogue warps
+//    drain TMEM with tcgen05.ld, hand it back to the MMA lane for the next tile, and run the
+//    epilogue (generic alpha*AB^T + beta*I + g1*C1 + g2*C2, or one step of the mu-branch SP2
+//    recursion with its trace partials) writing the fp32 master and the split planes of the
+//    result, overlapped with the next tile's MMAs.
 //  * f64_gemm: the same problems and epilogues in FP64 on the CUDA cores (64x64 tiles).
 #include "dense.cuh"
 
@@ -43,53 +44,48 @@ __device__ __forceinline__ void store_planes8(uint8_t* arena, long long base, lo
   if (nsplit > 2) *reinterpret_cast<uint4*>(arena + off + 2 * plane) = *reinterpret_cast<const uint4*>(l);
 }
 
+// ------------------------------------------------------------------------------------------
+// Persistent, warp-specialised split-bf16 GEMM.  One CTA per SM walks the work list (128x128
+// output tiles) with a stride of gridDim.x.  Warp 4 (one lane) streams the operand blocks of consecutive
+// tiles through the stage ring without pausing at tile boundaries; warp 5 (one lane) issues
+// the MMAs of a tile once the epilogue has drained the previous tile's accumulators; warps
+// 0-3 drain TMEM into registers, release it at once, and then run the epilogue math and stores
+// while the next tile's MMAs proceed.  Every wait is bounded.
+// ------------------------------------------------------------------------------------------
 template <int NSPLIT>
-__global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const GemmParams p) {
+struct TcPCfg {
+  static constexpr int kStages = TcCfg<NSPLIT>::kStages;
+  static constexpr int kStageBytes = TcCfg<NSPLIT>::kStageBytes;
+  static constexpr int kTransBytes = 4 * 32 * 33 * 4;
+  static constexpr int kSmem = kStages * kStageBytes + kTransBytes + 1024 + 256;
+};
+
+template <int NSPLIT>
+__global__ void __launch_bounds__(192, 1) tc_gemm_persistent(const GemmParams p, int n_work) {
   using Cfg = TcCfg<NSPLIT>;
+  using PCfg = TcPCfg<NSPLIT>;
+  if (*reinterpret_cast<volatile int*>(p.err) & kErrTimeout) return;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + Cfg::kStages * Cfg::kStageBytes);
+  float* tbuf = reinterpret_cast<float*>(smem + Cfg::kStages * Cfg::kStageBytes);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + Cfg::kStages * Cfg::kStageBytes + PCfg::kTransBytes);
   uint64_t* empty = full + Cfg::kStages;
-  uint64_t* accb = empty + Cfg::kStages;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accb + 1);
-  float* red = reinterpret_cast<float*>(tmem_slot + 4);
-
-  // a CTA that finds the timeout flag raised by another CTA exits at once
-  if (*reinterpret_cast<volatile int*>(p.err) & kErrTimeout) return;
-  const GemmWork w = p.work[blockIdx.x];
-  const GemmMat m = p.mats[w.mat];
-  int cur = 0;
-  int branch_sq = 0;
-  const bool stepping = (p.mode == kModeSp2 || p.mode == kModeRsp);
-  if (stepping) {
-    const Sp2State st = p.sp2[w.mat];
-    if (!st.active) return;
-    cur = st.cur;
-    branch_sq = st.y >= 0.5;
-  } else if (m.b_from_sp2 || m.a_from_sp2 || m.c_from_sp2) {
-    cur = p.sp2[w.mat].cur;
-  }
+  uint64_t* accf = empty + Cfg::kStages;
+  uint64_t* acce = accf + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long in_shift = stepping ? cur * m.buf_stride : 0;
-  const long long out_shift = stepping ? (1 - cur) * m.buf_stride : 0;
-  const uint8_t* A = p.arena + m.a_off + (stepping ? in_shift : (m.a_from_sp2 ? cur * m.buf_stride : 0));
-  const uint8_t* B = p.arena + m.b_off + (stepping ? in_shift : (m.b_from_sp2 ? cur * m.buf_stride : 0));
-  const int nkb = m.n_pad >> 6;
-  const int kb_end = (m.k_real + 63) >> 6;
+  const bool stepping = (p.mode == kModeSp2 || p.mode == kModeRsp);
+  constexpr uint32_t kTmemCols = NSPLIT > 1 ? 512 : 128;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < Cfg::kStages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(accb, 1);
+    mbar_init(accf, 1);
+    mbar_init(acce, 4);
     fence_mbar_init();
   }
-  // TMEM: the leading hi*hi products go to three accumulators by k-block (columns [0,384)),
-  // the split-correction products to a fourth ([384,512)): each accumulator takes few adds
-  // and the small corrections are not summed against the large partial sums; the epilogue
-  // adds the four in FP32.
-  constexpr uint32_t kTmemCols = NSPLIT > 1 ? 512 : 128;
   if (warp == 0) {
     tmem_alloc(tmem_slot, kTmemCols);
     tmem_relinquish();
@@ -100,226 +96,263 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const GemmParams p) {
   const uint32_t tmem = *tmem_slot;
   bool ok = true;
 
-  if (threadIdx.x == 0) {
-    // ---- producer: bulk copies of the operand blocks -------------------------------
-    for (int kb = 0; kb < kb_end; ++kb) {
-      const int s = kb % Cfg::kStages;
-      const int round = kb / Cfg::kStages;
-      if (kb >= Cfg::kStages && !mbar_wait(&empty[s], (round - 1) & 1)) {
-        ok = false;
-        break;
-      }
-      mbar_arrive_expect_tx(&full[s], Cfg::kStageBytes);
-      uint8_t* st = smem + s * Cfg::kStageBytes;
-      const long long aoff = ((long long)w.tm * nkb + kb) * kBlkBytes;
-      const long long boff = ((long long)w.tn * nkb + kb) * kBlkBytes;
-#pragma unroll
-      for (int pl = 0; pl < NSPLIT; ++pl) {
-        bulk_g2s(st + pl * kBlkBytes, A + pl * m.a_plane + aoff, kBlkBytes, &full[s]);
-        bulk_g2s(st + (NSPLIT + pl) * kBlkBytes, B + pl * m.b_plane + boff, kBlkBytes, &full[s]);
-      }
-    }
-  } else if (threadIdx.x == 32) {
-    // ---- MMA issuer -------------------------------------------------------------------
-    constexpr uint32_t idesc = idesc_bf16_f32(128, 128);
-    for (int kb = 0; kb < kb_end; ++kb) {
-      const int s = kb % Cfg::kStages;
-      const int round = kb / Cfg::kStages;
-      if (!mbar_wait(&full[s], round & 1)) {
-        ok = false;
-        break;
-      }
-      tc_fence_after();
-      const uint32_t st = smem_u32(smem + s * Cfg::kStageBytes);
-#pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {
-#pragma unroll
-        for (int pr = 0; pr < Cfg::kNumProd; ++pr) {
-          int pa, pb;
-          prod_planes(pr, pa, pb);
-          const uint64_t ad = smem_desc_sw128(st + pa * kBlkBytes + kk * 32);
-          const uint64_t bd = smem_desc_sw128(st + (NSPLIT + pb) * kBlkBytes + kk * 32);
-          const int hsel = kb % 3;
-          const uint32_t acc_col = (NSPLIT == 1) ? 0u : (pr == 0 ? 128u * hsel : 384u);
-          // the first product into each accumulator starts it
-          uint32_t accum;
-          if (NSPLIT == 1) accum = (kb | kk) != 0 ? 1u : 0u;
-          else if (pr == 0) accum = (kb >= 3 || kk != 0) ? 1u : 0u;
-          else accum = (pr == 1 && (kb | kk) == 0) ? 0u : 1u;
-          tc_mma_bf16(tmem + acc_col, ad, bd, idesc, accum);
-        }
-      }
-      tc_commit(&empty[s]);
-    }
-    tc_commit(accb);
-  }
-  // while the tensor cores run, pull this thread's epilogue input rows (X / C1 / C2 masters)
-  // towards L2 so the epilogue does not wait on DRAM
-  {
-    const int prow = w.tm * 128 + warp * 32 + lane;
-    const long long roff = ((long long)prow * m.n_pad + w.tn * 128) * 4;
-    const uint8_t* pre[3] = {nullptr, nullptr, nullptr};
-    if (stepping) pre[0] = p.arena + m.x_off + in_shift + roff;
-    if (p.mode == kModeRsp) pre[1] = p.arena + m.c_off + roff;
-    if (p.mode == kModeGeneric && m.c_off >= 0) pre[1] = p.arena + m.c_off + (m.c_from_sp2 ? cur * m.buf_stride : 0) + roff;
-    if (p.mode == kModeGeneric && m.c2_off >= 0) pre[2] = p.arena + m.c2_off + roff;
-    if (prow < m.m_real)
-      for (int u = 0; u < 3; ++u)
-        if (pre[u])
-#pragma unroll
-          for (int q = 0; q < 4; ++q) asm volatile("prefetch.global.L2 [%0];" ::"l"(pre[u] + q * 128));
-  }
-  __syncwarp();
-  if (!mbar_wait(accb, 0)) ok = false;
-  tc_fence_after();
+  // tiles of finished SP2 subgraphs are skipped by every role alike
+  auto tile_live = [&](const GemmWork& w) -> bool { return !stepping || p.sp2[w.mat].active; };
+  auto tile_cur = [&](const GemmWork& w, const GemmMat& m) -> int {
+    return (stepping || m.b_from_sp2 || m.a_from_sp2 || m.c_from_sp2) ? p.sp2[w.mat].cur : 0;
+  };
 
-  // ---- epilogue: 128 threads, thread = output row --------------------------------------
-  const int row_local = warp * 32 + lane;
-  const int row = w.tm * 128 + row_local;
-  const uint32_t t_row = tmem + ((uint32_t)(warp * 32) << 16);
-  const bool diag_tile = (w.tm == w.tn);
-  float tr_x = 0.f, tr_x2 = 0.f;
-  float* outm = (m.out_off >= 0) ? reinterpret_cast<float*>(p.arena + m.out_off + out_shift) : nullptr;
-  const float* xm = stepping ? reinterpret_cast<const float*>(p.arena + m.x_off + in_shift) : nullptr;
-  const float* cm = (p.mode == kModeRsp) ? reinterpret_cast<const float*>(p.arena + m.c_off) : nullptr;
-  const bool row_ok = row < m.m_real;
-#pragma unroll 1
-  for (int c = 0; c < 4; ++c) {
-    float v[32];
-    tmem_ld32(t_row + c * 32, v);
-    if (NSPLIT > 1) {
-      // accumulators 1, 2 hold hi*hi of k-blocks 1, 2 mod 3 (empty when fewer k-blocks)
-      if (kb_end > 1) {
-        float v2[32];
-        tmem_ld32(t_row + 128 + c * 32, v2);
+  if (warp == 4) {
+    if (lane == 0) {
+      long long g = 0;
+      for (int t = blockIdx.x; t < n_work && ok; t += gridDim.x) {
+        const GemmWork w = p.work[t];
+        if (!tile_live(w)) continue;
+        const GemmMat m = p.mats[w.mat];
+        const int cur = tile_cur(w, m);
+        const long long in_shift = stepping ? cur * m.buf_stride : 0;
+        const uint8_t* A = p.arena + m.a_off + (stepping ? in_shift : (m.a_from_sp2 ? cur * m.buf_stride : 0));
+        const uint8_t* B = p.arena + m.b_off + (stepping ? in_shift : (m.b_from_sp2 ? cur * m.buf_stride : 0));
+        const int nkb = m.n_pad >> 6, kb_end = (m.k_real + 63) >> 6;
+        for (int kb = 0; kb < kb_end; ++kb, ++g) {
+          const int s = (int)(g % Cfg::kStages);
+          const long long round = g / Cfg::kStages;
+          if (g >= Cfg::kStages && !mbar_wait(&empty[s], (uint32_t)((round - 1) & 1))) { ok = false; break; }
+          mbar_arrive_expect_tx(&full[s], Cfg::kStageBytes);
+          uint8_t* st = smem + s * Cfg::kStageBytes;
+          const long long aoff = ((long long)w.tm * nkb + kb) * kBlkBytes;
+          const long long boff = ((long long)w.tn * nkb + kb) * kBlkBytes;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] += v2[j];
-      }
-      if (kb_end > 2) {
-        float v2[32];
-        tmem_ld32(t_row + 256 + c * 32, v2);
-#pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] += v2[j];
-      }
-      float v3[32];
-      tmem_ld32(t_row + 384 + c * 32, v3);
-#pragma unroll
-      for (int j = 0; j < 32; ++j) v[j] += v3[j];
-    }
-    const int col0 = w.tn * 128 + c * 32;
-    if (p.mode == kModeRsp) {
-      const float4* sx = reinterpret_cast<const float4*>(xm + (long long)row * m.n_pad + col0);
-      const float4* sc = reinterpret_cast<const float4*>(cm + (long long)row * m.n_pad + col0);
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const float4 a = sx[q], c4 = sc[q];
-        const float xa[4] = {a.x, a.y, a.z, a.w}, ca[4] = {c4.x, c4.y, c4.z, c4.w};
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int j = 4 * q + e;
-          const bool ok_ij = row_ok && (col0 + j) < m.n_real;
-          const float sum = v[j] + ca[e];
-          v[j] = ok_ij ? (branch_sq ? sum : 2.f * xa[e] - sum) : 0.f;
+          for (int pl = 0; pl < NSPLIT; ++pl) {
+            bulk_g2s(st + pl * kBlkBytes, A + pl * m.a_plane + aoff, kBlkBytes, &full[s]);
+            bulk_g2s(st + (NSPLIT + pl) * kBlkBytes, B + pl * m.b_plane + boff, kBlkBytes, &full[s]);
+          }
         }
       }
-    } else if (p.mode == kModeSp2) {
-      float x[32];
-      const float4* src = reinterpret_cast<const float4*>(xm + (long long)row * m.n_pad + col0);
+      // the last copies issued into each stage have landed before shared memory is released
+      // (already true on the normal path; bounded on the error path)
+      for (long long q = g - 1; q >= 0 && q >= g - Cfg::kStages; --q)
+        mbar_wait(&full[q % Cfg::kStages], (uint32_t)((q / Cfg::kStages) & 1));
+    }
+  } else if (warp == 5) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_bf16_f32(128, 128);
+      long long g = 0;
+      int ti = 0;
+      for (int t = blockIdx.x; t < n_work && ok; t += gridDim.x) {
+        const GemmWork w = p.work[t];
+        if (!tile_live(w)) continue;
+        const GemmMat m = p.mats[w.mat];
+        const int kb_end = (m.k_real + 63) >> 6;
+        if (ti > 0 && !mbar_wait(acce, (uint32_t)((ti - 1) & 1))) { ok = false; break; }
+        tc_fence_after();
+        for (int kb = 0; kb < kb_end; ++kb, ++g) {
+          const int s = (int)(g % Cfg::kStages);
+          const long long round = g / Cfg::kStages;
+          if (!mbar_wait(&full[s], (uint32_t)(round & 1))) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t st = smem_u32(smem + s * Cfg::kStageBytes);
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const float4 t = src[q];
-        x[4 * q] = t.x; x[4 * q + 1] = t.y; x[4 * q + 2] = t.z; x[4 * q + 3] = t.w;
+          for (int kk = 0; kk < 4; ++kk) {
+#pragma unroll
+            for (int pr = 0; pr < Cfg::kNumProd; ++pr) {
+              int pa, pb;
+              prod_planes(pr, pa, pb);
+              const uint64_t ad = smem_desc_sw128(st + pa * kBlkBytes + kk * 32);
+              const uint64_t bd = smem_desc_sw128(st + (NSPLIT + pb) * kBlkBytes + kk * 32);
+              const int hsel = kb % 3;
+              const uint32_t acc_col = (NSPLIT == 1) ? 0u : (pr == 0 ? 128u * hsel : 384u);
+              uint32_t accum;
+              if (NSPLIT == 1) accum = (kb | kk) != 0 ? 1u : 0u;
+              else if (pr == 0) accum = (kb >= 3 || kk != 0) ? 1u : 0u;
+              else accum = (pr == 1 && (kb | kk) == 0) ? 0u : 1u;
+              tc_mma_bf16(tmem + acc_col, ad, bd, idesc, accum);
+            }
+          }
+          tc_commit(&empty[s]);
+        }
+        tc_commit(accf);
+        ++ti;
       }
-      if (diag_tile && c == warp && row_ok) {
+    }
+  } else {
+    // ---- epilogue warps 0-3: thread = output row of the tile ---------------------------------
+    int ti = 0;
+    float* tb = tbuf + warp * (32 * 33);
+    for (int t = blockIdx.x; t < n_work && ok; t += gridDim.x) {
+      const GemmWork w = p.work[t];
+      if (!tile_live(w)) continue;
+      const GemmMat m = p.mats[w.mat];
+      const int cur = tile_cur(w, m);
+      const int branch_sq = (p.mode == kModeSp2 || p.mode == kModeRsp) ? (p.sp2[w.mat].y >= 0.5) : 0;
+      const long long in_shift = stepping ? cur * m.buf_stride : 0;
+      const long long out_shift = stepping ? (1 - cur) * m.buf_stride : 0;
+      const int kb_end = (m.k_real + 63) >> 6;
+      const int row_local = warp * 32 + lane;
+      const int row = w.tm * 128 + row_local;
+      const bool row_ok = row < m.m_real;
+      const bool diag_tile = (w.tm == w.tn);
+      {
+        const long long roff = ((long long)row * m.n_pad + w.tn * 128) * 4;
+        const uint8_t* pre[3] = {nullptr, nullptr, nullptr};
+        if (stepping) pre[0] = p.arena + m.x_off + in_shift + roff;
+        if (p.mode == kModeRsp) pre[1] = p.arena + m.c_off + roff;
+        if (p.mode == kModeGeneric && m.c_off >= 0)
+          pre[1] = p.arena + m.c_off + (m.c_from_sp2 ? cur * m.buf_stride : 0) + roff;
+        if (p.mode == kModeGeneric && m.c2_off >= 0) pre[2] = p.arena + m.c2_off + roff;
+        if (row_ok)
+          for (int u = 0; u < 3; ++u)
+            if (pre[u])
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
-          if (j == lane) { tr_x = x[j]; tr_x2 = v[j]; }
+              for (int q = 0; q < 4; ++q) asm volatile("prefetch.global.L2 [%0];" ::"l"(pre[u] + q * 128));
       }
+      if (!mbar_wait(accf, (uint32_t)(ti & 1))) { ok = false; break; }
+      tc_fence_after();
+      // drain every accumulator of this tile into registers, then hand TMEM back
+      float v[4][32];
+      const uint32_t t_row = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const bool ok_ij = row_ok && (col0 + j) < m.n_real;
-        const float nv = branch_sq ? v[j] : 2.f * x[j] - v[j];
-        v[j] = ok_ij ? nv : 0.f;
-      }
-    } else {
-      float c1[32], c2[32];
+      for (int c = 0; c < 4; ++c) {
+        tmem_ld32(t_row + c * 32, v[c]);
+        if (NSPLIT > 1) {
+          float v2[32];
+          if (kb_end > 1) {
+            tmem_ld32(t_row + 128 + c * 32, v2);
 #pragma unroll
-      for (int j = 0; j < 32; ++j) { c1[j] = 0.f; c2[j] = 0.f; }
-      if (m.c_off >= 0) {
-        const float4* s1 = reinterpret_cast<const float4*>(
-            p.arena + m.c_off + (m.c_from_sp2 ? cur * m.buf_stride : 0) + ((long long)row * m.n_pad + col0) * 4);
+            for (int j = 0; j < 32; ++j) v[c][j] += v2[j];
+          }
+          if (kb_end > 2) {
+            tmem_ld32(t_row + 256 + c * 32, v2);
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const float4 t = s1[q];
-          c1[4 * q] = t.x; c1[4 * q + 1] = t.y; c1[4 * q + 2] = t.z; c1[4 * q + 3] = t.w;
+            for (int j = 0; j < 32; ++j) v[c][j] += v2[j];
+          }
+          tmem_ld32(t_row + 384 + c * 32, v2);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[c][j] += v2[j];
         }
       }
-      if (m.c2_off >= 0) {
-        const float4* s2 = reinterpret_cast<const float4*>(p.arena + m.c2_off + ((long long)row * m.n_pad + col0) * 4);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const float4 t = s2[q];
-          c2[4 * q] = t.x; c2[4 * q + 1] = t.y; c2[4 * q + 2] = t.z; c2[4 * q + 3] = t.w;
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int col = col0 + j;
-        const bool ok_ij = row_ok && col < m.n_real;
-        v[j] = ok_ij ? (p.alpha * v[j] + (row == col ? p.beta : 0.f) + p.g1 * c1[j] + p.g2 * c2[j]) : 0.f;
-      }
-    }
-    if (outm) {
-      float4* dst = reinterpret_cast<float4*>(outm + (long long)row * m.n_pad + col0);
-#pragma unroll
-      for (int q = 0; q < 8; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-    }
-    if (m.outp_off >= 0 && p.nsplit_out > 0) {
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        store_planes8(p.arena, m.outp_off + out_shift, m.outp_plane, p.nsplit_out, m.n_pad, row, col0 + 8 * q,
-                      v + 8 * q);
-    }
-    if (m.sym_out && !diag_tile) {
-      // mirrored tile through shared memory (the operand ring is idle now): the warp's
-      // 32 x 32 block is transposed so that lane l then holds output row (col0 + l) and
-      // writes it with the same vector stores as the direct tile.
-      float* tb = reinterpret_cast<float*>(smem) + warp * (32 * 33);
+      tc_fence_before();
       __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(acce)) : "memory");
+      ++ti;
+
+      float* outm = (m.out_off >= 0) ? reinterpret_cast<float*>(p.arena + m.out_off + out_shift) : nullptr;
+      const float* xm = stepping ? reinterpret_cast<const float*>(p.arena + m.x_off + in_shift) : nullptr;
+      const float* cm = (p.mode == kModeRsp) ? reinterpret_cast<const float*>(p.arena + m.c_off) : nullptr;
+      float tr_x = 0.f, tr_x2 = 0.f;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) tb[lane * 33 + j] = v[j];
-      __syncwarp();
-      float tv[32];
+      for (int c = 0; c < 4; ++c) {
+        float* vv = v[c];
+        const int col0 = w.tn * 128 + c * 32;
+        if (p.mode == kModeRsp) {
+          const float4* sx = reinterpret_cast<const float4*>(xm + (long long)row * m.n_pad + col0);
+          const float4* sc = reinterpret_cast<const float4*>(cm + (long long)row * m.n_pad + col0);
 #pragma unroll
-      for (int j = 0; j < 32; ++j) tv[j] = tb[j * 33 + lane];
-      const int trow = col0 + lane;                      // output row of the mirrored element
-      const int tcol0 = w.tm * 128 + warp * 32;          // its first column
-      if (outm) {
-        float4* dst = reinterpret_cast<float4*>(outm + (long long)trow * m.n_pad + tcol0);
+          for (int q = 0; q < 8; ++q) {
+            const float4 a = sx[q], c4 = sc[q];
+            const float xa[4] = {a.x, a.y, a.z, a.w}, ca[4] = {c4.x, c4.y, c4.z, c4.w};
 #pragma unroll
-        for (int q = 0; q < 8; ++q) dst[q] = make_float4(tv[4 * q], tv[4 * q + 1], tv[4 * q + 2], tv[4 * q + 3]);
+            for (int e = 0; e < 4; ++e) {
+              const int j = 4 * q + e;
+              const bool ok_ij = row_ok && (col0 + j) < m.n_real;
+              const float sum = vv[j] + ca[e];
+              vv[j] = ok_ij ? (branch_sq ? sum : 2.f * xa[e] - sum) : 0.f;
+            }
+          }
+        } else if (p.mode == kModeSp2) {
+          float x[32];
+          const float4* src = reinterpret_cast<const float4*>(xm + (long long)row * m.n_pad + col0);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const float4 t4 = src[q];
+            x[4 * q] = t4.x; x[4 * q + 1] = t4.y; x[4 * q + 2] = t4.z; x[4 * q + 3] = t4.w;
+          }
+          if (diag_tile && c == warp && row_ok) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (j == lane) { tr_x = x[j]; tr_x2 = vv[j]; }
+          }
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const bool ok_ij = row_ok && (col0 + j) < m.n_real;
+            const float nv = branch_sq ? vv[j] : 2.f * x[j] - vv[j];
+            vv[j] = ok_ij ? nv : 0.f;
+          }
+        } else {
+          float c1[32], c2[32];
+#pragma unroll
+          for (int j = 0; j < 32; ++j) { c1[j] = 0.f; c2[j] = 0.f; }
+          if (m.c_off >= 0) {
+            const float4* s1 = reinterpret_cast<const float4*>(
+                p.arena + m.c_off + (m.c_from_sp2 ? cur * m.buf_stride : 0) + ((long long)row * m.n_pad + col0) * 4);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const float4 t4 = s1[q];
+              c1[4 * q] = t4.x; c1[4 * q + 1] = t4.y; c1[4 * q + 2] = t4.z; c1[4 * q + 3] = t4.w;
+            }
+          }
+          if (m.c2_off >= 0) {
+            const float4* s2 =
+                reinterpret_cast<const float4*>(p.arena + m.c2_off + ((long long)row * m.n_pad + col0) * 4);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const float4 t4 = s2[q];
+              c2[4 * q] = t4.x; c2[4 * q + 1] = t4.y; c2[4 * q + 2] = t4.z; c2[4 * q + 3] = t4.w;
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int col = col0 + j;
+            const bool ok_ij = row_ok && col < m.n_real;
+            vv[j] = ok_ij ? (p.alpha * vv[j] + (row == col ? p.beta : 0.f) + p.g1 * c1[j] + p.g2 * c2[j]) : 0.f;
+          }
+        }
+        if (outm) {
+          float4* dst = reinterpret_cast<float4*>(outm + (long long)row * m.n_pad + col0);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) dst[q] = make_float4(vv[4 * q], vv[4 * q + 1], vv[4 * q + 2], vv[4 * q + 3]);
+        }
+        if (m.outp_off >= 0 && p.nsplit_out > 0) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            store_planes8(p.arena, m.outp_off + out_shift, m.outp_plane, p.nsplit_out, m.n_pad, row, col0 + 8 * q,
+                          vv + 8 * q);
+        }
+        if (m.sym_out && !diag_tile) {
+          __syncwarp();
+#pragma unroll
+          for (int j = 0; j < 32; ++j) tb[lane * 33 + j] = vv[j];
+          __syncwarp();
+          float tv[32];
+#pragma unroll
+          for (int j = 0; j < 32; ++j) tv[j] = tb[j * 33 + lane];
+          const int trow = col0 + lane;
+          const int tcol0 = w.tm * 128 + warp * 32;
+          if (outm) {
+            float4* dst = reinterpret_cast<float4*>(outm + (long long)trow * m.n_pad + tcol0);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) dst[q] = make_float4(tv[4 * q], tv[4 * q + 1], tv[4 * q + 2], tv[4 * q + 3]);
+          }
+          if (m.outp_off >= 0 && p.nsplit_out > 0) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              store_planes8(p.arena, m.outp_off + out_shift, m.outp_plane, p.nsplit_out, m.n_pad, trow,
+                            tcol0 + 8 * q, tv + 8 * q);
+          }
+        }
       }
-      if (m.outp_off >= 0 && p.nsplit_out > 0) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          store_planes8(p.arena, m.outp_off + out_shift, m.outp_plane, p.nsplit_out, m.n_pad, trow, tcol0 + 8 * q,
-                        tv + 8 * q);
+      if (p.mode == kModeSp2 && diag_tile) {
+        // one slot pair per warp of every diagonal tile (summed in fixed order by the control kernel)
+        const float sx = warp_sumf(tr_x), sx2 = warp_sumf(tr_x2);
+        if (lane == 0) {
+          p.tr_slots[m.tr_off + 8 * w.tm + 2 * warp] = sx;
+          p.tr_slots[m.tr_off + 8 * w.tm + 2 * warp + 1] = sx2;
+        }
       }
     }
-  }
-  if (p.mode == kModeSp2 && diag_tile) {
-    // fixed-order CTA reduction of the trace partials -> one slot per diagonal tile
-    const float sx = warp_sumf(tr_x), sx2 = warp_sumf(tr_x2);
-    if (lane == 0) { red[2 * warp] = sx; red[2 * warp + 1] = sx2; }
   }
   tc_fence_before();
   __syncthreads();
-  if (p.mode == kModeSp2 && diag_tile && threadIdx.x == 0) {
-    double a = 0.0, b = 0.0;
-    for (int q = 0; q < 4; ++q) { a += red[2 * q]; b += red[2 * q + 1]; }
-    p.tr_slots[m.tr_off + 2 * w.tm] = a;
-    p.tr_slots[m.tr_off + 2 * w.tm + 1] = b;
-  }
   if (warp == 0) {
     tc_fence_after();
     tmem_dealloc(tmem, kTmemCols);
@@ -416,35 +449,41 @@ __global__ void __launch_bounds__(256) f64_gemm_kernel(const GemmParams p) {
     if (tid == 0) {
       double sa = 0.0, sb = 0.0;
       for (int q = 0; q < 8; ++q) { sa += red[0][q]; sb += red[1][q]; }
-      p.tr_slots[m.tr_off + 2 * w.tm] = sa;
-      p.tr_slots[m.tr_off + 2 * w.tm + 1] = sb;
+      p.tr_slots[m.tr_off + 8 * w.tm] = sa;
+      p.tr_slots[m.tr_off + 8 * w.tm + 1] = sb;
+      for (int q = 2; q < 8; ++q) p.tr_slots[m.tr_off + 8 * w.tm + q] = 0.0;
     }
   }
 }
 
 }  // namespace
 
+static int g_num_sms = 0;
+
+template <int NSPLIT>
+static void launch_tc(const GemmParams& p, int n_work, cudaStream_t s) {
+  static bool init = false;
+  if (!init) {
+    cudaFuncSetAttribute(tc_gemm_persistent<NSPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         TcPCfg<NSPLIT>::kSmem);
+    init = true;
+  }
+  if (g_num_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 148;
+  }
+  const int grid = n_work < g_num_sms ? n_work : g_num_sms;
+  tc_gemm_persistent<NSPLIT><<<grid, 192, TcPCfg<NSPLIT>::kSmem, s>>>(p, n_work);
+}
+
 void launch_gemm_tc(const GemmParams& p, int n_work, int nsplit, cudaStream_t s) {
   if (n_work <= 0) return;
   switch (nsplit) {
-    case 1: {
-      static bool init = false;
-      if (!init) { cudaFuncSetAttribute(tc_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<1>::kSmem); init = true; }
-      tc_gemm_kernel<1><<<n_work, 128, TcCfg<1>::kSmem, s>>>(p);
-      break;
-    }
-    case 2: {
-      static bool init = false;
-      if (!init) { cudaFuncSetAttribute(tc_gemm_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<2>::kSmem); init = true; }
-      tc_gemm_kernel<2><<<n_work, 128, TcCfg<2>::kSmem, s>>>(p);
-      break;
-    }
-    default: {
-      static bool init = false;
-      if (!init) { cudaFuncSetAttribute(tc_gemm_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<3>::kSmem); init = true; }
-      tc_gemm_kernel<3><<<n_work, 128, TcCfg<3>::kSmem, s>>>(p);
-      break;
-    }
+    case 1: launch_tc<1>(p, n_work, s); break;
+    case 2: launch_tc<2>(p, n_work, s); break;
+    default: launch_tc<3>(p, n_work, s); break;
   }
 }
 

@@ -165,7 +165,7 @@ __global__ void sp2_advance_kernel(Sp2State* st, const double* slots, const long
   Sp2State s = st[i];
   if (!s.active) return;
   double a = 0.0, b = 0.0;
-  for (int q = 0; q < n_diag[i]; ++q) {
+  for (int q = 0; q < 4 * n_diag[i]; ++q) {     // fixed order: tiles, then warps
     a += slots[tr_off[i] + 2 * q];
     b += slots[tr_off[i] + 2 * q + 1];
   }

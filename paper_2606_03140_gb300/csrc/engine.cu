@@ -451,7 +451,7 @@ sedacs_status rebuild_layout(sedacs_ctx* ctx) {
     L.rw_total += (long long)L.m_pad[i] * L.n_pad[i];
     L.n_diag[i] = L.n_pad[i] / ctx->tile;
     L.tr_off[i] = L.tr_total;
-    L.tr_total += 2 * L.n_diag[i];
+    L.tr_total += 8 * L.n_diag[i];     // four (Tr X, Tr X^2) pairs per diagonal tile
     L.max_npad = std::max(L.max_npad, L.n_pad[i]);
     L.max_mpad = std::max(L.max_mpad, L.m_pad[i]);
   }
@@ -620,7 +620,7 @@ void compute_z(sedacs_ctx* ctx) {
   if (!ctx->f64) launch_split_planes(ctx->d_views[kZ1], L.n_sub, mr, ctx->arena, ns, false, s);
   ctx->launches += ctx->f64 ? 3 : 6;
   int c = 1;
-  const int K = std::max(2, ctx->prm.ns_iters);
+  const int K = ctx->prm.ns_iters > 0 ? std::max(2, ctx->prm.ns_iters) : (ctx->f64 ? 4 : 3);
   for (int k = 2; k <= K; ++k) {
     run_op(ctx, c == 0 ? OP_NS_T0 : OP_NS_T1, ns, ns);
     if (k < K) run_op(ctx, c == 0 ? OP_NS_Y0 : OP_NS_Y1b, ns, ns);
@@ -1056,7 +1056,7 @@ void sedacs_default_params(sedacs_params* p) {
   p->scc_alpha = 0.2;
   p->sp2_tol = 1e-9;
   p->sp2_kmax = 60;
-  p->ns_iters = 4;
+  p->ns_iters = 0;      // 0: 3 steps in the mixed forms, 4 in FP64
   p->ewald_tol = 0.0;
 }
 
