@@ -21,7 +21,6 @@ template <int NSPLIT>
 struct TcCfg {
   static constexpr int kStages = (NSPLIT == 3) ? 2 : 3;
   static constexpr int kStageBytes = 2 * NSPLIT * kBlkBytes;
-  static constexpr int kSmem = kStages * kStageBytes + 1024 + 256;
   static constexpr int kNumProd = (NSPLIT == 1) ? 1 : (NSPLIT == 2 ? 3 : 6);
 };
 
@@ -46,22 +45,33 @@ __device__ __forceinline__ void store_planes8(uint8_t* arena, long long base, lo
 
 // ------------------------------------------------------------------------------------------
 // Persistent, warp-specialised split-bf16 GEMM.  One CTA per SM walks the work list (128x128
-// output tiles) with a stride of gridDim.x.  Warp 4 (one lane) streams the operand blocks of consecutive
-// tiles through the stage ring without pausing at tile boundaries; warp 5 (one lane) issues
-// the MMAs of a tile once the epilogue has drained the previous tile's accumulators; warps
-// 0-3 drain TMEM into registers, release it at once, and then run the epilogue math and stores
-// while the next tile's MMAs proceed.  Every wait is bounded.
+// output tiles) with a stride of gridDim.x.  The producer warp (one lane) streams the operand
+// blocks of consecutive tiles through the stage ring without pausing at tile boundaries; the
+// MMA warp (one lane) issues the MMAs of a tile once the epilogue has drained the previous
+// tile's accumulators; eight epilogue warps prefetch their inputs, drain TMEM into registers,
+// release it at once, and then run the epilogue math and stores while the next tile's MMAs
+// proceed.  Every wait is bounded.
 // ------------------------------------------------------------------------------------------
+// Epilogue warps: two per TMEM lane quadrant (warp & 3), each owning one half (warp >> 2)
+// of the tile's 128 columns; then one producer warp and one MMA warp.
+constexpr int kEpiWarps = 8;
+constexpr int kProducerWarp = kEpiWarps, kMmaWarp = kEpiWarps + 1;
+constexpr int kTcThreads = 32 * (kEpiWarps + 2);
+
+// Per-warp 32x32 FP32 staging chunk, float4 groups XOR-swizzled by row so that row-wise and
+// 8-column-wise float4 accesses spread over all banks.
+__device__ __forceinline__ int tb_idx(int r, int c) { return r * 32 + ((((c >> 2) ^ (r & 7))) << 2) + (c & 3); }
+
 template <int NSPLIT>
 struct TcPCfg {
   static constexpr int kStages = TcCfg<NSPLIT>::kStages;
   static constexpr int kStageBytes = TcCfg<NSPLIT>::kStageBytes;
-  static constexpr int kTransBytes = 4 * 32 * 33 * 4;
+  static constexpr int kTransBytes = kEpiWarps * 32 * 32 * 4;
   static constexpr int kSmem = kStages * kStageBytes + kTransBytes + 1024 + 256;
 };
 
 template <int NSPLIT>
-__global__ void __launch_bounds__(192, 1) tc_gemm_persistent(const GemmParams p, int n_work) {
+__global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_persistent(const GemmParams p, int n_work) {
   using Cfg = TcCfg<NSPLIT>;
   using PCfg = TcPCfg<NSPLIT>;
   if (*reinterpret_cast<volatile int*>(p.err) & kErrTimeout) return;
@@ -83,7 +93,7 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_persistent(const GemmParams p,
       mbar_init(&empty[s], 1);
     }
     mbar_init(accf, 1);
-    mbar_init(acce, 4);
+    mbar_init(acce, kEpiWarps);
     fence_mbar_init();
   }
   if (warp == 0) {
@@ -102,7 +112,7 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_persistent(const GemmParams p,
     return (stepping || m.b_from_sp2 || m.a_from_sp2 || m.c_from_sp2) ? p.sp2[w.mat].cur : 0;
   };
 
-  if (warp == 4) {
+  if (warp == kProducerWarp) {
     if (lane == 0) {
       long long g = 0;
       for (int t = blockIdx.x; t < n_work && ok; t += gridDim.x) {
@@ -134,7 +144,7 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_persistent(const GemmParams p,
       for (long long q = g - 1; q >= 0 && q >= g - Cfg::kStages; --q)
         mbar_wait(&full[q % Cfg::kStages], (uint32_t)((q / Cfg::kStages) & 1));
     }
-  } else if (warp == 5) {
+  } else if (warp == kMmaWarp) {
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_bf16_f32(128, 128);
       long long g = 0;
@@ -176,59 +186,87 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_persistent(const GemmParams p,
       }
     }
   } else {
-    // ---- epilogue warps 0-3: thread = output row of the tile ---------------------------------
+    // ---- epilogue warps --------------------------------------------------------------------
+    // TMEM lane quadrant qd (tile rows 32 qd ..), column half hf (tile columns 64 hf ..).  The
+    // drain maps a thread to a row; everything global uses the coalesced mapping of 4 lanes
+    // per row and 8 consecutive columns per lane (8 rows per instruction).
+    const int qd = warp & 3, hf = warp >> 2;
+    const int rsub = lane >> 2, csub = (lane & 3) * 8;
+    float* tb = tbuf + warp * (32 * 32);
     int ti = 0;
-    float* tb = tbuf + warp * (32 * 33);
     for (int t = blockIdx.x; t < n_work && ok; t += gridDim.x) {
       const GemmWork w = p.work[t];
       if (!tile_live(w)) continue;
       const GemmMat m = p.mats[w.mat];
       const int cur = tile_cur(w, m);
-      const int branch_sq = (p.mode == kModeSp2 || p.mode == kModeRsp) ? (p.sp2[w.mat].y >= 0.5) : 0;
+      const int branch_sq = stepping ? (p.sp2[w.mat].y >= 0.5) : 0;
       const long long in_shift = stepping ? cur * m.buf_stride : 0;
       const long long out_shift = stepping ? (1 - cur) * m.buf_stride : 0;
       const int kb_end = (m.k_real + 63) >> 6;
-      const int row_local = warp * 32 + lane;
-      const int row = w.tm * 128 + row_local;
-      const bool row_ok = row < m.m_real;
       const bool diag_tile = (w.tm == w.tn);
-      {
-        const long long roff = ((long long)row * m.n_pad + w.tn * 128) * 4;
-        const uint8_t* pre[3] = {nullptr, nullptr, nullptr};
-        if (stepping) pre[0] = p.arena + m.x_off + in_shift + roff;
-        if (p.mode == kModeRsp) pre[1] = p.arena + m.c_off + roff;
-        if (p.mode == kModeGeneric && m.c_off >= 0)
-          pre[1] = p.arena + m.c_off + (m.c_from_sp2 ? cur * m.buf_stride : 0) + roff;
-        if (p.mode == kModeGeneric && m.c2_off >= 0) pre[2] = p.arena + m.c2_off + roff;
-        if (row_ok)
-          for (int u = 0; u < 3; ++u)
-            if (pre[u])
+      const int row0 = w.tm * 128 + qd * 32;          // first tile row of this warp
+      const int colh = w.tn * 128 + hf * 64;          // first tile column of this warp
+      // first epilogue input (X for the SP2 / response steps, C1 for the generic form), loaded
+      // before the accumulators are ready so that its latency hides behind the MMAs
+      const float* in1 = nullptr;
+      if (stepping) in1 = reinterpret_cast<const float*>(p.arena + m.x_off + in_shift);
+      else if (m.c_off >= 0) in1 = reinterpret_cast<const float*>(p.arena + m.c_off + (m.c_from_sp2 ? cur * m.buf_stride : 0));
+      const float* in2 = nullptr;
+      if (p.mode == kModeRsp) in2 = reinterpret_cast<const float*>(p.arena + m.c_off);
+      else if (!stepping && m.c2_off >= 0) in2 = reinterpret_cast<const float*>(p.arena + m.c2_off);
+      float pre[4][8];
+      auto load8x4 = [&](const float* base, int col, float (*dst)[8]) {
 #pragma unroll
-              for (int q = 0; q < 4; ++q) asm volatile("prefetch.global.L2 [%0];" ::"l"(pre[u] + q * 128));
+        for (int i = 0; i < 4; ++i) {
+          if (base) {
+            const float* src = base + (long long)(row0 + 8 * i + rsub) * m.n_pad + col + csub;
+            const float4 a0 = __ldg(reinterpret_cast<const float4*>(src));
+            const float4 a1 = __ldg(reinterpret_cast<const float4*>(src + 4));
+            dst[i][0] = a0.x; dst[i][1] = a0.y; dst[i][2] = a0.z; dst[i][3] = a0.w;
+            dst[i][4] = a1.x; dst[i][5] = a1.y; dst[i][6] = a1.z; dst[i][7] = a1.w;
+          } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) dst[i][e] = 0.f;
+          }
+        }
+      };
+      // L2 prefetch of both inputs for this warp's rows and columns while the MMAs run
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const long long ro = (long long)(row0 + 8 * i + rsub) * m.n_pad + colh + csub;
+        if (in1) {
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(in1 + ro));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(in1 + ro + 32));
+        }
+        if (in2) {
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(in2 + ro));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(in2 + ro + 32));
+        }
       }
       if (!mbar_wait(accf, (uint32_t)(ti & 1))) { ok = false; break; }
       tc_fence_after();
-      // drain every accumulator of this tile into registers, then hand TMEM back
-      float v[4][32];
-      const uint32_t t_row = tmem + ((uint32_t)(warp * 32) << 16);
+      // drain this warp's 64 columns of every accumulator into registers, then hand TMEM back
+      float v[2][32];
+      const uint32_t t_row = tmem + ((uint32_t)(qd * 32) << 16);
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        tmem_ld32(t_row + c * 32, v[c]);
+      for (int cc = 0; cc < 2; ++cc) {
+        const uint32_t col = (uint32_t)(hf * 64 + cc * 32);
+        tmem_ld32(t_row + col, v[cc]);
         if (NSPLIT > 1) {
           float v2[32];
           if (kb_end > 1) {
-            tmem_ld32(t_row + 128 + c * 32, v2);
+            tmem_ld32(t_row + 128 + col, v2);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) v[c][j] += v2[j];
+            for (int j = 0; j < 32; ++j) v[cc][j] += v2[j];
           }
           if (kb_end > 2) {
-            tmem_ld32(t_row + 256 + c * 32, v2);
+            tmem_ld32(t_row + 256 + col, v2);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) v[c][j] += v2[j];
+            for (int j = 0; j < 32; ++j) v[cc][j] += v2[j];
           }
-          tmem_ld32(t_row + 384 + c * 32, v2);
+          tmem_ld32(t_row + 384 + col, v2);
 #pragma unroll
-          for (int j = 0; j < 32; ++j) v[c][j] += v2[j];
+          for (int j = 0; j < 32; ++j) v[cc][j] += v2[j];
         }
       }
       tc_fence_before();
@@ -237,116 +275,100 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_persistent(const GemmParams p,
       ++ti;
 
       float* outm = (m.out_off >= 0) ? reinterpret_cast<float*>(p.arena + m.out_off + out_shift) : nullptr;
-      const float* xm = stepping ? reinterpret_cast<const float*>(p.arena + m.x_off + in_shift) : nullptr;
-      const float* cm = (p.mode == kModeRsp) ? reinterpret_cast<const float*>(p.arena + m.c_off) : nullptr;
+      const bool planes = m.outp_off >= 0 && p.nsplit_out > 0;
+      const bool mirror = m.sym_out && !diag_tile;
       float tr_x = 0.f, tr_x2 = 0.f;
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        float* vv = v[c];
-        const int col0 = w.tn * 128 + c * 32;
-        if (p.mode == kModeRsp) {
-          const float4* sx = reinterpret_cast<const float4*>(xm + (long long)row * m.n_pad + col0);
-          const float4* sc = reinterpret_cast<const float4*>(cm + (long long)row * m.n_pad + col0);
+      for (int cc = 0; cc < 2; ++cc) {
+        const int ctile = hf * 64 + cc * 32;            // chunk's first column within the tile
+        const int col0 = w.tn * 128 + ctile;
+        load8x4(in1, col0, pre);
+        __syncwarp();
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const float4 a = sx[q], c4 = sc[q];
-            const float xa[4] = {a.x, a.y, a.z, a.w}, ca[4] = {c4.x, c4.y, c4.z, c4.w};
+        for (int q = 0; q < 8; ++q)
+          *reinterpret_cast<float4*>(tb + tb_idx(lane, 4 * q)) =
+              make_float4(v[cc][4 * q], v[cc][4 * q + 1], v[cc][4 * q + 2], v[cc][4 * q + 3]);
+        __syncwarp();
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const int j = 4 * q + e;
-              const bool ok_ij = row_ok && (col0 + j) < m.n_real;
-              const float sum = vv[j] + ca[e];
-              vv[j] = ok_ij ? (branch_sq ? sum : 2.f * xa[e] - sum) : 0.f;
+        for (int i = 0; i < 4; ++i) {
+          const int rl = 8 * i + rsub;
+          const int grow = row0 + rl;
+          const int gcol = col0 + csub;
+          float acc[8], out[8];
+          {
+            const float4 a0 = *reinterpret_cast<const float4*>(tb + tb_idx(rl, csub));
+            const float4 a1 = *reinterpret_cast<const float4*>(tb + tb_idx(rl, csub + 4));
+            acc[0] = a0.x; acc[1] = a0.y; acc[2] = a0.z; acc[3] = a0.w;
+            acc[4] = a1.x; acc[5] = a1.y; acc[6] = a1.z; acc[7] = a1.w;
+          }
+          float sec[8];
+          if (in2) {
+            const float* src = in2 + (long long)grow * m.n_pad + gcol;
+            const float4 a0 = __ldg(reinterpret_cast<const float4*>(src));
+            const float4 a1 = __ldg(reinterpret_cast<const float4*>(src + 4));
+            sec[0] = a0.x; sec[1] = a0.y; sec[2] = a0.z; sec[3] = a0.w;
+            sec[4] = a1.x; sec[5] = a1.y; sec[6] = a1.z; sec[7] = a1.w;
+          } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) sec[e] = 0.f;
+          }
+          const bool rok = grow < m.m_real;
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const bool ok_ij = rok && (gcol + e) < m.n_real;
+            float r;
+            if (stepping) {
+              const float sum = acc[e] + sec[e];
+              r = branch_sq ? sum : 2.f * pre[i][e] - sum;
+              if (p.mode == kModeSp2 && diag_tile && ok_ij && (qd * 32 + rl) == (ctile + csub + e)) {
+                tr_x += pre[i][e];
+                tr_x2 += acc[e];
+              }
+            } else {
+              r = p.alpha * acc[e] + (grow == gcol + e ? p.beta : 0.f) + p.g1 * pre[i][e] + p.g2 * sec[e];
             }
+            out[e] = ok_ij ? r : 0.f;
           }
-        } else if (p.mode == kModeSp2) {
-          float x[32];
-          const float4* src = reinterpret_cast<const float4*>(xm + (long long)row * m.n_pad + col0);
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const float4 t4 = src[q];
-            x[4 * q] = t4.x; x[4 * q + 1] = t4.y; x[4 * q + 2] = t4.z; x[4 * q + 3] = t4.w;
-          }
-          if (diag_tile && c == warp && row_ok) {
-#pragma unroll
-            for (int j = 0; j < 32; ++j)
-              if (j == lane) { tr_x = x[j]; tr_x2 = vv[j]; }
-          }
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const bool ok_ij = row_ok && (col0 + j) < m.n_real;
-            const float nv = branch_sq ? vv[j] : 2.f * x[j] - vv[j];
-            vv[j] = ok_ij ? nv : 0.f;
-          }
-        } else {
-          float c1[32], c2[32];
-#pragma unroll
-          for (int j = 0; j < 32; ++j) { c1[j] = 0.f; c2[j] = 0.f; }
-          if (m.c_off >= 0) {
-            const float4* s1 = reinterpret_cast<const float4*>(
-                p.arena + m.c_off + (m.c_from_sp2 ? cur * m.buf_stride : 0) + ((long long)row * m.n_pad + col0) * 4);
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              const float4 t4 = s1[q];
-              c1[4 * q] = t4.x; c1[4 * q + 1] = t4.y; c1[4 * q + 2] = t4.z; c1[4 * q + 3] = t4.w;
-            }
-          }
-          if (m.c2_off >= 0) {
-            const float4* s2 =
-                reinterpret_cast<const float4*>(p.arena + m.c2_off + ((long long)row * m.n_pad + col0) * 4);
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              const float4 t4 = s2[q];
-              c2[4 * q] = t4.x; c2[4 * q + 1] = t4.y; c2[4 * q + 2] = t4.z; c2[4 * q + 3] = t4.w;
-            }
-          }
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int col = col0 + j;
-            const bool ok_ij = row_ok && col < m.n_real;
-            vv[j] = ok_ij ? (p.alpha * vv[j] + (row == col ? p.beta : 0.f) + p.g1 * c1[j] + p.g2 * c2[j]) : 0.f;
-          }
-        }
-        if (outm) {
-          float4* dst = reinterpret_cast<float4*>(outm + (long long)row * m.n_pad + col0);
-#pragma unroll
-          for (int q = 0; q < 8; ++q) dst[q] = make_float4(vv[4 * q], vv[4 * q + 1], vv[4 * q + 2], vv[4 * q + 3]);
-        }
-        if (m.outp_off >= 0 && p.nsplit_out > 0) {
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-            store_planes8(p.arena, m.outp_off + out_shift, m.outp_plane, p.nsplit_out, m.n_pad, row, col0 + 8 * q,
-                          vv + 8 * q);
-        }
-        if (m.sym_out && !diag_tile) {
-          __syncwarp();
-#pragma unroll
-          for (int j = 0; j < 32; ++j) tb[lane * 33 + j] = vv[j];
-          __syncwarp();
-          float tv[32];
-#pragma unroll
-          for (int j = 0; j < 32; ++j) tv[j] = tb[j * 33 + lane];
-          const int trow = col0 + lane;
-          const int tcol0 = w.tm * 128 + warp * 32;
+          const long long goff = (long long)grow * m.n_pad + gcol;
           if (outm) {
-            float4* dst = reinterpret_cast<float4*>(outm + (long long)trow * m.n_pad + tcol0);
-#pragma unroll
-            for (int q = 0; q < 8; ++q) dst[q] = make_float4(tv[4 * q], tv[4 * q + 1], tv[4 * q + 2], tv[4 * q + 3]);
+            float4* dst = reinterpret_cast<float4*>(outm + goff);
+            dst[0] = make_float4(out[0], out[1], out[2], out[3]);
+            dst[1] = make_float4(out[4], out[5], out[6], out[7]);
           }
-          if (m.outp_off >= 0 && p.nsplit_out > 0) {
+          if (planes) store_planes8(p.arena, m.outp_off + out_shift, m.outp_plane, p.nsplit_out, m.n_pad, grow, gcol, out);
+          if (mirror) {
+            *reinterpret_cast<float4*>(tb + tb_idx(rl, csub)) = make_float4(out[0], out[1], out[2], out[3]);
+            *reinterpret_cast<float4*>(tb + tb_idx(rl, csub + 4)) = make_float4(out[4], out[5], out[6], out[7]);
+          }
+        }
+        if (mirror) {
+          // mirrored tile: output row (col0 + j) takes column j of the chunk
+          __syncwarp();
+#pragma unroll 1
+          for (int i = 0; i < 4; ++i) {
+            const int jl = 8 * i + rsub;
+            const int trow = col0 + jl;
+            const int tcol = row0 + csub;
+            float tv[8];
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-              store_planes8(p.arena, m.outp_off + out_shift, m.outp_plane, p.nsplit_out, m.n_pad, trow,
-                            tcol0 + 8 * q, tv + 8 * q);
+            for (int e = 0; e < 8; ++e) tv[e] = tb[tb_idx(csub + e, jl)];
+            const long long toff = (long long)trow * m.n_pad + tcol;
+            if (outm) {
+              float4* dst = reinterpret_cast<float4*>(outm + toff);
+              dst[0] = make_float4(tv[0], tv[1], tv[2], tv[3]);
+              dst[1] = make_float4(tv[4], tv[5], tv[6], tv[7]);
+            }
+            if (planes) store_planes8(p.arena, m.outp_off + out_shift, m.outp_plane, p.nsplit_out, m.n_pad, trow, tcol, tv);
           }
         }
       }
-      if (p.mode == kModeSp2 && diag_tile) {
-        // one slot pair per warp of every diagonal tile (summed in fixed order by the control kernel)
+      if (p.mode == kModeSp2 && diag_tile && (qd >> 1) == hf) {
+        // the warp holding the diagonal of quadrant qd writes its slot pair (summed in fixed
+        // order by the control kernel)
         const float sx = warp_sumf(tr_x), sx2 = warp_sumf(tr_x2);
         if (lane == 0) {
-          p.tr_slots[m.tr_off + 8 * w.tm + 2 * warp] = sx;
-          p.tr_slots[m.tr_off + 8 * w.tm + 2 * warp + 1] = sx2;
+          p.tr_slots[m.tr_off + 8 * w.tm + 2 * qd] = sx;
+          p.tr_slots[m.tr_off + 8 * w.tm + 2 * qd + 1] = sx2;
         }
       }
     }
@@ -475,7 +497,7 @@ static void launch_tc(const GemmParams& p, int n_work, cudaStream_t s) {
     if (g_num_sms <= 0) g_num_sms = 148;
   }
   const int grid = n_work < g_num_sms ? n_work : g_num_sms;
-  tc_gemm_persistent<NSPLIT><<<grid, 192, TcPCfg<NSPLIT>::kSmem, s>>>(p, n_work);
+  tc_gemm_persistent<NSPLIT><<<grid, kTcThreads, TcPCfg<NSPLIT>::kSmem, s>>>(p, n_work);
 }
 
 void launch_gemm_tc(const GemmParams& p, int n_work, int nsplit, cudaStream_t s) {
