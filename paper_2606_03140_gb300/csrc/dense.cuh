@@ -31,6 +31,10 @@ struct GemmMat {
   int c_from_sp2;                // generic mode: C1 taken from the SP2 result buffer
   int sym_out;                   // result is symmetric: only tiles tn >= tm are run, each
                                  // off-diagonal tile is also written transposed
+  int x_planes;                  // SP2 mode, three planes: the epilogue takes X from A's planes
+                                 // (hi + mid + lo reproduces the fp32 value exactly), no master
+  int c_planes;                  // generic mode: C1 is three blocked bf16 planes at c_off
+  long long c_plane;             // bytes between the planes of C1
 };
 
 struct GemmWork {

@@ -209,17 +209,40 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_persistent(const GemmPa
       // first epilogue input (X for the SP2 / response steps, C1 for the generic form), loaded
       // before the accumulators are ready so that its latency hides behind the MMAs
       const float* in1 = nullptr;
-      if (stepping) in1 = reinterpret_cast<const float*>(p.arena + m.x_off + in_shift);
-      else if (m.c_off >= 0) in1 = reinterpret_cast<const float*>(p.arena + m.c_off + (m.c_from_sp2 ? cur * m.buf_stride : 0));
+      const uint8_t* in1p = nullptr;                  // ... or three blocked bf16 planes
+      long long in1_plane = 0;
+      if (NSPLIT == 3 && p.mode == kModeSp2 && m.x_planes) {
+        in1p = p.arena + m.a_off + in_shift;
+        in1_plane = m.a_plane;
+      } else if (NSPLIT == 3 && !stepping && m.c_planes && m.c_off >= 0) {
+        in1p = p.arena + m.c_off + (m.c_from_sp2 ? cur * m.buf_stride : 0);
+        in1_plane = m.c_plane;
+      } else if (stepping) {
+        in1 = reinterpret_cast<const float*>(p.arena + m.x_off + in_shift);
+      } else if (m.c_off >= 0) {
+        in1 = reinterpret_cast<const float*>(p.arena + m.c_off + (m.c_from_sp2 ? cur * m.buf_stride : 0));
+      }
       const float* in2 = nullptr;
       if (p.mode == kModeRsp) in2 = reinterpret_cast<const float*>(p.arena + m.c_off);
       else if (!stepping && m.c2_off >= 0) in2 = reinterpret_cast<const float*>(p.arena + m.c2_off);
       float pre[4][8];
-      auto load8x4 = [&](const float* base, int col, float (*dst)[8]) {
+      // the first input of one 32-column chunk in the coalesced mapping (zeros when absent)
+      auto load_in1 = [&](int col, float (*dst)[8]) {
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          if (base) {
-            const float* src = base + (long long)(row0 + 8 * i + rsub) * m.n_pad + col + csub;
+          if (in1p) {
+            const long long off = blocked_offset(row0 + 8 * i + rsub, col + csub, m.n_pad);
+            const uint4 h = __ldg(reinterpret_cast<const uint4*>(in1p + off));
+            const uint4 md = __ldg(reinterpret_cast<const uint4*>(in1p + off + in1_plane));
+            const uint4 l = __ldg(reinterpret_cast<const uint4*>(in1p + off + 2 * in1_plane));
+            const __nv_bfloat16* hb = reinterpret_cast<const __nv_bfloat16*>(&h);
+            const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(&md);
+            const __nv_bfloat16* lb = reinterpret_cast<const __nv_bfloat16*>(&l);
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+              dst[i][e] = (__bfloat162float(hb[e]) + __bfloat162float(mb[e])) + __bfloat162float(lb[e]);
+          } else if (in1) {
+            const float* src = in1 + (long long)(row0 + 8 * i + rsub) * m.n_pad + col + csub;
             const float4 a0 = __ldg(reinterpret_cast<const float4*>(src));
             const float4 a1 = __ldg(reinterpret_cast<const float4*>(src + 4));
             dst[i][0] = a0.x; dst[i][1] = a0.y; dst[i][2] = a0.z; dst[i][3] = a0.w;
@@ -237,6 +260,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_persistent(const GemmPa
         if (in1) {
           asm volatile("prefetch.global.L2 [%0];" ::"l"(in1 + ro));
           asm volatile("prefetch.global.L2 [%0];" ::"l"(in1 + ro + 32));
+        }
+        if (in1p) {
+          // this lane's two 16 B granules of the row in each plane
+          const long long o0 = blocked_offset(row0 + 8 * i + rsub, colh + csub, m.n_pad);
+          const long long o1 = blocked_offset(row0 + 8 * i + rsub, colh + 32 + csub, m.n_pad);
+#pragma unroll
+          for (int pl = 0; pl < 3; ++pl) {
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(in1p + o0 + pl * in1_plane));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(in1p + o1 + pl * in1_plane));
+          }
         }
         if (in2) {
           asm volatile("prefetch.global.L2 [%0];" ::"l"(in2 + ro));
@@ -282,7 +315,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_persistent(const GemmPa
       for (int cc = 0; cc < 2; ++cc) {
         const int ctile = hf * 64 + cc * 32;            // chunk's first column within the tile
         const int col0 = w.tn * 128 + ctile;
-        load8x4(in1, col0, pre);
+        load_in1(col0, pre);
         __syncwarp();
 #pragma unroll
         for (int q = 0; q < 8; ++q)

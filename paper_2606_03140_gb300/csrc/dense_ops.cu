@@ -26,18 +26,67 @@ __global__ void split_planes_kernel(const SubView* views, uint8_t* arena, int ns
   }
 }
 
-// out = a * in + b * I on the valid block, zero elsewhere (in may alias out).
+// Affine maps of a master onto one or two outputs, each written as master and / or split
+// planes, on the valid block (zero elsewhere): y = a x + b I.  kind 0: (a, b) given; kind 1:
+// SP2 start X0 = (emax I - h~) / (emax - emin); kind 2: its first-order change
+// dX0 = -dh~ / (emax - emin), with the spectral bounds of each subgraph.  One warp per row,
+// 8 consecutive columns per lane (one 16-byte granule of each plane).
+struct AffineOut {
+  const SubView* views;   // nullptr: no such output
+  double a, b;
+  int master;             // write the row-major master
+  int nsplit;             // planes to write (0: none)
+};
+
 template <typename T>
-__global__ void affine_kernel(const SubView* in_v, const SubView* out_v, uint8_t* arena, double a, double b) {
+__global__ void affine_planes_kernel(const SubView* in_v, AffineOut o1, AffineOut o2, int kind, const double* bounds,
+                                     uint8_t* arena) {
   const SubView vi = in_v[blockIdx.y];
-  const SubView vo = out_v[blockIdx.y];
-  const int row = blockIdx.x * 8 + (threadIdx.x >> 5);     // one warp per row
-  if (row >= vo.rows_pad) return;
+  const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= vi.rows_pad) return;
+  double a1 = o1.a, b1 = o1.b;
+  if (kind != 0) {
+    const double emin = bounds[2 * blockIdx.y], emax = bounds[2 * blockIdx.y + 1];
+    const double inv = 1.0 / (emax - emin);
+    a1 = -inv;
+    b1 = kind == 1 ? emax * inv : 0.0;
+  }
   const T* src = reinterpret_cast<const T*>(arena + vi.master) + (long long)row * vi.n_pad;
-  T* dst = reinterpret_cast<T*>(arena + vo.master) + (long long)row * vo.n_pad;
-  for (int c = threadIdx.x & 31; c < vo.n_pad; c += 32) {
-    const bool ok = row < vo.n_real && c < vo.n_real;
-    dst[c] = ok ? (T)(a * (double)src[c] + (row == c ? b : 0.0)) : (T)0;
+  for (int c8 = lane * 8; c8 < vi.n_pad; c8 += 256) {
+    double x[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) x[e] = (double)src[c8 + e];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const AffineOut& o = k == 0 ? o1 : o2;
+      if (!o.views) continue;
+      const SubView vo = o.views[blockIdx.y];
+      const double a = k == 0 ? a1 : o.a, b = k == 0 ? b1 : o.b;
+      float yf[8];
+      T y[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int c = c8 + e;
+        const bool ok = row < vi.n_real && c < vi.n_real;
+        y[e] = ok ? (T)(a * x[e] + (row == c ? b : 0.0)) : (T)0;
+        yf[e] = (float)y[e];
+      }
+      if (o.master) {
+        T* dst = reinterpret_cast<T*>(arena + vo.master) + (long long)row * vo.n_pad + c8;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) dst[e] = y[e];
+      }
+      if (o.nsplit > 0) {
+        __align__(16) __nv_bfloat16 h[8], m[8], l[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) split3(yf[e], h[e], m[e], l[e]);
+        const long long off = vo.planes + blocked_offset(row, c8, vo.n_pad);
+        *reinterpret_cast<uint4*>(arena + off) = *reinterpret_cast<const uint4*>(h);
+        if (o.nsplit > 1) *reinterpret_cast<uint4*>(arena + off + vo.plane_stride) = *reinterpret_cast<const uint4*>(m);
+        if (o.nsplit > 2) *reinterpret_cast<uint4*>(arena + off + 2 * vo.plane_stride) = *reinterpret_cast<const uint4*>(l);
+      }
+    }
   }
 }
 
@@ -87,41 +136,6 @@ __global__ void gersh_reduce_kernel(const SubView* views, const double* lo, cons
 
 // X0 = (emax I - h~) / (emax - emin) on the valid block (h~ is stored exactly symmetric:
 // its GEMM writes each off-diagonal tile and its transpose from the same values).
-template <typename T>
-__global__ void sp2_x0_kernel(const SubView* hv, const SubView* xv, uint8_t* arena, const double* bounds) {
-  const SubView vh = hv[blockIdx.y];
-  const SubView vx = xv[blockIdx.y];
-  const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (row >= vx.rows_pad) return;
-  const double emin = bounds[2 * blockIdx.y], emax = bounds[2 * blockIdx.y + 1];
-  const double inv = 1.0 / (emax - emin);
-  const T* h = reinterpret_cast<const T*>(arena + vh.master) + (long long)row * vh.n_pad;
-  T* x = reinterpret_cast<T*>(arena + vx.master) + (long long)row * vx.n_pad;
-  for (int c = threadIdx.x & 31; c < vx.n_pad; c += 32) {
-    T out = (T)0;
-    if (row < vx.n_real && c < vx.n_real) out = (T)(((row == c ? emax : 0.0) - (double)h[c]) * inv);
-    x[c] = out;
-  }
-}
-
-// dX0 = -dh~ / (emax - emin): first-order change of the SP2 start matrix.
-template <typename T>
-__global__ void sp2_dx0_kernel(const SubView* hv, const SubView* xv, uint8_t* arena, const double* bounds) {
-  const SubView vh = hv[blockIdx.y];
-  const SubView vx = xv[blockIdx.y];
-  const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (row >= vx.rows_pad) return;
-  const double inv = 1.0 / (bounds[2 * blockIdx.y + 1] - bounds[2 * blockIdx.y]);
-  const T* h = reinterpret_cast<const T*>(arena + vh.master) + (long long)row * vh.n_pad;
-  T* x = reinterpret_cast<T*>(arena + vx.master) + (long long)row * vx.n_pad;
-  for (int c = threadIdx.x & 31; c < vx.n_pad; c += 32) {
-    T out = (T)0;
-    if (row < vx.n_real && c < vx.n_real) out = (T)(-(double)h[c] * inv);
-    x[c] = out;
-  }
-}
-
-// State of a replay of the recorded SP2 branch sequence (fixed step count per subgraph).
 __global__ void sp2_replay_init_kernel(Sp2State* st, const double* bounds, const int* n_real, const int* steps,
                                        double mu, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -193,12 +207,15 @@ void launch_split_planes(const SubView* views, int n_sub, int max_rows, uint8_t*
   else split_planes_kernel<float><<<g, 64, 0, s>>>(views, arena, nsplit);
 }
 
-void launch_affine(const SubView* in, const SubView* out, int n_sub, int max_rows, uint8_t* arena, double a,
-                   double b, bool f64, cudaStream_t s) {
+void launch_affine_planes(const SubView* in, const SubView* out1, double a1, double b1, int master1, int nsplit1,
+                          const SubView* out2, double a2, double b2, int master2, int nsplit2, int kind,
+                          const double* bounds, int n_sub, int max_rows, uint8_t* arena, bool f64, cudaStream_t s) {
   if (n_sub <= 0 || max_rows <= 0) return;
   dim3 g((max_rows + 7) / 8, n_sub);
-  if (f64) affine_kernel<double><<<g, 256, 0, s>>>(in, out, arena, a, b);
-  else affine_kernel<float><<<g, 256, 0, s>>>(in, out, arena, a, b);
+  const AffineOut o1{out1, a1, b1, master1, f64 ? 0 : nsplit1};
+  const AffineOut o2{out2, a2, b2, master2, f64 ? 0 : nsplit2};
+  if (f64) affine_planes_kernel<double><<<g, 256, 0, s>>>(in, o1, o2, kind, bounds, arena);
+  else affine_planes_kernel<float><<<g, 256, 0, s>>>(in, o1, o2, kind, bounds, arena);
 }
 
 void launch_gershgorin(const SubView* views, int n_sub, int max_rows, const uint8_t* arena, double* lo, double* hi,
@@ -208,22 +225,6 @@ void launch_gershgorin(const SubView* views, int n_sub, int max_rows, const uint
   if (f64) gersh_rows_kernel<double><<<g, 256, 0, s>>>(views, arena, lo, hi, row_base);
   else gersh_rows_kernel<float><<<g, 256, 0, s>>>(views, arena, lo, hi, row_base);
   gersh_reduce_kernel<<<n_sub, 256, 0, s>>>(views, lo, hi, row_base, bounds);
-}
-
-void launch_sp2_x0(const SubView* hv, const SubView* xv, int n_sub, int max_rows, uint8_t* arena,
-                   const double* bounds, bool f64, cudaStream_t s) {
-  if (n_sub <= 0) return;
-  dim3 g((max_rows + 7) / 8, n_sub);
-  if (f64) sp2_x0_kernel<double><<<g, 256, 0, s>>>(hv, xv, arena, bounds);
-  else sp2_x0_kernel<float><<<g, 256, 0, s>>>(hv, xv, arena, bounds);
-}
-
-void launch_sp2_dx0(const SubView* hv, const SubView* xv, int n_sub, int max_rows, uint8_t* arena,
-                    const double* bounds, bool f64, cudaStream_t s) {
-  if (n_sub <= 0) return;
-  dim3 g((max_rows + 7) / 8, n_sub);
-  if (f64) sp2_dx0_kernel<double><<<g, 256, 0, s>>>(hv, xv, arena, bounds);
-  else sp2_dx0_kernel<float><<<g, 256, 0, s>>>(hv, xv, arena, bounds);
 }
 
 void launch_sp2_replay_init(Sp2State* st, const double* bounds, const int* n_real, const int* steps, double mu, int n,

@@ -17,14 +17,13 @@ struct SubView {
 
 void launch_split_planes(const SubView* views, int n_sub, int max_rows, uint8_t* arena, int nsplit, bool f64,
                          cudaStream_t s);
-void launch_affine(const SubView* in, const SubView* out, int n_sub, int max_rows, uint8_t* arena, double a,
-                   double b, bool f64, cudaStream_t s);
+// out1 = a1 in + b1 I (kind 0), the SP2 start (kind 1) or its first-order change (kind 2) from
+// the subgraph bounds; optional out2 = a2 in + b2 I.  Each output: master and / or nsplit planes.
+void launch_affine_planes(const SubView* in, const SubView* out1, double a1, double b1, int master1, int nsplit1,
+                          const SubView* out2, double a2, double b2, int master2, int nsplit2, int kind,
+                          const double* bounds, int n_sub, int max_rows, uint8_t* arena, bool f64, cudaStream_t s);
 void launch_gershgorin(const SubView* views, int n_sub, int max_rows, const uint8_t* arena, double* lo, double* hi,
                        const long long* row_base, double* bounds, bool f64, cudaStream_t s);
-void launch_sp2_x0(const SubView* hv, const SubView* xv, int n_sub, int max_rows, uint8_t* arena,
-                   const double* bounds, bool f64, cudaStream_t s);
-void launch_sp2_dx0(const SubView* hv, const SubView* xv, int n_sub, int max_rows, uint8_t* arena,
-                    const double* bounds, bool f64, cudaStream_t s);
 void launch_sp2_replay_init(Sp2State* st, const double* bounds, const int* n_real, const int* steps, double mu, int n,
                             cudaStream_t s);
 void launch_sp2_init(Sp2State* st, const double* bounds, const int* n_real, double mu, double tol, int kmax, int n,

@@ -337,6 +337,18 @@ sedacs_status build_op(sedacs_ctx* ctx, int id, int a, int b, int out, int mode,
     m.k_real = L.n_real[i];
     m.b_from_sp2 = b_from_sp2 ? 1 : 0;
     m.a_from_sp2 = a_from_sp2 ? 1 : 0;
+    // three-plane SP2 iterates carry no fp32 master: the SP2 epilogue and the consumers of X
+    // as an addend (C1) read the planes, whose sum is the fp32 value exactly
+    const bool x3 = !ctx->f64 && ctx->nsplit_sp2 == 3;
+    if (x3 && mode == kModeSp2) {
+      m.x_planes = 1;
+      m.out_off = -1;
+    }
+    if (x3 && mode == kModeGeneric && c1 == kX) {
+      m.c_off = pptr_(ctx, kX, i);
+      m.c_plane = ctx->slot[kX].plane_stride;
+      m.c_planes = 1;
+    }
     mats[i] = m;
     if (L.n_real[i] == 0) continue;
     const int tiles_n = L.n_pad[i] / ctx->tile;
@@ -540,7 +552,7 @@ sedacs_status rebuild_layout(sedacs_ctx* ctx) {
   // GEMM tables
   // S^-1/2 in deviation form: Y = I + E_y (kY*), Z = I + E_z (kZ*), T = I + E_t (kT);
   // only products of the small deviations go through the tensor cores.
-  STCHK(build_op(ctx, OP_NS_Y1, kY0, kT, kY1, kModeGeneric, 1.f, 0.f, false, false, kY0, 1.f, kT, 1.f, false, true));
+  STCHK(build_op(ctx, OP_NS_Y1, kY0, kZ1, kY1, kModeGeneric, 1.f, 0.f, false, false, kY0, 1.f, kZ1, 1.f, false, true));
   STCHK(build_op(ctx, OP_NS_T0, kZ0, kY0, kT, kModeGeneric, -0.5f, 0.f, false, false, kZ0, -0.5f, kY0, -0.5f, false, true));
   STCHK(build_op(ctx, OP_NS_T1, kZ1, kY1, kT, kModeGeneric, -0.5f, 0.f, false, false, kZ1, -0.5f, kY1, -0.5f, false, true));
   STCHK(build_op(ctx, OP_NS_Y0, kY0, kT, kY1, kModeGeneric, 1.f, 0.f, false, false, kY0, 1.f, kT, 1.f, false, true));
@@ -609,16 +621,12 @@ void compute_z(sedacs_ctx* ctx) {
   const Layout& L = ctx->lay;
   const int mr = max_rows(ctx);
   const int ns = ctx->nsplit_ns;
-  launch_affine(ctx->d_views[kS], ctx->d_views[kY0], L.n_sub, mr, ctx->arena, 1.0, -1.0, ctx->f64, s);   // E_y0 = s - I
-  launch_affine(ctx->d_views[kY0], ctx->d_views[kT], L.n_sub, mr, ctx->arena, -0.5, 0.0, ctx->f64, s);   // E_t = -E_y0/2
-  if (!ctx->f64) {
-    launch_split_planes(ctx->d_views[kY0], L.n_sub, mr, ctx->arena, ns, false, s);
-    launch_split_planes(ctx->d_views[kT], L.n_sub, mr, ctx->arena, ns, false, s);
-  }
+  // first step from Z0 = I: E_t = -E_y0 / 2 is also E_z1, so one pass writes E_y0 = s - I and
+  // E_z1 = -(s - I) / 2 (masters and planes), and E_y1 = E_y0 + E_z1 + E_y0 E_z1
+  launch_affine_planes(ctx->d_views[kS], ctx->d_views[kY0], 1.0, -1.0, 1, ns, ctx->d_views[kZ1], -0.5, 0.5, 1, ns, 0,
+                       nullptr, L.n_sub, mr, ctx->arena, ctx->f64, s);
   run_op(ctx, OP_NS_Y1, ns, ns);                       // E_y1
-  launch_affine(ctx->d_views[kT], ctx->d_views[kZ1], L.n_sub, mr, ctx->arena, 1.0, 0.0, ctx->f64, s);    // E_z1 = E_t
-  if (!ctx->f64) launch_split_planes(ctx->d_views[kZ1], L.n_sub, mr, ctx->arena, ns, false, s);
-  ctx->launches += ctx->f64 ? 3 : 6;
+  ctx->launches += 1;
   int c = 1;
   const int K = ctx->prm.ns_iters > 0 ? std::max(2, ctx->prm.ns_iters) : (ctx->f64 ? 4 : 3);
   for (int k = 2; k <= K; ++k) {
@@ -643,18 +651,54 @@ void compute_ht(sedacs_ctx* ctx) {
                   ctx->stream);
 }
 
+// SP2 start X0 = (emax I - h~) / (emax - emin) (and, for the response, dX0 = -dh~ / (emax - emin)).
+// Three-plane iterates are written as planes only (their sum is the fp32 value); the other
+// forms keep the master the epilogue reads.
+void launch_sp2_start(sedacs_ctx* ctx, bool with_dx) {
+  const Layout& L = ctx->lay;
+  const int n2 = ctx->nsplit_sp2;
+  const int x_master = (!ctx->f64 && n2 == 3) ? 0 : 1;
+  launch_affine_planes(ctx->d_views[kHt], ctx->d_views[kX], 0.0, 0.0, x_master, n2, nullptr, 0.0, 0.0, 0, 0, 1,
+                       ctx->d_bounds, L.n_sub, max_rows(ctx), ctx->arena, ctx->f64, ctx->stream);
+  if (with_dx)
+    launch_affine_planes(ctx->d_views[kdHt], ctx->d_views[kR2], 0.0, 0.0, 1, n2, nullptr, 0.0, 0.0, 0, 0, 2,
+                         ctx->d_bounds, L.n_sub, max_rows(ctx), ctx->arena, ctx->f64, ctx->stream);
+}
+
 // mu-branch SP2 (T -> 0 Fermi operator, Sec. "Density Matrix Evaluation on Partitioned Graphs").
 sedacs_status run_sp2(sedacs_ctx* ctx, double mu, int kmax) {
   cudaStream_t s = ctx->stream;
   const Layout& L = ctx->lay;
   const int mr = max_rows(ctx);
-  launch_sp2_x0(ctx->d_views[kHt], ctx->d_views[kX], L.n_sub, mr, ctx->arena, ctx->d_bounds, ctx->f64, s);
-  if (!ctx->f64) launch_split_planes(ctx->d_views[kX], L.n_sub, mr, ctx->arena, ctx->nsplit_sp2, false, s);
+  launch_sp2_start(ctx, false);
   launch_sp2_init(ctx->d_sp2, ctx->d_bounds, ctx->d_n_real, mu, ctx->prm.sp2_tol, kmax, L.n_sub, s);
-  ctx->launches += ctx->f64 ? 2 : 3;
-  if (!ctx->d_nactive) CUCHK(cudaMalloc(&ctx->d_nactive, sizeof(int)));
+  ctx->launches += 2;
+  if (ctx->h_nactive_cap < kmax) {
+    if (ctx->h_nactive) cudaFreeHost(ctx->h_nactive);
+    ctx->h_nactive = nullptr;
+    ctx->h_nactive_cap = 0;
+    CUCHK(cudaHostAlloc(reinterpret_cast<void**>(&ctx->h_nactive), sizeof(int) * kmax, cudaHostAllocDefault));
+    ctx->h_nactive_cap = kmax;
+    cudaFree(ctx->d_nactive);
+    ctx->d_nactive = nullptr;
+    CUCHK(cudaMalloc(&ctx->d_nactive, sizeof(int) * kmax));
+  }
+  while ((int)ctx->sp2_ev.size() < kmax) {
+    cudaEvent_t e;
+    CUCHK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    ctx->sp2_ev.push_back(e);
+  }
+  // Steps run while any subgraph is active.  The host keeps kLookahead steps queued: before
+  // queueing step k it waits for the count of step k - kLookahead; steps queued after the last
+  // subgraph stopped find no active tile and return at once.
+  constexpr int kLookahead = 3;
   const int ev0 = ctx->kev_used;
+  cudaMemsetAsync(ctx->d_nactive, 0, sizeof(int) * kmax, s);
   for (int k = 0; k < kmax; ++k) {
+    if (k >= kLookahead) {
+      CUCHK(cudaEventSynchronize(ctx->sp2_ev[k - kLookahead]));
+      if (ctx->h_nactive[k - kLookahead] == 0) break;
+    }
     const bool rec = ctx->kstats && ctx->kev_used + 2 <= (int)ctx->kev.size();
     if (rec) cudaEventRecord(ctx->kev[ctx->kev_used], s);
     run_op(ctx, OP_SP2, ctx->nsplit_sp2, ctx->nsplit_sp2);
@@ -662,15 +706,10 @@ sedacs_status run_sp2(sedacs_ctx* ctx, double mu, int kmax) {
       cudaEventRecord(ctx->kev[ctx->kev_used + 1], s);
       ctx->kev_used += 2;
     }
-    cudaMemsetAsync(ctx->d_nactive, 0, sizeof(int), s);
-    launch_sp2_advance(ctx->d_sp2, ctx->d_slots, ctx->d_tr_off, ctx->d_n_diag, ctx->d_nactive, L.n_sub, s);
+    launch_sp2_advance(ctx->d_sp2, ctx->d_slots, ctx->d_tr_off, ctx->d_n_diag, ctx->d_nactive + k, L.n_sub, s);
+    CUCHK(cudaMemcpyAsync(ctx->h_nactive + k, ctx->d_nactive + k, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUCHK(cudaEventRecord(ctx->sp2_ev[k], s));
     ctx->launches += 1;
-    if (k >= 6 && (k % 3 == 0 || k == kmax - 1)) {
-      int na = 0;
-      CUCHK(cudaMemcpyAsync(&na, ctx->d_nactive, sizeof(int), cudaMemcpyDeviceToHost, s));
-      CUCHK(cudaStreamSynchronize(s));
-      if (na == 0) break;
-    }
   }
   if (ctx->kstats) {
     CUCHK(cudaStreamSynchronize(s));
@@ -903,15 +942,10 @@ sedacs_status response_core(sedacs_ctx* ctx, const double* d_v, double* d_dq) {
   ctx->launches += 8;
   run_op(ctx, ctx->zc == 0 ? OP_DP0 : OP_DP1, ns, ns);
   run_op(ctx, ctx->zc == 0 ? OP_DHT0 : OP_DHT1, ns, ns);
-  launch_sp2_x0(ctx->d_views[kHt], ctx->d_views[kX], L.n_sub, mr, ctx->arena, ctx->d_bounds, ctx->f64, s);
-  launch_sp2_dx0(ctx->d_views[kdHt], ctx->d_views[kR2], L.n_sub, mr, ctx->arena, ctx->d_bounds, ctx->f64, s);
-  if (!ctx->f64) {
-    launch_split_planes(ctx->d_views[kX], L.n_sub, mr, ctx->arena, n2, false, s);
-    launch_split_planes(ctx->d_views[kR2], L.n_sub, mr, ctx->arena, n2, false, s);
-  }
+  launch_sp2_start(ctx, true);
   STCHK(upload_vec(ctx, &ctx->d_steps, ctx->sp2_iters_h));
   launch_sp2_replay_init(ctx->d_sp2, ctx->d_bounds, ctx->d_n_real, ctx->d_steps, ctx->mu, L.n_sub, s);
-  ctx->launches += 5;
+  ctx->launches += 3;
   int kmax = 0;
   for (int k : ctx->sp2_iters_h) kmax = std::max(kmax, k);
   if (!ctx->d_nactive) CUCHK(cudaMalloc(&ctx->d_nactive, sizeof(int)));
@@ -1159,6 +1193,9 @@ void sedacs_destroy(sedacs_ctx* ctx) {
     if (e) cudaEventDestroy(e);
   for (auto& e : ctx->kev)
     if (e) cudaEventDestroy(e);
+  for (auto& e : ctx->sp2_ev)
+    if (e) cudaEventDestroy(e);
+  if (ctx->h_nactive) cudaFreeHost(ctx->h_nactive);
   GnnState& G = ctx->gnn;
   for (void* p : {(void*)G.P, (void*)G.grad, (void*)G.m, (void*)G.v, (void*)G.act, (void*)G.part, (void*)G.ebas,
                   (void*)G.gu, (void*)G.u, (void*)G.pX, (void*)G.pV})

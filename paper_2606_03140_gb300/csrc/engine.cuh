@@ -180,6 +180,11 @@ struct sedacs_ctx {
   // timing of the SP2 square kernel (per launch, events on the context stream)
   bool kstats = false;
   std::vector<cudaEvent_t> kev;
+  // SP2 step control: per-step active counts copied into pinned host memory, one event per
+  // step, so that the host waits on a step a few launches back instead of draining the stream
+  int* h_nactive = nullptr;
+  int h_nactive_cap = 0;
+  std::vector<cudaEvent_t> sp2_ev;
   int kev_used = 0;
   double k_ms = 0.0, k_flops = 0.0;
   long long k_launches = 0;
