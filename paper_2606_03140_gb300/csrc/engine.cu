@@ -807,7 +807,8 @@ sedacs_status density_core(sedacs_ctx* ctx, double* mu_io, bool allow_resolve = 
   cudaStream_t s = ctx->stream;
   STCHK(prepare_geometry(ctx));
   phase_begin(ctx, 0);
-  CUCHK(ctx->ew.potential(ctx->d_n, ctx->d_V, s));
+  ctx->ew_tag = ctx->ew_tag % 1000000 + 1;
+  CUCHK(ctx->ew.potential(ctx->d_n, ctx->d_V, s, ctx->ew_tag));
   ctx->launches += 6;
   phase_end(ctx, 0, 1);
   phase_begin(ctx, 0);
@@ -869,7 +870,7 @@ sedacs_status forces_core(sedacs_ctx* ctx) {
   phase_begin(ctx, 0);
   STCHK(observe(ctx, true, nullptr));
   coul_a_kernel<<<nblk(ctx->N, 128), 128, 0, s>>>(ctx->d_q, ctx->d_n, ctx->d_tmp, ctx->N);
-  CUCHK(ctx->ew.gradient(ctx->d_tmp, ctx->d_n, ctx->d_F, s));
+  CUCHK(ctx->ew.gradient(ctx->d_tmp, ctx->d_n, ctx->d_F, s, ctx->ew_tag));
   add_kernel<<<nblk(3 * ctx->N, 256), 256, 0, s>>>(ctx->d_dU, ctx->d_F, 3 * ctx->N);
   launch_repulsion(ctx->model, ctx->d_R, ctx->d_species, sk_geom(ctx), ctx->d_pptr, ctx->d_pcol, ctx->N, ctx->d_erep,
                    ctx->d_dU, s);

@@ -14,7 +14,7 @@ struct EwaldGeom {
   int nmax[3];          // largest |m| per axis in reciprocal space
   int nmax_all;
   int nimg[3];          // periodic images needed in real space (small boxes)
-  int nc[3];            // cell grid (cells wider than rc)
+  int nc[3];            // cell grid (cells at least rc wide)
   int brute;            // 1: loop over all atoms and images
 };
 
@@ -40,7 +40,9 @@ struct Ewald {
   double* recip_buf = nullptr;
   double* rpart = nullptr;   // per-row-chunk partial sums
   double* scal = nullptr;
-  int *cell_of = nullptr, *cell_count = nullptr, *cell_start = nullptr, *cell_fill = nullptr, *cell_atoms = nullptr;
+  int *cell_of = nullptr, *cell_count = nullptr, *cell_start = nullptr, *cell_atoms = nullptr;
+  void* pos_s = nullptr;     // cell-sorted cell-relative coordinates and species (float4 / double4)
+  int sb_tag_ = 0;           // tag of the charges whose S(k) sits in vector 0 of ws (0: none)
   const double* dR_ = nullptr;
   const int* dspecies_ = nullptr;
   ~Ewald();
@@ -49,10 +51,11 @@ struct Ewald {
   cudaError_t setup(int N, const double box_A[3], const double hubbard_u[3], bool fp64, double tol);
   // Phase tables and cell list for positions dR (Angstrom, device, N x 3).
   cudaError_t prepare(const double* dR, const int* dspecies, cudaStream_t s);
-  // V = gamma b (Ha per e).
-  cudaError_t potential(const double* b, double* V, cudaStream_t s);
+  // V = gamma b (Ha per e).  A nonzero tag names b: a later gradient with the same tag and the
+  // same b reuses its structure factor (valid until the next prepare or potential call).
+  cudaError_t potential(const double* b, double* V, cudaStream_t s, int tag = 0);
   // G = d/dR (a^T gamma b) in Ha/A.
-  cudaError_t gradient(const double* a, const double* b, double* G, cudaStream_t s);
+  cudaError_t gradient(const double* a, const double* b, double* G, cudaStream_t s, int tag = 0);
 };
 
 }  // namespace sedacs
