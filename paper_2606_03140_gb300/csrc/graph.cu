@@ -6,8 +6,9 @@
 // The distance test uses separately rounded IEEE operations (no contraction into fused
 // multiply-adds) so the integer result is reproducible bit for bit:
 //   dx = (x_J - x_I) - L * rint((x_J - x_I) / L),  r2 = (dx*dx + dy*dy) + dz*dz < r_G*r_G.
-// Neighbour search uses a cell list with cells wider than r_G; every row is sorted and
-// de-duplicated in shared memory, then compacted into CSR.
+// Neighbour search uses a cell list with cells wider than r_G (one warp per atom over the
+// flattened candidates of the 27 neighbour cells); every row is sorted and de-duplicated in
+// shared memory, then compacted into CSR.
 //
 // Cores (Fig. 1b): recursive coordinate bisection of the wrapped coordinates
 // w = x - L * floor(x / L).  The split sizes follow from integers only
@@ -80,46 +81,71 @@ __global__ void cell_fill_kernel(const int* cell_of, int N, const int* cell_star
   cell_atoms[cell_start[c] + slot] = i;
 }
 
-// Visit every candidate j (cells around i, or all atoms) and call f(j) when r2 < rg2.
+// Warp per atom i: the candidates (atoms of the 27 cells around i's cell, or every atom when
+// the grid is too coarse) are flattened, lane l takes candidates l, l + 32, ...; the cell of a
+// flat index comes from a shuffle scan of the 27 cell counts and a shuffle binary search.
+// f(j, hit) is called by all lanes together once per round (hit false on idle lanes).
 template <typename F>
-__device__ __forceinline__ void for_each_distance_neighbour(const double* R, int N, int i, const CellGrid& g,
-                                                            const int* cell_of, const int* cell_start,
-                                                            const int* cell_count, const int* cell_atoms,
-                                                            double rg2, F f) {
+__device__ __forceinline__ void warp_distance_scan(const double* R, int N, int i, const CellGrid& g,
+                                                   const int* cell_of, const int* cell_start, const int* cell_count,
+                                                   const int* cell_atoms, double rg2, int lane, F f) {
   const double box[3] = {g.box[0], g.box[1], g.box[2]};
   const float rg2f = (float)rg2;
   auto within = [&](int j) {
     return g.exact ? (min_image_r2(R, i, j, box) < rg2) : (min_image_r2_f(R, i, j, box) < rg2f);
   };
   if (g.brute) {
-    for (int j = 0; j < N; ++j)
-      if (j != i && within(j)) f(j);
+    for (int b = 0; b < N; b += 32) {
+      const int j = b + lane;
+      f(j, j < N && j != i && within(j));
+    }
     return;
   }
   const int cid = cell_of[i];
   const int cz = cid % g.nc[2], cy = (cid / g.nc[2]) % g.nc[1], cx = cid / (g.nc[2] * g.nc[1]);
-  for (int dx = -1; dx <= 1; ++dx)
-    for (int dy = -1; dy <= 1; ++dy)
-      for (int dz = -1; dz <= 1; ++dz) {
-        const int x = (cx + dx + g.nc[0]) % g.nc[0];
-        const int y = (cy + dy + g.nc[1]) % g.nc[1];
-        const int z = (cz + dz + g.nc[2]) % g.nc[2];
-        const int c = (x * g.nc[1] + y) * g.nc[2] + z;
-        const int s = cell_start[c], n = cell_count[c];
-        for (int q = 0; q < n; ++q) {
-          const int j = cell_atoms[s + q];
-          if (j != i && within(j)) f(j);
-        }
-      }
+  int st = 0, cnt = 0;
+  if (lane < 27) {
+    const int x = (cx + lane / 9 - 1 + g.nc[0]) % g.nc[0];
+    const int y = (cy + (lane / 3) % 3 - 1 + g.nc[1]) % g.nc[1];
+    const int z = (cz + lane % 3 - 1 + g.nc[2]) % g.nc[2];
+    const int c = (x * g.nc[1] + y) * g.nc[2] + z;
+    st = cell_start[c];
+    cnt = cell_count[c];
+  }
+  int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const int excl = incl - cnt;
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  for (int b = 0; b < total; b += 32) {
+    const int t = b + lane;
+    int lo = 0;                                   // largest cell q < 27 with excl[q] <= t
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const int c = lo + step;
+      const int ex = __shfl_sync(0xffffffffu, excl, c & 31);
+      if (c < 27 && ex <= t) lo = c;
+    }
+    const int s0 = __shfl_sync(0xffffffffu, st, lo);
+    const int e0 = __shfl_sync(0xffffffffu, excl, lo);
+    int j = -1;
+    if (t < total) j = cell_atoms[s0 + (t - e0)];
+    f(j, t < total && j != i && within(j));
+  }
 }
 
 __global__ void count_dist_kernel(const double* R, int N, CellGrid g, const int* cell_of, const int* cell_start,
                                   const int* cell_count, const int* cell_atoms, double rg2, int* cnt) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (i >= N) return;
   int n = 0;
-  for_each_distance_neighbour(R, N, i, g, cell_of, cell_start, cell_count, cell_atoms, rg2, [&](int) { ++n; });
-  cnt[i] = n;
+  warp_distance_scan(R, N, i, g, cell_of, cell_start, cell_count, cell_atoms, rg2, lane,
+                     [&](int, bool hit) { n += __popc(__ballot_sync(0xffffffffu, hit)); });
+  if (lane == 0) cnt[i] = n;
 }
 
 __global__ void count_gd_kernel(const long long* gptr, const int* gcol, const double* gval, int N, double tau,
@@ -137,13 +163,43 @@ __global__ void count_gd_kernel(const long long* gptr, const int* gcol, const do
 __global__ void fill_dist_kernel(const double* R, int N, CellGrid g, const int* cell_of, const int* cell_start,
                                  const int* cell_count, const int* cell_atoms, double rg2, const long long* cptr,
                                  int* fillc, int* cand) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (i >= N) return;
   const long long base = cptr[i];
   int n = 0;
-  for_each_distance_neighbour(R, N, i, g, cell_of, cell_start, cell_count, cell_atoms, rg2,
-                              [&](int j) { cand[base + n++] = j; });
-  fillc[i] = n;
+  warp_distance_scan(R, N, i, g, cell_of, cell_start, cell_count, cell_atoms, rg2, lane, [&](int j, bool hit) {
+    const unsigned m = __ballot_sync(0xffffffffu, hit);
+    if (hit) cand[base + n + __popc(m & ((1u << lane) - 1u))] = j;
+    n += __popc(m);
+  });
+  if (lane == 0) fillc[i] = n;
+}
+
+// exclusive scan of the cell counts (one block)
+__global__ void cell_scan_kernel(const int* count, int ncell, int* start) {
+  __shared__ int part[1024];
+  const int per = (ncell + blockDim.x - 1) / blockDim.x;
+  const int b0 = threadIdx.x * per, b1 = min(ncell, b0 + per);
+  int s = 0;
+  for (int c = b0; c < b1; ++c) s += count[c];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int t = 0; t < (int)blockDim.x; ++t) {
+      const int v = part[t];
+      part[t] = acc;
+      acc += v;
+    }
+    start[ncell] = acc;
+  }
+  __syncthreads();
+  int acc = part[threadIdx.x];
+  for (int c = b0; c < b1; ++c) {
+    start[c] = acc;
+    acc += count[c];
+  }
 }
 
 __global__ void fill_gd_kernel(const long long* gptr, const int* gcol, const double* gval, int N, double tau,
@@ -428,16 +484,11 @@ cudaError_t GraphBuilder::build(const double* dR, int N, const double box[3], do
     cudaMemsetAsync(cell_count, 0, sizeof(int) * ncell, s);
     cudaMemsetAsync(cell_fill, 0, sizeof(int) * ncell, s);
     cell_assign_kernel<<<nb, TB, 0, s>>>(dR, N, g, cell_of, cell_count);
-    // exclusive scan of the cell counts on the host (cells are few)
-    std::vector<int> hc(ncell);
-    cudaMemcpyAsync(hc.data(), cell_count, sizeof(int) * ncell, cudaMemcpyDeviceToHost, s);
-    cudaStreamSynchronize(s);
-    std::vector<int> hs(ncell + 1, 0);
-    for (int c = 0; c < ncell; ++c) hs[c + 1] = hs[c] + hc[c];
-    cudaMemcpyAsync(cell_start, hs.data(), sizeof(int) * (ncell + 1), cudaMemcpyHostToDevice, s);
+    cell_scan_kernel<<<1, 1024, 0, s>>>(cell_count, ncell, cell_start);
     cell_fill_kernel<<<nb, TB, 0, s>>>(cell_of, N, cell_start, cell_fill, cell_atoms);
   }
-  count_dist_kernel<<<nb, TB, 0, s>>>(dR, N, g, cell_of, cell_start, cell_count, cell_atoms, rg2, cnt);
+  const int nbw = (N + 3) / 4;   // warp per atom, four per block
+  count_dist_kernel<<<nbw, 128, 0, s>>>(dR, N, g, cell_of, cell_start, cell_count, cell_atoms, rg2, cnt);
   if (gptr) count_gd_kernel<<<N, 64, 0, s>>>(gptr, gcol, gval, N, tau, cnt);
   scan_kernel<<<1, 1024, 0, s>>>(cnt, N, cptr);
   long long ncand = 0;
@@ -448,7 +499,7 @@ cudaError_t GraphBuilder::build(const double* dR, int N, const double box[3], do
     cap_cand = ncand + ncand / 4 + 1024;
     if ((e = cudaMalloc(&cand, sizeof(int) * cap_cand))) return e;
   }
-  fill_dist_kernel<<<nb, TB, 0, s>>>(dR, N, g, cell_of, cell_start, cell_count, cell_atoms, rg2, cptr, fillc, cand);
+  fill_dist_kernel<<<nbw, 128, 0, s>>>(dR, N, g, cell_of, cell_start, cell_count, cell_atoms, rg2, cptr, fillc, cand);
   if (gptr) fill_gd_kernel<<<N, 64, 0, s>>>(gptr, gcol, gval, N, tau, cptr, fillc, cand);
   const int cap = 8192;
   row_unique_kernel<<<N, 256, cap * sizeof(int), s>>>(cptr, cand, ucnt, derr, cap);
