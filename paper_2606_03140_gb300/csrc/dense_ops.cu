@@ -54,28 +54,39 @@ __global__ void affine_planes_kernel(const SubView* in_v, AffineOut o1, AffineOu
   }
   const T* src = reinterpret_cast<const T*>(arena + vi.master) + (long long)row * vi.n_pad;
   for (int c8 = lane * 8; c8 < vi.n_pad; c8 += 256) {
-    double x[8];
+    // arithmetic in T (FP32 for the mixed forms: the outputs are FP32 anyway)
+    T x[8];
+    if (sizeof(T) == 4) {
+      const float4 q0 = *reinterpret_cast<const float4*>(src + c8), q1 = *reinterpret_cast<const float4*>(src + c8 + 4);
+      x[0] = q0.x; x[1] = q0.y; x[2] = q0.z; x[3] = q0.w; x[4] = q1.x; x[5] = q1.y; x[6] = q1.z; x[7] = q1.w;
+    } else {
 #pragma unroll
-    for (int e = 0; e < 8; ++e) x[e] = (double)src[c8 + e];
+      for (int e = 0; e < 8; ++e) x[e] = src[c8 + e];
+    }
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       const AffineOut& o = k == 0 ? o1 : o2;
       if (!o.views) continue;
       const SubView vo = o.views[blockIdx.y];
-      const double a = k == 0 ? a1 : o.a, b = k == 0 ? b1 : o.b;
+      const T a = (T)(k == 0 ? a1 : o.a), b = (T)(k == 0 ? b1 : o.b);
       float yf[8];
       T y[8];
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
         const int c = c8 + e;
         const bool ok = row < vi.n_real && c < vi.n_real;
-        y[e] = ok ? (T)(a * x[e] + (row == c ? b : 0.0)) : (T)0;
+        y[e] = ok ? a * x[e] + (row == c ? b : (T)0) : (T)0;
         yf[e] = (float)y[e];
       }
       if (o.master) {
         T* dst = reinterpret_cast<T*>(arena + vo.master) + (long long)row * vo.n_pad + c8;
+        if (sizeof(T) == 4) {
+          reinterpret_cast<float4*>(dst)[0] = make_float4(yf[0], yf[1], yf[2], yf[3]);
+          reinterpret_cast<float4*>(dst)[1] = make_float4(yf[4], yf[5], yf[6], yf[7]);
+        } else {
 #pragma unroll
-        for (int e = 0; e < 8; ++e) dst[e] = y[e];
+          for (int e = 0; e < 8; ++e) dst[e] = y[e];
+        }
       }
       if (o.nsplit > 0) {
         __align__(16) __nv_bfloat16 h[8], m[8], l[8];
@@ -100,9 +111,25 @@ __global__ void gersh_rows_kernel(const SubView* views, const uint8_t* arena, do
   if (row >= v.n_real) return;
   const T* src = reinterpret_cast<const T*>(arena + v.master) + (long long)row * v.n_pad;
   double s = 0.0, d = 0.0;
-  for (int c = lane; c < v.n_real; c += 32) {
-    const double x = (double)src[c];
-    if (c == row) d = x; else s += fabs(x);
+  // four consecutive columns per lane and step (rows are 16-byte aligned, padding is zero);
+  // the four magnitudes are added in T, the running sum in FP64
+  for (int c4 = lane * 4; c4 < v.n_real; c4 += 128) {
+    T x[4];
+    if (sizeof(T) == 4) {
+      const float4 q = *reinterpret_cast<const float4*>(src + c4);
+      x[0] = q.x; x[1] = q.y; x[2] = q.z; x[3] = q.w;
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) x[e] = src[c4 + e];
+    }
+    T part = 0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const bool dg = (c4 + e) == row;
+      if (dg) d = (double)x[e];
+      else part += (c4 + e) < v.n_real ? fabs(x[e]) : (T)0;
+    }
+    s += (double)part;
   }
   s = warp_sum(s);
   d = warp_sum(d);

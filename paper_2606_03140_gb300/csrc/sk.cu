@@ -151,32 +151,49 @@ __global__ void loc_fill_kernel(const long long* sub_ptr, const int* sub_atoms, 
     L[sub_atoms[q]] = (int)(q - sub_ptr[i]);
 }
 
-// Orbital offsets of every subgraph atom (serial per subgraph: lists are short).
+// Orbital offsets of every subgraph atom: warp per subgraph, shuffle prefix sums over chunks
+// of 32 atoms.
 __global__ void orb_offsets_kernel(const long long* sub_ptr, const int* sub_atoms, const int* species, ModelDev m,
                                    int* orb_off, int* n_orb_sub, const int* n_core, int* n_core_orb, int n_sub) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (i >= n_sub) return;
-  int o = 0;
-  for (long long q = sub_ptr[i]; q < sub_ptr[i + 1]; ++q) {
-    if ((int)(q - sub_ptr[i]) == n_core[i]) n_core_orb[i] = o;
-    orb_off[q] = o;
-    o += m.n_orb[species[sub_atoms[q]]];
+  const long long q0 = sub_ptr[i], q1 = sub_ptr[i + 1];
+  const int nc = n_core[i];
+  int o = 0;                                   // orbitals before this chunk
+  for (long long qb = q0; qb < q1; qb += 32) {
+    const long long q = qb + lane;
+    const int n = q < q1 ? m.n_orb[species[sub_atoms[q]]] : 0;
+    int incl = n;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += v;
+    }
+    if (q < q1) {
+      orb_off[q] = o + incl - n;
+      if ((int)(q - q0) == nc) n_core_orb[i] = o + incl - n;
+    }
+    o += __shfl_sync(0xffffffffu, incl, 31);
   }
-  if ((int)(sub_ptr[i + 1] - sub_ptr[i]) == n_core[i]) n_core_orb[i] = o;
-  n_orb_sub[i] = o;
+  if (lane == 0) {
+    if ((int)(q1 - q0) == nc) n_core_orb[i] = o;
+    n_orb_sub[i] = o;
+  }
 }
 
-// Padded h (with the Coulomb shift) and s of every subgraph; one thread per subgraph atom row.
+// Padded h (with the Coulomb shift) and s of every subgraph; one warp per subgraph atom row,
+// lanes over the atom's pair list, each lane writing one atom-pair block.
 template <typename T>
 __global__ void gather_kernel(const ModelDev m, const long long* sub_ptr, const int* sub_atoms, const int* orb_off,
                               const int* species, const long long* pptr, const int* pcol, const T* h0b, const T* sb,
                               const int* loc, int N, const double* V, const long long* hoff, const long long* soff,
                               const int* n_pad, uint8_t* arena, int n_sub, const int* sub_of_row,
                               long long total_rows, int shift_only) {
-  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long q = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (q >= total_rows) return;
   const int i = sub_of_row[q];
-  const int a = (int)(q - sub_ptr[i]);
   const int A = sub_atoms[q];
   const int ld = n_pad[i];
   T* H = reinterpret_cast<T*>(arena + hoff[i]);
@@ -187,12 +204,13 @@ __global__ void gather_kernel(const ModelDev m, const long long* sub_ptr, const 
   const int* L = loc + (long long)i * N;
   const double va = V[A];
   // on-site block: eps + V_A on the diagonal of h, identity in s
-  for (int u = 0; u < na; ++u) {
+  if (lane < na) {
+    const int u = lane;
     const long long idx = (long long)(oa + u) * ld + (oa + u);
     H[idx] = (T)((shift_only ? 0.0 : (u == 0 ? m.eps_s[sa] : m.eps_p[sa])) + va);
     Sm[idx] = (T)1;
   }
-  for (long long p = pptr[A]; p < pptr[A + 1]; ++p) {
+  for (long long p = pptr[A] + lane; p < pptr[A + 1]; p += 32) {
     const int B = pcol[p];
     const int b = L[B];
     if (b < 0) continue;
@@ -332,14 +350,18 @@ __global__ void gd_kernel(const ModelDev m, const long long* sub_ptr, const int*
 }
 
 // Repulsion energy per atom (1/2 sum) and its gradient, over the pair CSR (images within r_off).
+// Warp per atom A, lanes over its pair-list entries; FP64 throughout, lane sums combined by a
+// fixed shuffle tree.
 __global__ void repulsion_kernel(const ModelDev m, const double* R, const int* species, SkGeom g,
                                  const long long* pptr, const int* pcol, int N, double* erep_atom, double* dU) {
-  const int A = blockIdx.x * blockDim.x + threadIdx.x;
+  const int A = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (A >= N) return;
   double e = 0.0, ga[3] = {0.0, 0.0, 0.0};
-  for (long long p = pptr[A]; p < pptr[A + 1]; ++p) {
+  const int sa = species[A];
+  for (long long p = pptr[A] + lane; p < pptr[A + 1]; p += 32) {
     const int B = pcol[p];
-    const double amp = m.rep_a[species[A]][species[B]];
+    const double amp = m.rep_a[sa][species[B]];
     if (amp == 0.0) continue;
     double d0[3];
     min_image(R, A, B, g.box, d0);
@@ -361,8 +383,12 @@ __global__ void repulsion_kernel(const ModelDev m, const double* R, const int* s
           for (int c = 0; c < 3; ++c) ga[c] -= de * d[c] / r;
         }
   }
-  erep_atom[A] = e;
-  for (int c = 0; c < 3; ++c) dU[3 * A + c] += ga[c];
+  e = warp_sum(e);
+  for (int c = 0; c < 3; ++c) ga[c] = warp_sum(ga[c]);
+  if (lane == 0) {
+    erep_atom[A] = e;
+    for (int c = 0; c < 3; ++c) dU[3 * A + c] += ga[c];
+  }
 }
 
 }  // namespace
@@ -380,8 +406,8 @@ void launch_loc_fill(const long long* sub_ptr, const int* sub_atoms, int* loc, i
 
 void launch_orb_offsets(const long long* sub_ptr, const int* sub_atoms, const int* species, const ModelDev& m,
                         int* orb_off, int* n_orb_sub, const int* n_core, int* n_core_orb, int n_sub, cudaStream_t s) {
-  orb_offsets_kernel<<<(n_sub + 63) / 64, 64, 0, s>>>(sub_ptr, sub_atoms, species, m, orb_off, n_orb_sub, n_core,
-                                                      n_core_orb, n_sub);
+  orb_offsets_kernel<<<(n_sub + 3) / 4, 128, 0, s>>>(sub_ptr, sub_atoms, species, m, orb_off, n_orb_sub, n_core,
+                                                     n_core_orb, n_sub);
 }
 
 void launch_gather(const ModelDev& m, const long long* sub_ptr, const int* sub_atoms, const int* orb_off,
@@ -390,7 +416,7 @@ void launch_gather(const ModelDev& m, const long long* sub_ptr, const int* sub_a
                    const int* n_pad, uint8_t* arena, int n_sub, const int* sub_of_row, long long total_rows,
                    int shift_only, bool f64, cudaStream_t s) {
   const int TB = 128;
-  const int nb = (int)((total_rows + TB - 1) / TB);
+  const int nb = (int)((32 * total_rows + TB - 1) / TB);   // warp per subgraph atom row
   if (f64)
     gather_kernel<double><<<nb, TB, 0, s>>>(m, sub_ptr, sub_atoms, orb_off, species, pptr, pcol, (const double*)h0b,
                                             (const double*)sb, loc, N, V, hoff, soff, n_pad, arena, n_sub, sub_of_row,
@@ -433,7 +459,7 @@ void launch_gd(const ModelDev& m, const long long* sub_ptr, const int* sub_atoms
 
 void launch_repulsion(const ModelDev& m, const double* R, const int* species, const SkGeom& g, const long long* pptr,
                       const int* pcol, int N, double* erep_atom, double* dU, cudaStream_t s) {
-  repulsion_kernel<<<(N + 127) / 128, 128, 0, s>>>(m, R, species, g, pptr, pcol, N, erep_atom, dU);
+  repulsion_kernel<<<(N + 3) / 4, 128, 0, s>>>(m, R, species, g, pptr, pcol, N, erep_atom, dU);
 }
 
 }  // namespace sedacs
