@@ -111,6 +111,9 @@ sedacs_status sedacs_set_device_io(sedacs_ctx* ctx, int32_t on, void* stream);
  * value exceeds tau in either direction.  gd: optional CSR over atoms of the previous
  * atom-condensed density graph (ptr [N+1] int64, col int32, val double; NULL = none).
  * use_prev_D != 0 takes the density graph of the last sedacs_subgraph_density call instead.
+ * A gd given here also serves the graph rebuilds of sedacs_scc_step / sedacs_xlbomd_init /
+ * sedacs_xlbomd_step until the context has computed a density of its own (a ground state
+ * handed over from another context keeps its graph).
  * The graph is kept in the context; *nnz receives its number of directed edges.
  * Integer result, bit-reproducible (separately rounded IEEE operations, no FMA). */
 sedacs_status sedacs_graph_build(sedacs_ctx* ctx, const double* R, const int64_t* gd_ptr, const int32_t* gd_col,

@@ -907,10 +907,16 @@ sedacs_status halos_core(sedacs_ctx* ctx) {
 }
 
 // one graph -> halos -> density cycle with the previous density graph
+// (the previous density graph is the context's own once it has computed a density; before
+// that, one given to sedacs_graph_build stands in for it)
 sedacs_status cycle(sedacs_ctx* ctx, double* mu) {
   phase_begin(ctx, 0);
-  STCHK(graph_core(ctx, ctx->have_gd ? ctx->d_gd_ptr : nullptr, ctx->have_gd ? ctx->d_gd_col : nullptr,
-                   ctx->have_gd ? ctx->d_gd_val : nullptr));
+  if (ctx->have_gd)
+    STCHK(graph_core(ctx, ctx->d_gd_ptr, ctx->d_gd_col, ctx->d_gd_val));
+  else if (ctx->have_xgd)
+    STCHK(graph_core(ctx, ctx->d_xgd_ptr, ctx->d_xgd_col, ctx->d_xgd_val));
+  else
+    STCHK(graph_core(ctx, nullptr, nullptr, nullptr));
   STCHK(halos_core(ctx));
   phase_end(ctx, 0, 0);
   return density_core(ctx, mu);
@@ -1246,6 +1252,7 @@ sedacs_status sedacs_graph_build(sedacs_ctx* ctx, const double* R, const int64_t
     CUCHK(cudaMemcpyAsync(ctx->d_xgd_col, gd_col, sizeof(int) * gd_nnz, cudaMemcpyDefault, ctx->stream));
     CUCHK(cudaMemcpyAsync(ctx->d_xgd_val, gd_val, sizeof(double) * gd_nnz, cudaMemcpyDefault, ctx->stream));
     gp = ctx->d_xgd_ptr; gc = ctx->d_xgd_col; gv = ctx->d_xgd_val;
+    ctx->have_xgd = true;
   }
   STCHK(graph_core(ctx, gp, gc, gv));
   if (nnz) *nnz = ctx->nnz;

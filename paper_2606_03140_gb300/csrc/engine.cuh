@@ -182,6 +182,7 @@ struct sedacs_ctx {
   std::vector<cudaEvent_t> kev;
   // SP2 step control: per-step active counts copied into pinned host memory, one event per
   // step, so that the host waits on a step a few launches back instead of draining the stream
+  bool have_xgd = false;  // a density graph was given to sedacs_graph_build (d_xgd_*)
   int ew_tag = 0;         // tag of the Coulomb potential of d_n at the current geometry
   int* h_nactive = nullptr;
   int h_nactive_cap = 0;

@@ -13,6 +13,7 @@
 // fixed order.  The potential kernel keeps each atom's Z row in shared memory and streams
 // the k-rows.  T = float for the mixed path (FP64 final sums), double for the plain path.
 #include <cmath>
+#include <mutex>
 #include <vector>
 #include "ewald.cuh"
 
@@ -659,12 +660,30 @@ cudaError_t Ewald::setup(int N, const double box_A[3], const double hubbard_u[3]
   return cudaSuccess;
 }
 
+// The dynamic shared-memory limit of a kernel is a process-wide attribute, while the size a
+// launch needs depends on the context's k set: the limit only ever grows (largest request of
+// any context so far), so a context never lowers it below what another one launches with.
+static std::mutex g_recip_smem_mutex;
+static int g_recip_smem[4] = {0, 0, 0, 0};
+
+template <typename T, int MODE>
+static void raise_recip_smem(int slot, int bytes) {
+  std::lock_guard<std::mutex> lock(g_recip_smem_mutex);
+  if (bytes > g_recip_smem[slot]) {
+    cudaFuncSetAttribute(recip_atom_kernel<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    g_recip_smem[slot] = bytes;
+  }
+}
+
 cudaError_t Ewald::prepare(const double* dR, const int* dspecies, cudaStream_t s) {
   const int W = 2 * m3max_ + 1;
-  cudaFuncSetAttribute(recip_atom_kernel<double, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(double2) * 64 * W);
-  cudaFuncSetAttribute(recip_atom_kernel<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(double2) * 64 * W);
-  cudaFuncSetAttribute(recip_atom_kernel<float, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(float2) * 128 * W);
-  cudaFuncSetAttribute(recip_atom_kernel<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(float2) * 128 * W);
+  if (fp64_) {
+    raise_recip_smem<double, 0>(0, (int)sizeof(double2) * 64 * W);
+    raise_recip_smem<double, 1>(1, (int)sizeof(double2) * 64 * W);
+  } else {
+    raise_recip_smem<float, 0>(2, (int)sizeof(float2) * 128 * W);
+    raise_recip_smem<float, 1>(3, (int)sizeof(float2) * 128 * W);
+  }
   const int TB = 128, nb = (N_ + TB - 1) / TB;
   if (fp64_) phase_table_kernel<double><<<nb, TB, 0, s>>>(dR, N_, g, reinterpret_cast<double2*>(tab));
   else phase_table_kernel<float><<<nb, TB, 0, s>>>(dR, N_, g, reinterpret_cast<float2*>(tab));

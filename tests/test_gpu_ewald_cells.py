@@ -38,3 +38,23 @@ def test_coulomb_potential_cells(box, precision):
     assert np.max(np.abs(V - Vref)) < TOL_V[precision]
     # the cell order is deterministic: a repeated call gives the same bits
     assert np.array_equal(V, V2)
+
+
+def test_contexts_of_both_forms_coexist(box):
+    """The FP64 k set of this box needs more shared memory per block than the mixed one; a
+    mixed context prepared after an FP64 one must not lower the limit the FP64 launches use."""
+    from paper_2606_03140_gb300 import sedacs as S
+
+    s, m, n, Vref = box
+    R = np.ascontiguousarray(s.R)
+    c0 = S.sedacs_create(s.species, s.box, m, S.sedacs_default_params(core_size=32, precision=0))
+    c1 = S.sedacs_create(s.species, s.box, m, S.sedacs_default_params(core_size=32, precision=1))
+    try:
+        Va = S.sedacs_coulomb_potential(c0, R, n)
+        S.sedacs_coulomb_potential(c1, R, n)
+        Vb = S.sedacs_coulomb_potential(c0, R, n)
+    finally:
+        S.sedacs_destroy(c0)
+        S.sedacs_destroy(c1)
+    assert np.array_equal(Va, Vb)
+    assert np.max(np.abs(Va - Vref)) < TOL_V[0]
