@@ -43,6 +43,7 @@ def test_scc_matches_oracle(ground, precision, tol):
         mu, resid, it, ok = S.sedacs_scc_step(ctx, R, n, max_iter=80)
         if precision == 0:
             assert ok and resid <= 1e-9
+        print(f"[parity] water96 SCC, form {precision}: max|dn| = {np.max(np.abs(n - n_ref)):.3e} e, {it} iterations")
         assert np.max(np.abs(n - n_ref)) < tol
         assert it < 40
     finally:
@@ -68,6 +69,8 @@ def test_xlbomd_trajectory_matches_oracle(ground):
         S.sedacs_destroy(ctx)
     # the GPU's FP64 SP2 stops at Tr(X - X^2) < 1e-9 n, the oracle diagonalises exactly:
     # agreement at that level (1e-8 Ha per atom)
+    print(f"[parity] water96 XL-BOMD 10 steps, FP64: max|dE_tot| = {np.max(np.abs(E[:, 2] - ref['energies'][1:, 2])):.3e} Ha, "
+          f"max|dR| = {np.max(np.abs(R - ref['R'])):.3e} A, max|dn| = {np.max(np.abs(nout - ref['n'])):.3e} e")
     assert np.max(np.abs(E[:, 2] - ref["energies"][1:, 2])) < 1e-6
     assert np.max(np.abs(R - ref["R"])) < 1e-8
     assert np.max(np.abs(nout - ref["n"])) < 1e-7

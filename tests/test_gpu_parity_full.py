@@ -73,5 +73,6 @@ def test_sampled_subgraph_charges_full_size(full):
     assert full["width"] > 0.05                      # mu sits in a clean window of the sampled spectra
     atoms = np.concatenate([full["cores"][i] for i in PICK])
     err = np.max(np.abs(full["q"][atoms] - res.q[atoms]))
+    print(f"[parity] water9000 form 1, sampled subgraphs: max|dq| = {err:.3e} e")
     assert err < 1e-5, err
     assert np.all(np.isfinite(full["F"]))

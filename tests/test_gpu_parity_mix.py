@@ -46,4 +46,5 @@ def test_mixture_graph_and_sampled_charges():
     finally:
         S.sedacs_destroy(ctx)
     atoms = np.concatenate([cores[i] for i in PICK])
+    print(f"[parity] mix9999 form 1, sampled subgraphs: max|dq| = {np.max(np.abs(q[atoms] - ref.q[atoms])):.3e} e")
     assert np.max(np.abs(q[atoms] - ref.q[atoms])) < 1e-5

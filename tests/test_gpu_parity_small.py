@@ -112,15 +112,18 @@ def test_density_stages_and_charges(S, sysdata, precision):
         mu_o, eh, el = odn.solve_mu([sg.eps for sg in ref.subs], [sg.w for sg in ref.subs], 256.0)
         assert eh < mu < el
         dq = np.max(np.abs(q - ref.q))
+        print(f"[parity] water96 form {precision}: max|dq| = {dq:.3e} e")
         assert dq < tol["q"], f"charges differ by {dq}"
         assert abs(eb - ref.e_band) / 96 < tol["e"]
         assert np.all(iters > 0) and np.all(iters < 60)
         # forces
         F = S.sedacs_forces(ctx, 96)
         Fref = odn.forces(ref, d["n"], s.R, s.species, s.box, d["m"])
+        print(f"[parity] water96 form {precision}: max|dF| = {np.max(np.abs(F - Fref)):.3e} Ha/A")
         assert np.max(np.abs(F - Fref)) < tol["F"], f"forces differ by {np.max(np.abs(F - Fref))}"
         e = S.sedacs_energy(ctx)
         eref = odn.shadow_energy(ref, d["n"], s.R, s.species, s.box, d["m"])
+        print(f"[parity] water96 form {precision}: |dE|/atom = {abs(e[3] - eref['total']) / 96:.3e} Ha")
         assert abs(e[3] - eref["total"]) / 96 < tol["e"]
         # density graph
         gp, gc, gv = S.sedacs_density_graph_get(ctx, 96)
