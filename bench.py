@@ -50,6 +50,22 @@ def parse():
 
 
 METRIC = "atoms*QMD-steps/s at |dq|<=1e-5 e vs FP64 oracle (mixed vs plain, one GB300)"
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the SP2 square kernel, averaged
+# over the SP2 launches of 2 timed steps of the 9,000-atom water workload in the mixed form (one
+# ncu capture, profiles/tc_gemm_sp2_traffic_water9000.md).  Reported only while the kernel
+# source is the one the counters were taken on.
+SP2_TRAFFIC = {"bytes_per_launch": 506.7e6, "workload": "water9000", "precision": 1,
+               "kernel_sha1": "fa7afaacd8c46a32a3324ab33f7cd7edc8eac0c7"}
+
+
+def kernel_sha1() -> str:
+    import hashlib
+    h = hashlib.sha1()
+    for f in ("dense_gemm.cu", "dense.cuh", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_2606_03140_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
 UNIT = "atom-steps/s"
 
 
@@ -258,7 +274,11 @@ def run_ours(args, world, rank, local):
     peak = bf16 / nsplit_products
     roof = {"kernel": "tc_gemm_persistent (SP2 square, split-bf16 tcgen05)", "bound": "tensor",
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "frac": (achieved / peak) if achieved else None,
+            "traffic": (SP2_TRAFFIC["bytes_per_launch"]
+                        if (kernel_sha1() == SP2_TRAFFIC["kernel_sha1"] and args.workload == SP2_TRAFFIC["workload"]
+                            and args.precision == SP2_TRAFFIC["precision"]) else None),
+            "traffic_unit": "bytes per launch (DRAM read + write, ncu, average over the SP2 launches)",
             "peak_note": f"measured sustained bf16 {bf16} TF/s / {nsplit_products} split products (of measured)",
             "launches": k_launch, "kernel_ms": k_ms}
     drift = float(E[-1, 2] - E[0, 2])
