@@ -159,48 +159,15 @@ def allmax(world, x: float) -> float:
 
 
 def setup_system(S, I, workload: str, precision: int, seed_v: int = 20260703, quick: bool = False):
-    """SCC ground state, mu in the gap and Maxwell-Boltzmann velocities; returns a context ready for XL-BOMD.
+    """SCC ground state and velocities, context ready for XL-BOMD (paper_2606_03140_gb300.runs)."""
+    from paper_2606_03140_gb300 import runs
 
-    The plain FP64 form (precision 0) takes the ground state computed by the mixed form (the
-    charges, mu and density graph are handed over), so both forms time the same dynamics."""
-    s = I.workload(workload)
-    model = I.default_model()
-    R = np.ascontiguousarray(s.R.copy())
-    n = np.zeros(s.n_atoms)
-    V = np.ascontiguousarray(I.maxwell_boltzmann(s.species, 300.0, seed_v, model))
-    # ground state by the kernel-accelerated quasi-Newton SCC (SI Sec. C), rank-4 Krylov
-    prm = S.sedacs_default_params(core_size=32, precision=precision if precision > 0 else 1, scc_tol=2e-5,
-                                  kernel=1, krylov_rank=4)
-    ctx = S.sedacs_create(s.species, s.box, model, prm)
-    S.sedacs_graph_build(ctx, R)
-    S.sedacs_partition(ctx, R)
-    it = it2 = 0
-    res2 = None
-    if quick:
-        mu, _, _, _ = S.sedacs_subgraph_density(ctx, R, n)
-        S.sedacs_graph_build(ctx, R, use_prev_D=True)
-    else:
-        mu, res, it, ok = S.sedacs_scc_step(ctx, R, n, max_iter=60)
-        # place mu in the middle of the gap of the final graph, then settle the charges again
-        mu, q, _, _ = S.sedacs_subgraph_density(ctx, R, n)
-        mu, res2, it2, ok2 = S.sedacs_scc_step(ctx, R, n, max_iter=30, mu=mu)
-    if not quick and not (res2 is not None and res2 < 1e-3):
+    try:
+        return runs.ground_state(workload, precision, seed_v=seed_v, quick=quick)
+    except runs.NoGroundState as e:
         # XL-BOMD starts from the SCC ground state; timing dynamics from an unconverged start
         # would time charge oscillations, not the method
-        raise SystemExit(f"{workload}: SCC ground state not reached (max residual {res2}); the zero-temperature "
-                         "SCC does not converge for this workload, so it is not an MD benchmark")
-    if precision == 0:
-        gd = S.sedacs_density_graph_get(ctx, s.n_atoms)
-        S.sedacs_destroy(ctx)
-        prm = S.sedacs_default_params(core_size=32, precision=0)
-        ctx = S.sedacs_create(s.species, s.box, model, prm)
-        S.sedacs_graph_build(ctx, R, gd=gd)
-        S.sedacs_partition(ctx, R)
-    # dynamics with the scaled-delta kernel K0 = -c I (SI Sec. B; adequate for a large gap)
-    prm.kernel = 0
-    S.sedacs_set_params(ctx, prm)
-    S.sedacs_xlbomd_init(ctx, R, V, n, mu)
-    return s, model, ctx, R, V, n, {"scc_iters": it + it2, "scc_resid": res2, "mu": mu}
+        raise SystemExit(f"{e}; it is not an MD benchmark")
 
 
 def run_ours(args, world, rank, local):

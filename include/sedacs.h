@@ -169,7 +169,10 @@ sedacs_status sedacs_kernel_apply(sedacs_ctx* ctx, const double* f, double* u, i
 
 /* ---- a12: self-consistent charges (Sec. "Determining the Subgraphs", SI Sec. C).  Starting
  * from n (inout), iterates graph -> halos -> density -> n update until max |q - n| <= scc_tol
- * (linear mixing, or the kernel quasi-Newton step once max |q - n| < 0.1 when kernel = 1).
+ * (linear mixing, or the kernel quasi-Newton step n <- n - K (q - n) once max |q - n| < 0.1 when
+ * kernel = 1 (rank-m Krylov) or 2 (learned)).  When max |q - n| has not fallen by 10 % over 8
+ * iterations, mu is placed in the middle of the current gap again (a kept mu can end up at a band
+ * edge as the charges move the levels).
  * Cores must exist (sedacs_partition / sedacs_set_cores).  mu inout as in sedacs_subgraph_density. */
 sedacs_status sedacs_scc_step(sedacs_ctx* ctx, const double* R, double* n, int32_t max_iter, double* mu,
                               double* resid_max, int32_t* iters);

@@ -45,14 +45,17 @@ class GraphParams:
     core_size: int = 12
 
 
-def graph_and_halos(R, box, gp: GraphParams, cores, gd):
-    row_ptr, col = graph.build_graph(R, box, gp.r_graph, gd, gp.tau)
+def graph_and_halos(R, box, gp: GraphParams, cores, gd, keep=None):
+    row_ptr, col = graph.build_graph(R, box, gp.r_graph, gd, gp.tau, keep)
     return row_ptr, col, graph.halos(row_ptr, col, cores)
 
 
 def scc(R, species, box, model, gp: GraphParams, n0=None, max_iter: int = 300, tol: float = 1e-8,
         alpha: float = 0.2, cores=None, gd=None, krylov_rank: int = 0, c_k0: float = 0.5):
-    """Self-consistent charges.  Returns (n, density result, iterations, residual history)."""
+    """Self-consistent charges.  Returns (n, density result, iterations, residual history).
+
+    Each iteration rebuilds the graph from the latest density graph; from the second iteration on
+    the new graph also keeps every edge of the previous one."""
     N = R.shape[0]
     if cores is None:
         cores = graph.rcb_partition(R, box, gp.core_size)
@@ -60,8 +63,12 @@ def scc(R, species, box, model, gp: GraphParams, n0=None, max_iter: int = 300, t
     hist = []
     res = None
     it = 0
+    prev = None
     for it in range(1, max_iter + 1):
-        _, _, hal = graph_and_halos(R, box, gp, cores, gd)
+        # from the second iteration on the graph keeps the edges it had (SCF iterations add edges
+        # and do not remove them, Sec. "Determining the Subgraphs"), so halos only grow
+        rp, col, hal = graph_and_halos(R, box, gp, cores, gd, prev)
+        prev = (rp, col)
         res = dn.density(R, species, box, model, n, cores, hal)
         f = res.q - n
         r = float(np.max(np.abs(f)))

@@ -35,12 +35,14 @@ def min_image_r2(R: np.ndarray, box: np.ndarray, i: int, js: np.ndarray) -> np.n
     return (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2]
 
 
-def build_graph(R: np.ndarray, box: np.ndarray, r_graph: float, gd=None, tau: float = 0.0):
+def build_graph(R: np.ndarray, box: np.ndarray, r_graph: float, gd=None, tau: float = 0.0, keep=None):
     """Symmetric CSR (row_ptr int64, col int32, columns ascending) of the atom graph.
 
     gd: optional previous atom-condensed density graph as (ptr, col, val) CSR over
     atoms (rows need not be symmetric); an entry with val > tau adds edge (I, J)
     and (J, I).
+    keep: optional previous graph (row_ptr, col) whose edges are all kept (during the
+    initial SCF, edges are added and not removed: Sec. "Determining the Subgraphs").
     """
     R = np.asarray(R, dtype=np.float64)
     box = np.asarray(box, dtype=np.float64)
@@ -62,6 +64,11 @@ def build_graph(R: np.ndarray, box: np.ndarray, r_graph: float, gd=None, tau: fl
                 if j != i and val[p] > tau:
                     adj[i].add(j)
                     adj[j].add(i)
+    if keep is not None:
+        kp, kc = keep
+        for i in range(N):
+            for p in range(int(kp[i]), int(kp[i + 1])):
+                adj[i].add(int(kc[p]))
     row_ptr = np.zeros(N + 1, dtype=np.int64)
     cols = []
     for i in range(N):

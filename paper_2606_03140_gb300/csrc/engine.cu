@@ -884,13 +884,14 @@ sedacs_status forces_core(sedacs_ctx* ctx) {
   return check_dev_err(ctx);
 }
 
-sedacs_status graph_core(sedacs_ctx* ctx, const long long* gptr, const int* gcol, const double* gval) {
+sedacs_status graph_core(sedacs_ctx* ctx, const long long* gptr, const int* gcol, const double* gval,
+                         bool keep_prev = false) {
   cudaStream_t s = ctx->stream;
   CUCHK(grow(&ctx->d_row_ptr, &ctx->rows_cap, (long long)ctx->N + 1) == cudaSuccess ? cudaSuccess
                                                                                    : cudaErrorMemoryAllocation);
   long long nnz = 0;
   CUCHK(ctx->gb.build(ctx->d_R, ctx->N, ctx->box, ctx->prm.r_graph, gptr, gcol, gval, ctx->prm.tau, ctx->d_row_ptr,
-                      &ctx->d_col, &ctx->col_cap, &nnz, ctx->d_err, s));
+                      &ctx->d_col, &ctx->col_cap, &nnz, ctx->d_err, s, true, keep_prev && ctx->have_graph));
   ctx->launches += 9;
   ctx->nnz = nnz;
   ctx->have_graph = true;
@@ -908,15 +909,16 @@ sedacs_status halos_core(sedacs_ctx* ctx) {
 
 // one graph -> halos -> density cycle with the previous density graph
 // (the previous density graph is the context's own once it has computed a density; before
-// that, one given to sedacs_graph_build stands in for it)
-sedacs_status cycle(sedacs_ctx* ctx, double* mu) {
+// that, one given to sedacs_graph_build stands in for it).  keep_prev: the current graph keeps
+// its edges (SCC iterations add edges and do not remove them, Sec. "Determining the Subgraphs").
+sedacs_status cycle(sedacs_ctx* ctx, double* mu, bool keep_prev = false) {
   phase_begin(ctx, 0);
   if (ctx->have_gd)
-    STCHK(graph_core(ctx, ctx->d_gd_ptr, ctx->d_gd_col, ctx->d_gd_val));
+    STCHK(graph_core(ctx, ctx->d_gd_ptr, ctx->d_gd_col, ctx->d_gd_val, keep_prev));
   else if (ctx->have_xgd)
-    STCHK(graph_core(ctx, ctx->d_xgd_ptr, ctx->d_xgd_col, ctx->d_xgd_val));
+    STCHK(graph_core(ctx, ctx->d_xgd_ptr, ctx->d_xgd_col, ctx->d_xgd_val, keep_prev));
   else
-    STCHK(graph_core(ctx, nullptr, nullptr, nullptr));
+    STCHK(graph_core(ctx, nullptr, nullptr, nullptr, keep_prev));
   STCHK(halos_core(ctx));
   phase_end(ctx, 0, 0);
   return density_core(ctx, mu);
@@ -1440,13 +1442,28 @@ sedacs_status sedacs_scc_step(sedacs_ctx* ctx, const double* R, double* n, int32
   double m = *mu, r = 0.0;
   int it = 0;
   cudaStream_t s = ctx->stream;
+  // mu is placed in the gap once and kept while the count stays in its window; as the charges
+  // move the levels, a kept mu can end up next to a band edge where occupations flicker and the
+  // iteration stalls.  When the residual has not fallen by 10 % over 8 iterations, mu is placed
+  // in the middle of the current gap again.
+  double r_best = std::numeric_limits<double>::infinity();
+  int stalled = 0;
   for (it = 1; it <= max_iter; ++it) {
-    STCHK(cycle(ctx, &m));
+    STCHK(cycle(ctx, &m, it > 1));
     maxdiff_kernel<<<1, 1024, 0, s>>>(ctx->d_q, ctx->d_n, ctx->N, ctx->d_scal + 4);
     r = host_scalar(ctx, ctx->d_scal + 4);
     if (r <= ctx->prm.scc_tol) break;
-    if (ctx->prm.kernel == 1 && r < 0.1) {
-      // quasi-Newton step n <- n - (K0 J)^-1 K0 (q - n)  (SI Sec. C)
+    if (r < 0.9 * r_best) {
+      r_best = r;
+      stalled = 0;
+    } else if (++stalled >= 8) {
+      STCHK(solve_mu(ctx, &m));
+      stalled = 0;
+      r_best = std::numeric_limits<double>::infinity();
+    }
+    if (ctx->prm.kernel >= 1 && r < 0.1) {
+      // quasi-Newton step n <- n - K (q - n) with the rank-m Krylov kernel (K0 J)^-1 K0 or the
+      // learned one (SI Sec. C)
       double* f = ctx->d_vec + 20LL * ctx->N;
       double* u = ctx->d_vec + 21LL * ctx->N;
       sub_kernel<<<nblk(ctx->N, 128), 128, 0, s>>>(f, ctx->d_q, ctx->d_n, ctx->N);

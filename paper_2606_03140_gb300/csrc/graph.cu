@@ -202,6 +202,23 @@ __global__ void cell_scan_kernel(const int* count, int ncell, int* start) {
   }
 }
 
+// Candidates from a previous (symmetric) graph: every edge is kept (used while the SCC grows
+// its graph, edges added and not removed).
+__global__ void count_prev_kernel(const long long* pptr, int N, int* cnt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) cnt[i] += (int)(pptr[i + 1] - pptr[i]);
+}
+
+__global__ void fill_prev_kernel(const long long* pptr, const int* pcol, int N, const long long* cptr, int* fillc,
+                                 int* cand) {
+  const int i = blockIdx.x;
+  const long long b = pptr[i], e = pptr[i + 1];
+  const int base = fillc[i];
+  for (long long p = b + threadIdx.x; p < e; p += blockDim.x) cand[cptr[i] + base + (p - b)] = pcol[p];
+  __syncthreads();
+  if (threadIdx.x == 0) fillc[i] = base + (int)(e - b);
+}
+
 __global__ void fill_gd_kernel(const long long* gptr, const int* gcol, const double* gval, int N, double tau,
                                const long long* cptr, int* fillc, int* cand) {
   const int i = blockIdx.x;
@@ -455,7 +472,8 @@ static CellGrid make_grid(const double box[3], double rc, int exact = 1) {
 
 cudaError_t GraphBuilder::build(const double* dR, int N, const double box[3], double r_graph, const long long* gptr,
                                 const int* gcol, const double* gval, double tau, long long* row_ptr, int** col_out,
-                                long long* col_cap, long long* nnz_host, int* derr, cudaStream_t s, bool exact) {
+                                long long* col_cap, long long* nnz_host, int* derr, cudaStream_t s, bool exact,
+                                bool keep_prev) {
   cudaError_t e;
   CellGrid g = make_grid(box, r_graph, exact ? 1 : 0);
   const int ncell = g.nc[0] * g.nc[1] * g.nc[2];
@@ -490,6 +508,9 @@ cudaError_t GraphBuilder::build(const double* dR, int N, const double box[3], do
   const int nbw = (N + 3) / 4;   // warp per atom, four per block
   count_dist_kernel<<<nbw, 128, 0, s>>>(dR, N, g, cell_of, cell_start, cell_count, cell_atoms, rg2, cnt);
   if (gptr) count_gd_kernel<<<N, 64, 0, s>>>(gptr, gcol, gval, N, tau, cnt);
+  // keep_prev: the edges of the graph currently in row_ptr / col_out are candidates as well (they
+  // are read here, before the new graph overwrites them)
+  if (keep_prev) count_prev_kernel<<<nb, TB, 0, s>>>(row_ptr, N, cnt);
   scan_kernel<<<1, 1024, 0, s>>>(cnt, N, cptr);
   long long ncand = 0;
   cudaMemcpyAsync(&ncand, cptr + N, sizeof(long long), cudaMemcpyDeviceToHost, s);
@@ -501,6 +522,7 @@ cudaError_t GraphBuilder::build(const double* dR, int N, const double box[3], do
   }
   fill_dist_kernel<<<nbw, 128, 0, s>>>(dR, N, g, cell_of, cell_start, cell_count, cell_atoms, rg2, cptr, fillc, cand);
   if (gptr) fill_gd_kernel<<<N, 64, 0, s>>>(gptr, gcol, gval, N, tau, cptr, fillc, cand);
+  if (keep_prev) fill_prev_kernel<<<N, 64, 0, s>>>(row_ptr, *col_out, N, cptr, fillc, cand);
   const int cap = 8192;
   row_unique_kernel<<<N, 256, cap * sizeof(int), s>>>(cptr, cand, ucnt, derr, cap);
   scan_kernel<<<1, 1024, 0, s>>>(ucnt, N, row_ptr);

@@ -28,10 +28,12 @@ struct GraphBuilder {
   void release();
   // Builds the symmetric CSR of the atom graph into row_ptr (device, N+1) and *col_out
   // (device, grown as needed).  gptr/gcol/gval: optional device CSR of the previous
-  // atom-condensed density graph.
+  // atom-condensed density graph.  keep_prev: the graph already in row_ptr / *col_out keeps all
+  // its edges (the new graph is its union with the rule's edges).
   cudaError_t build(const double* dR, int N, const double box[3], double r_graph, const long long* gptr,
                     const int* gcol, const double* gval, double tau, long long* row_ptr, int** col_out,
-                    long long* col_cap, long long* nnz_host, int* derr, cudaStream_t s, bool exact = true);
+                    long long* col_cap, long long* nnz_host, int* derr, cudaStream_t s, bool exact = true,
+                    bool keep_prev = false);
 };
 
 struct Partitioner {

@@ -1,0 +1,62 @@
+"""Run drivers on top of the C ABI: the SCC ground state an XL-BOMD run starts from.
+
+Used by bench.py and by the trajectory tool (python -m paper_2606_03140_gb300.md).  Argument
+marshalling and orchestration only: every step runs in the library's kernels.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import inputs as I
+from . import sedacs as S
+
+
+class NoGroundState(RuntimeError):
+    """The zero-temperature SCC did not reach the ground state."""
+
+
+def ground_state(workload: str, precision: int, seed_v: int = 20260703, quick: bool = False,
+                 core_size: int = 32):
+    """SCC ground state, mu in the gap and Maxwell-Boltzmann velocities at 300 K.
+
+    Returns (system, model, ctx, R, V, n, info) with ctx ready for sedacs_xlbomd_init (kernel
+    K0).  The ground state comes from the kernel-accelerated quasi-Newton SCC (SI Sec. C, rank-4
+    Krylov) in the mixed form; the plain FP64 form (precision 0) receives its charges, mu and
+    density graph, so both forms start from the same state.  quick=True starts from zero charges
+    (same per-step work, no SCC)."""
+    s = I.workload(workload)
+    model = I.default_model()
+    R = np.ascontiguousarray(s.R.copy())
+    n = np.zeros(s.n_atoms)
+    V = np.ascontiguousarray(I.maxwell_boltzmann(s.species, 300.0, seed_v, model))
+    prm = S.sedacs_default_params(core_size=core_size, precision=precision if precision > 0 else 1,
+                                  scc_tol=2e-5, kernel=1, krylov_rank=4)
+    ctx = S.sedacs_create(s.species, s.box, model, prm)
+    S.sedacs_graph_build(ctx, R)
+    S.sedacs_partition(ctx, R)
+    it = it2 = 0
+    res2 = None
+    if quick:
+        mu, _, _, _ = S.sedacs_subgraph_density(ctx, R, n)
+        S.sedacs_graph_build(ctx, R, use_prev_D=True)
+    else:
+        mu, res, it, ok = S.sedacs_scc_step(ctx, R, n, max_iter=60)
+        # place mu in the middle of the gap of the final graph, then settle the charges again
+        mu, q, _, _ = S.sedacs_subgraph_density(ctx, R, n)
+        mu, res2, it2, ok2 = S.sedacs_scc_step(ctx, R, n, max_iter=30, mu=mu)
+        if not (res2 < 1e-3):
+            S.sedacs_destroy(ctx)
+            raise NoGroundState(f"{workload}: SCC ground state not reached (max residual {res2}); the "
+                                "zero-temperature SCC does not converge for this workload")
+    if precision == 0:
+        gd = S.sedacs_density_graph_get(ctx, s.n_atoms)
+        S.sedacs_destroy(ctx)
+        prm = S.sedacs_default_params(core_size=core_size, precision=0)
+        ctx = S.sedacs_create(s.species, s.box, model, prm)
+        S.sedacs_graph_build(ctx, R, gd=gd)
+        S.sedacs_partition(ctx, R)
+    # dynamics with the scaled-delta kernel K0 = -c I (SI Sec. B; adequate for a large gap)
+    prm.kernel = 0
+    S.sedacs_set_params(ctx, prm)
+    S.sedacs_xlbomd_init(ctx, R, V, n, mu)
+    return s, model, ctx, R, V, n, {"scc_iters": it + it2, "scc_resid": res2, "mu": mu}

@@ -111,3 +111,21 @@ def test_halo_brute_force():
     for c, h in zip(cores, hal):
         ref = sorted({j for (i, j) in E if i in set(c)} - set(c))
         assert list(h) == ref
+
+
+def test_graph_keep_is_union_of_kept_and_rule_edges():
+    """SCF graphs keep the edges they had: the graph built with keep= is the set union of the
+    kept graph's edges and the rule's own edges (brute force on a small box)."""
+    s = I.small_water_box(8, 7.0, seed=12)
+    N = s.n_atoms
+    rp1, c1 = graph.build_graph(s.R, s.box, 2.2)              # a sparser graph to keep
+    shifted = s.R + 0.3 * np.random.default_rng(3).standard_normal(s.R.shape)
+    rp2, c2 = graph.build_graph(shifted, s.box, 3.0)          # the rule's edges at another geometry
+    rpu, cu = graph.build_graph(shifted, s.box, 3.0, keep=(rp1, c1))
+    for i in range(N):
+        want = set(c1[rp1[i]:rp1[i + 1]].tolist()) | set(c2[rp2[i]:rp2[i + 1]].tolist())
+        got = cu[rpu[i]:rpu[i + 1]].tolist()
+        assert got == sorted(want)
+    # symmetric
+    edges = {(i, int(j)) for i in range(N) for j in cu[rpu[i]:rpu[i + 1]]}
+    assert all((j, i) in edges for i, j in edges)
