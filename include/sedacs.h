@@ -192,9 +192,10 @@ sedacs_status sedacs_xlbomd_step(sedacs_ctx* ctx, double* R, double* V, int32_t 
  * graph that is linear in y (species embedding times y, radial edge filters of the minimum-image
  * distance with a 6 A cosine cutoff, residual 64 x 64 mixes, linear read-out).  Parameters are a
  * flat FP64 vector of sedacs_gnn_num_params() entries (device copy in FP32): e[3][64], then per
- * layer C[8][64], A[64][64], B[64][64], then w[64].  Trained by Adam on pairs (x = J v, v) of the
- * Krylov kernel's responses (SI Sec. B): with kernel 1 and collection on, every Krylov vector
- * adds a pair to a ring of `capacity` pairs (device memory). */
+ * layer C[8][64], A[64][64], B[64][64], then w[64].  Trained by Adam on pairs of the Krylov
+ * kernel (SI Sec. B): with kernel 1 and collection on, every Krylov vector adds the pair
+ * (x = J v, v) and every kernel application the pair (f, K_m f) to a ring of `capacity` pairs
+ * (device memory). */
 int32_t sedacs_gnn_num_params(void);
 sedacs_status sedacs_gnn_init(sedacs_ctx* ctx, uint64_t seed);
 sedacs_status sedacs_gnn_set_params(sedacs_ctx* ctx, const double* p);

@@ -155,7 +155,7 @@ void gnn_adam(sedacs_ctx* ctx, float lr);
 void gnn_zero_grad(sedacs_ctx* ctx);
 void gnn_set_params_f64(sedacs_ctx* ctx, const double* d_p);
 void gnn_get_params_f64(sedacs_ctx* ctx, double* d_p, bool grad);
-double gnn_train_step(sedacs_ctx* ctx, const double* X, const double* V, int n, float lr);
+double gnn_train_step(sedacs_ctx* ctx, const double* X, const double* V, int n, float lr, bool want_loss);
 
 void dev_dot_into(sedacs_ctx* ctx, const double* a, const double* b, double* out) {
   dot_kernel<<<1, 1024, 0, ctx->stream>>>(a, b, ctx->N, out);
@@ -1072,6 +1072,19 @@ sedacs_status kernel_core(sedacs_ctx* ctx, const double* f, double* u, int* rank
   for (int a = 0; a < m; ++a) axpy2_kernel<<<nblk(N, 128), 128, 0, s>>>(u, V_(a), coef[a], N);
   ctx->launches += m;
   *rank_out = m;
+  GnnState& G = ctx->gnn;
+  if (G.collect && G.pair_cap > 0) {
+    // training pair of the learned preconditioner on the residual itself: x = f, target K_m f,
+    // both scaled by 1/|f| (the map is linear) so that these pairs weigh like the unit Krylov ones
+    const double nf = std::sqrt(dev_dot(ctx, f, f));
+    if (nf > 0.0) {
+      const int slot = G.pair_head;
+      scale_kernel<<<nblk(N, 128), 128, 0, s>>>(G.pX + (size_t)slot * N, f, 1.0 / nf, N);
+      scale_kernel<<<nblk(N, 128), 128, 0, s>>>(G.pV + (size_t)slot * N, u, 1.0 / nf, N);
+      G.pair_head = (G.pair_head + 1) % G.pair_cap;
+      G.pairs = std::min(G.pairs + 1, G.pair_cap);
+    }
+  }
   return SEDACS_OK;
 }
 
@@ -1722,9 +1735,10 @@ sedacs_status sedacs_gnn_train(sedacs_ctx* ctx, const double* X, const double* V
   CUCHK(gnn_prepare(ctx));
   double l0 = 0.0, l1 = 0.0;
   for (int e = 0; e < epochs; ++e) {
-    const double l = gnn_train_step(ctx, dX, dV, n, (float)lr);
+    const bool ends = e == 0 || e == epochs - 1;
+    const double l = gnn_train_step(ctx, dX, dV, n, (float)lr, ends);
     if (e == 0) l0 = l;
-    l1 = l;
+    if (ends) l1 = l;
   }
   CUCHK(cudaStreamSynchronize(ctx->stream));
   if (own) cudaFree(own);

@@ -327,8 +327,9 @@ void gnn_get_params_f64(sedacs_ctx* ctx, double* d_p, bool grad) {
   f2d_kernel<<<nb(kParams, 256), 256, 0, ctx->stream>>>(grad ? ctx->gnn.grad : ctx->gnn.P, d_p, kParams);
 }
 
-// one Adam step on the mean squared error over n pairs (x_k, v_k), each an N-vector in device memory
-double gnn_train_step(sedacs_ctx* ctx, const double* X, const double* V, int n, float lr) {
+// one Adam step on the mean squared error over n pairs (x_k, v_k), each an N-vector in device
+// memory; the loss is read back (one sync per pair) only when want_loss
+double gnn_train_step(sedacs_ctx* ctx, const double* X, const double* V, int n, float lr, bool want_loss) {
   const int N = ctx->N;
   cudaStream_t s = ctx->stream;
   GnnState& G = ctx->gnn;
@@ -342,6 +343,7 @@ double gnn_train_step(sedacs_ctx* ctx, const double* X, const double* V, int n, 
     gnn_forward(ctx, x, G.u);
     residual_kernel<<<nb(N, 256), 256, 0, s>>>(G.u, v, N, 2.0 / n, G.gu, nullptr);
     gnn_backward(ctx, x, G.gu);
+    if (!want_loss) continue;
     // loss: sum (u - v)^2 / n  = sum gu^2 * n / 4
     dev_dot_into(ctx, G.gu, G.gu, lbuf);
     double l = 0.0;
