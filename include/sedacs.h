@@ -80,7 +80,9 @@ typedef struct {
   double scc_alpha;     /* linear mixing coefficient */
   double sp2_tol;       /* SP2 stop: Tr(X - X^2) < sp2_tol * n_orbitals */
   int32_t sp2_kmax;     /* maximum SP2 steps */
-  int32_t ns_iters;     /* Newton-Schulz steps for S^-1/2 (0: 3 in the mixed forms, 4 in FP64) */
+  int32_t ns_iters;     /* Newton-Schulz steps for S^-1/2; 0: automatic (mixed forms: degree-6 Taylor
+                           polynomial of (I + E)^-1/2 in three products when |s - I| <= 0.13 in
+                           every subgraph, else 3 steps; FP64: 4 steps) */
   double ewald_tol;     /* relative accuracy of the Ewald sums (0: 1e-12 FP64, 1e-8 mixed) */
   int32_t judge_every;  /* kernel 2: every judge_every MD steps compare with the Krylov kernel */
   double judge_tol;     /* kernel 2: relative error above which the Krylov kernel takes over */

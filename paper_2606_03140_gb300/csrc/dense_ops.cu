@@ -101,6 +101,64 @@ __global__ void affine_planes_kernel(const SubView* in_v, AffineOut o1, AffineOu
   }
 }
 
+// Two cubic combinations of E, E^2, E^3 (masters): y_k = a_k E + b_k E^2 + c_k E^3 on the valid
+// block, zero elsewhere, each written as master and / or planes.  One warp per row, 8 columns
+// per lane.
+struct PolyOut {
+  const SubView* views;
+  double a, b, c;
+  int master;
+  int nsplit;
+};
+
+template <typename T>
+__global__ void poly3_kernel(const SubView* e1, const SubView* e2, const SubView* e3, PolyOut o1, PolyOut o2,
+                             uint8_t* arena) {
+  const SubView v1 = e1[blockIdx.y], v2 = e2[blockIdx.y], v3 = e3[blockIdx.y];
+  const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= v1.rows_pad) return;
+  const T* p1 = reinterpret_cast<const T*>(arena + v1.master) + (long long)row * v1.n_pad;
+  const T* p2 = reinterpret_cast<const T*>(arena + v2.master) + (long long)row * v2.n_pad;
+  const T* p3 = reinterpret_cast<const T*>(arena + v3.master) + (long long)row * v3.n_pad;
+  for (int c8 = lane * 8; c8 < v1.n_pad; c8 += 256) {
+    T x1[8], x2[8], x3[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      x1[e] = p1[c8 + e];
+      x2[e] = p2[c8 + e];
+      x3[e] = p3[c8 + e];
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const PolyOut& o = k == 0 ? o1 : o2;
+      const SubView vo = o.views[blockIdx.y];
+      T y[8];
+      float yf[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const bool ok = row < v1.n_real && (c8 + e) < v1.n_real;
+        y[e] = ok ? (T)o.a * x1[e] + (T)o.b * x2[e] + (T)o.c * x3[e] : (T)0;
+        yf[e] = (float)y[e];
+      }
+      if (o.master) {
+        T* dst = reinterpret_cast<T*>(arena + vo.master) + (long long)row * vo.n_pad + c8;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) dst[e] = y[e];
+      }
+      if (o.nsplit > 0) {
+        __align__(16) __nv_bfloat16 h[8], m[8], l[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) split3(yf[e], h[e], m[e], l[e]);
+        const long long off = vo.planes + blocked_offset(row, c8, vo.n_pad);
+        *reinterpret_cast<uint4*>(arena + off) = *reinterpret_cast<const uint4*>(h);
+        if (o.nsplit > 1) *reinterpret_cast<uint4*>(arena + off + vo.plane_stride) = *reinterpret_cast<const uint4*>(m);
+        if (o.nsplit > 2) *reinterpret_cast<uint4*>(arena + off + 2 * vo.plane_stride) = *reinterpret_cast<const uint4*>(l);
+      }
+    }
+  }
+}
+
 // Gershgorin: per row (one warp), d - r and d + r of the valid block.
 template <typename T>
 __global__ void gersh_rows_kernel(const SubView* views, const uint8_t* arena, double* lo, double* hi,
@@ -243,6 +301,17 @@ void launch_affine_planes(const SubView* in, const SubView* out1, double a1, dou
   const AffineOut o2{out2, a2, b2, master2, f64 ? 0 : nsplit2};
   if (f64) affine_planes_kernel<double><<<g, 256, 0, s>>>(in, o1, o2, kind, bounds, arena);
   else affine_planes_kernel<float><<<g, 256, 0, s>>>(in, o1, o2, kind, bounds, arena);
+}
+
+void launch_poly3(const SubView* e1, const SubView* e2, const SubView* e3, const SubView* out1, double a1, double b1,
+                  double c1, int master1, int nsplit1, const SubView* out2, double a2, double b2, double c2,
+                  int master2, int nsplit2, int n_sub, int max_rows, uint8_t* arena, bool f64, cudaStream_t s) {
+  if (n_sub <= 0 || max_rows <= 0) return;
+  dim3 g((max_rows + 7) / 8, n_sub);
+  const PolyOut o1{out1, a1, b1, c1, master1, f64 ? 0 : nsplit1};
+  const PolyOut o2{out2, a2, b2, c2, master2, f64 ? 0 : nsplit2};
+  if (f64) poly3_kernel<double><<<g, 256, 0, s>>>(e1, e2, e3, o1, o2, arena);
+  else poly3_kernel<float><<<g, 256, 0, s>>>(e1, e2, e3, o1, o2, arena);
 }
 
 void launch_gershgorin(const SubView* views, int n_sub, int max_rows, const uint8_t* arena, double* lo, double* hi,

@@ -22,6 +22,10 @@ void launch_split_planes(const SubView* views, int n_sub, int max_rows, uint8_t*
 void launch_affine_planes(const SubView* in, const SubView* out1, double a1, double b1, int master1, int nsplit1,
                           const SubView* out2, double a2, double b2, int master2, int nsplit2, int kind,
                           const double* bounds, int n_sub, int max_rows, uint8_t* arena, bool f64, cudaStream_t s);
+// out1 = a1 E + b1 E^2 + c1 E^3 and out2 likewise (E, E^2, E^3 from masters), valid block only.
+void launch_poly3(const SubView* e1, const SubView* e2, const SubView* e3, const SubView* out1, double a1, double b1,
+                  double c1, int master1, int nsplit1, const SubView* out2, double a2, double b2, double c2,
+                  int master2, int nsplit2, int n_sub, int max_rows, uint8_t* arena, bool f64, cudaStream_t s);
 void launch_gershgorin(const SubView* views, int n_sub, int max_rows, const uint8_t* arena, double* lo, double* hi,
                        const long long* row_base, double* bounds, bool f64, cudaStream_t s);
 void launch_sp2_replay_init(Sp2State* st, const double* bounds, const int* n_real, const int* steps, double mu, int n,

@@ -48,6 +48,8 @@ enum OpId : int {
   OP_T1_0, OP_T1_1, OP_DC0, OP_DC1, OP_T2, OP_WC0, OP_WC1,
   // response (first-order SP2), see response.cu
   OP_RSP_A, OP_RSP_B, OP_DP0, OP_DP1, OP_DHT0, OP_DHT1, OP_DT1_0, OP_DT1_1, OP_DDC0, OP_DDC1,
+  // Z = s^-1/2 by the degree-6 Taylor polynomial of (I + E)^-1/2 (Paterson-Stockmeyer)
+  OP_TE2, OP_TE3, OP_TZ,
   OP_NUM
 };
 
