@@ -874,14 +874,17 @@ sedacs_status density_core(sedacs_ctx* ctx, double* mu_io, bool allow_resolve = 
   phase_end(ctx, 0, 4);
   phase_begin(ctx, 0);
   back_transform(ctx, true);
-  STCHK(observe(ctx, false, &nel));
+  // when forces follow (XL-BOMD), the same pass also contracts the force blocks
+  const bool fused = ctx->fuse_forces;
+  STCHK(observe(ctx, fused, &nel));
   if (allow_resolve && std::fabs(nel - ctx->n_electrons) > count_window(ctx->n_electrons)) {
     // mu left the gap (the levels moved): place it again
     STCHK(solve_mu(ctx, &mu));
     STCHK(run_sp2(ctx, mu, ctx->prm.sp2_kmax));
     back_transform(ctx, true);
-    STCHK(observe(ctx, false, &nel));
+    STCHK(observe(ctx, fused, &nel));
   }
+  ctx->du_ready = fused;
   launch_gd(ctx->model, ctx->d_sub_ptr, ctx->d_sub_atoms, ctx->d_orb_off, ctx->d_species, ctx->part.perm,
             ctx->d_core_sub, ctx->d_core_local, ctx->n_core_total, ctx->arena, ctx->f64, ctx->d_dcoff, ctx->d_n_pad,
             ctx->d_gd_ptr, ctx->d_gd_col, ctx->d_gd_val, s);
@@ -914,7 +917,8 @@ sedacs_status forces_core(sedacs_ctx* ctx) {
   if (!ctx->have_density) { ctx->err = "no density: call sedacs_subgraph_density first"; return SEDACS_EINVAL; }
   cudaStream_t s = ctx->stream;
   phase_begin(ctx, 0);
-  STCHK(observe(ctx, true, nullptr));
+  if (!ctx->du_ready) STCHK(observe(ctx, true, nullptr));   // else done with the density
+  ctx->du_ready = false;
   coul_a_kernel<<<nblk(ctx->N, 128), 128, 0, s>>>(ctx->d_q, ctx->d_n, ctx->d_tmp, ctx->N);
   CUCHK(ctx->ew.gradient(ctx->d_tmp, ctx->d_n, ctx->d_F, s, ctx->ew_tag));
   add_kernel<<<nblk(3 * ctx->N, 256), 256, 0, s>>>(ctx->d_dU, ctx->d_F, 3 * ctx->N);
@@ -1555,7 +1559,10 @@ sedacs_status sedacs_xlbomd_init(sedacs_ctx* ctx, const double* R, const double*
   fill_hist_kernel<<<nblk(ctx->N, 128), 128, 0, ctx->stream>>>(ctx->d_hist, ctx->d_n, ctx->N);
   ctx->hist_head = 0;
   double m = mu;
-  STCHK(cycle(ctx, &m));
+  ctx->fuse_forces = true;
+  const sedacs_status st = cycle(ctx, &m);
+  ctx->fuse_forces = false;
+  STCHK(st);
   STCHK(forces_core(ctx));
   ctx->md_ready = true;
   return SEDACS_OK;
@@ -1604,7 +1611,10 @@ sedacs_status sedacs_xlbomd_step(sedacs_ctx* ctx, double* R, double* V, int32_t 
     ctx->geom_valid = false;
     phase_end(ctx, 0, 7);
     double m = ctx->mu;
-    STCHK(cycle(ctx, &m));
+    ctx->fuse_forces = true;
+    const sedacs_status st = cycle(ctx, &m);
+    ctx->fuse_forces = false;
+    STCHK(st);
     STCHK(forces_core(ctx));
     kick_kernel<<<nblk(3 * N, 256), 256, 0, s>>>(ctx->d_vel, ctx->d_F, ctx->d_mass, 0.5 * dt_fs * kAccHaAAmu, N);
     kin_kernel<<<1, 1024, 0, s>>>(ctx->d_vel, ctx->d_mass, N, ctx->d_scal + 5);

@@ -185,6 +185,8 @@ struct sedacs_ctx {
   // SP2 step control: per-step active counts copied into pinned host memory, one event per
   // step, so that the host waits on a step a few launches back instead of draining the stream
   bool have_xgd = false;  // a density graph was given to sedacs_graph_build (d_xgd_*)
+  bool fuse_forces = false;  // the next density's observables pass also contracts the forces
+  bool du_ready = false;     // d_dU holds the band-structure force terms of the last density
   int ew_tag = 0;         // tag of the Coulomb potential of d_n at the current geometry
   int* h_nactive = nullptr;
   int h_nactive_cap = 0;
