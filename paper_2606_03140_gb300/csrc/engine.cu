@@ -308,6 +308,61 @@ long long pptr_(const sedacs_ctx* ctx, int sl, int i, int copy = 0) {
 }
 
 // C = alpha A B^T + beta I + g1 C1 + g2 C2 over every subgraph (slots a, b, out, c1, c2; -1: none).
+// Staged uploads: the bytes are appended to ctx->stage_host (16-byte aligned) and sent by
+// flush_staged, which copies them once into pinned memory and enqueues one asynchronous copy
+// per destination (no pageable copies, no stream synchronisation per array).
+void stage_bytes(sedacs_ctx* ctx, void* dst, const void* src, size_t bytes) {
+  if (bytes == 0) return;
+  const size_t off = (ctx->stage_host.size() + 15) & ~size_t(15);
+  ctx->stage_host.resize(off + bytes);
+  std::memcpy(ctx->stage_host.data() + off, src, bytes);
+  ctx->stage_recs.emplace_back(dst, off, bytes);
+}
+
+template <typename T>
+sedacs_status stage_vec(sedacs_ctx* ctx, T** dst, const std::vector<T>& v) {
+  CUCHK(ensure(ctx, reinterpret_cast<void**>(dst), sizeof(T) * std::max<size_t>(1, v.size())));
+  stage_bytes(ctx, *dst, v.data(), sizeof(T) * v.size());
+  return SEDACS_OK;
+}
+
+sedacs_status stage_views(sedacs_ctx* ctx, int sl, int copy, SubView** dst) {
+  const Layout& L = ctx->lay;
+  std::vector<SubView> v(L.n_sub);
+  for (int i = 0; i < L.n_sub; ++i) {
+    SubView s;
+    s.master = mptr(ctx, sl, i, copy);
+    s.planes = pptr_(ctx, sl, i, copy);
+    s.plane_stride = ctx->slot[sl].plane_stride;
+    s.n_pad = L.n_pad[i];
+    s.rows_pad = ctx->slot[sl].rows ? L.m_pad[i] : L.n_pad[i];
+    s.n_real = L.n_real[i];
+    s.pad = 0;
+    v[i] = s;
+  }
+  return stage_vec(ctx, dst, v);
+}
+
+// The caller synchronises the stream before the next staging round reuses the pinned buffer.
+sedacs_status flush_staged(sedacs_ctx* ctx) {
+  const size_t n = ctx->stage_host.size();
+  if (n > ctx->stage_pinned_cap) {
+    if (ctx->stage_pinned) cudaFreeHost(ctx->stage_pinned);
+    ctx->stage_pinned = nullptr;
+    ctx->stage_pinned_cap = 0;
+    const size_t want = n + n / 2 + 4096;
+    CUCHK(cudaHostAlloc(reinterpret_cast<void**>(&ctx->stage_pinned), want, cudaHostAllocDefault));
+    ctx->stage_pinned_cap = want;
+  }
+  if (n) std::memcpy(ctx->stage_pinned, ctx->stage_host.data(), n);
+  for (const auto& r : ctx->stage_recs)
+    CUCHK(cudaMemcpyAsync(std::get<0>(r), ctx->stage_pinned + std::get<1>(r), std::get<2>(r), cudaMemcpyHostToDevice,
+                          ctx->stream));
+  ctx->stage_host.clear();
+  ctx->stage_recs.clear();
+  return SEDACS_OK;
+}
+
 sedacs_status build_op(sedacs_ctx* ctx, int id, int a, int b, int out, int mode, float alpha, float beta,
                        bool b_from_sp2, bool a_from_sp2 = false, int c1 = -1, float g1 = 0.f, int c2 = -1,
                        float g2 = 0.f, bool c_from_sp2 = false, bool sym = false) {
@@ -359,10 +414,8 @@ sedacs_status build_op(sedacs_ctx* ctx, int id, int a, int b, int out, int mode,
   GemmOp& op = ctx->ops[id];
   CUCHK(ensure(ctx, reinterpret_cast<void**>(&op.mats_d), sizeof(GemmMat) * std::max(1, L.n_sub)));
   CUCHK(ensure(ctx, reinterpret_cast<void**>(&op.work_d), sizeof(GemmWork) * std::max<size_t>(1, work.size())));
-  CUCHK(cudaMemcpyAsync(op.mats_d, mats.data(), sizeof(GemmMat) * L.n_sub, cudaMemcpyHostToDevice, ctx->stream));
-  if (!work.empty())
-    CUCHK(cudaMemcpyAsync(op.work_d, work.data(), sizeof(GemmWork) * work.size(), cudaMemcpyHostToDevice,
-                          ctx->stream));
+  stage_bytes(ctx, op.mats_d, mats.data(), sizeof(GemmMat) * L.n_sub);
+  stage_bytes(ctx, op.work_d, work.data(), sizeof(GemmWork) * work.size());
   op.n_work = (int)work.size();
   op.alpha = alpha;
   op.beta = beta;
@@ -392,26 +445,6 @@ void run_op(sedacs_ctx* ctx, int id, int nsplit_in, int nsplit_out) {
   ctx->launches += op.n_work > 0 ? 1 : 0;
 }
 
-sedacs_status upload_views(sedacs_ctx* ctx, int sl, int copy, SubView** dst) {
-  const Layout& L = ctx->lay;
-  std::vector<SubView> v(L.n_sub);
-  for (int i = 0; i < L.n_sub; ++i) {
-    SubView s;
-    s.master = mptr(ctx, sl, i, copy);
-    s.planes = pptr_(ctx, sl, i, copy);
-    s.plane_stride = ctx->slot[sl].plane_stride;
-    s.n_pad = L.n_pad[i];
-    s.rows_pad = ctx->slot[sl].rows ? L.m_pad[i] : L.n_pad[i];
-    s.n_real = L.n_real[i];
-    s.pad = 0;
-    v[i] = s;
-  }
-  CUCHK(ensure(ctx, reinterpret_cast<void**>(dst), sizeof(SubView) * std::max(1, L.n_sub)));
-  CUCHK(cudaMemcpyAsync(*dst, v.data(), sizeof(SubView) * L.n_sub, cudaMemcpyHostToDevice, ctx->stream));
-  CUCHK(cudaStreamSynchronize(ctx->stream));   // v is a local
-  return SEDACS_OK;
-}
-
 template <typename T>
 sedacs_status upload_vec(sedacs_ctx* ctx, T** dst, const std::vector<T>& v) {
   CUCHK(ensure(ctx, reinterpret_cast<void**>(dst), sizeof(T) * std::max<size_t>(1, v.size())));
@@ -438,6 +471,7 @@ sedacs_status rebuild_layout(sedacs_ctx* ctx) {
   CUCHK(ensure(ctx, reinterpret_cast<void**>(&ctx->d_n_core_orb), sizeof(int) * std::max(1, P)));
   launch_orb_offsets(ctx->d_sub_ptr, ctx->d_sub_atoms, ctx->d_species, ctx->model, ctx->d_orb_off, ctx->d_n_orb_sub,
                      ctx->d_n_core, ctx->d_n_core_orb, P, s);
+  CUCHK(cudaGetLastError());
   L.n_real.resize(P);
   L.n_core_orb.resize(P);
   CUCHK(cudaMemcpyAsync(L.n_real.data(), ctx->d_n_orb_sub, sizeof(int) * P, cudaMemcpyDeviceToHost, s));
@@ -491,8 +525,8 @@ sedacs_status rebuild_layout(sedacs_ctx* ctx) {
     ctx->arena_cap = want;
   }
   // views and per-subgraph offset arrays
-  for (int k = 0; k < kNumSlots; ++k) STCHK(upload_views(ctx, k, 0, &ctx->d_views[k]));
-  STCHK(upload_views(ctx, kX, 1, &ctx->d_views_x1));
+  for (int k = 0; k < kNumSlots; ++k) STCHK(stage_views(ctx, k, 0, &ctx->d_views[k]));
+  STCHK(stage_views(ctx, kX, 1, &ctx->d_views_x1));
   std::vector<long long> hoff(P), soff(P), dco(P), wco(P), rbase(P), troff(P), ddco(P), dhoff(P);
   std::vector<int> npad(P), nreal(P), ndiag(P);
   long long rb = 0;
@@ -510,17 +544,17 @@ sedacs_status rebuild_layout(sedacs_ctx* ctx) {
     nreal[i] = L.n_real[i];
     ndiag[i] = L.n_diag[i];
   }
-  STCHK(upload_vec(ctx, &ctx->d_hoff, hoff));
-  STCHK(upload_vec(ctx, &ctx->d_soff, soff));
-  STCHK(upload_vec(ctx, &ctx->d_dcoff, dco));
-  STCHK(upload_vec(ctx, &ctx->d_wcoff, wco));
-  STCHK(upload_vec(ctx, &ctx->d_dcoff_d, ddco));
-  STCHK(upload_vec(ctx, &ctx->d_dhoff, dhoff));
-  STCHK(upload_vec(ctx, &ctx->d_rowbase, rbase));
-  STCHK(upload_vec(ctx, &ctx->d_tr_off, troff));
-  STCHK(upload_vec(ctx, &ctx->d_n_pad, npad));
-  STCHK(upload_vec(ctx, &ctx->d_n_real, nreal));
-  STCHK(upload_vec(ctx, &ctx->d_n_diag, ndiag));
+  STCHK(stage_vec(ctx, &ctx->d_hoff, hoff));
+  STCHK(stage_vec(ctx, &ctx->d_soff, soff));
+  STCHK(stage_vec(ctx, &ctx->d_dcoff, dco));
+  STCHK(stage_vec(ctx, &ctx->d_wcoff, wco));
+  STCHK(stage_vec(ctx, &ctx->d_dcoff_d, ddco));
+  STCHK(stage_vec(ctx, &ctx->d_dhoff, dhoff));
+  STCHK(stage_vec(ctx, &ctx->d_rowbase, rbase));
+  STCHK(stage_vec(ctx, &ctx->d_tr_off, troff));
+  STCHK(stage_vec(ctx, &ctx->d_n_pad, npad));
+  STCHK(stage_vec(ctx, &ctx->d_n_real, nreal));
+  STCHK(stage_vec(ctx, &ctx->d_n_diag, ndiag));
   CUCHK(ensure(ctx, reinterpret_cast<void**>(&ctx->d_glo), sizeof(double) * std::max(1LL, rb)));
   CUCHK(ensure(ctx, reinterpret_cast<void**>(&ctx->d_ghi), sizeof(double) * std::max(1LL, rb)));
   CUCHK(ensure(ctx, reinterpret_cast<void**>(&ctx->d_bounds), sizeof(double) * 2 * std::max(1, P)));
@@ -540,15 +574,16 @@ sedacs_status rebuild_layout(sedacs_ctx* ctx) {
   }
   for (int A = 0; A < N; ++A) gdp[A + 1] = gdp[A] + gdlen[A];
   ctx->n_core_total = (int)csub.size();
-  STCHK(upload_vec(ctx, &ctx->d_sub_of_row, sor));
-  STCHK(upload_vec(ctx, &ctx->d_core_sub, csub));
-  STCHK(upload_vec(ctx, &ctx->d_core_local, cloc));
-  STCHK(upload_vec(ctx, &ctx->d_gd_ptr, gdp));
+  STCHK(stage_vec(ctx, &ctx->d_sub_of_row, sor));
+  STCHK(stage_vec(ctx, &ctx->d_core_sub, csub));
+  STCHK(stage_vec(ctx, &ctx->d_core_local, cloc));
+  STCHK(stage_vec(ctx, &ctx->d_gd_ptr, gdp));
   ctx->gd_nnz = gdp[N];
   CUCHK(grow(&ctx->d_gd_col, &ctx->gd_cap, ctx->gd_nnz + 1) == cudaSuccess ? cudaSuccess : cudaErrorMemoryAllocation);
   CUCHK(ensure(ctx, reinterpret_cast<void**>(&ctx->d_gd_val), sizeof(double) * ctx->gd_cap));
   CUCHK(ensure(ctx, reinterpret_cast<void**>(&ctx->d_loc), sizeof(int) * (size_t)N * std::max(1, P)));
   launch_loc_fill(ctx->d_sub_ptr, ctx->d_sub_atoms, ctx->d_loc, N, P, s);
+  CUCHK(cudaGetLastError());
   // GEMM tables
   // S^-1/2 in deviation form: Y = I + E_y (kY*), Z = I + E_z (kZ*), T = I + E_t (kT);
   // only products of the small deviations go through the tensor cores.
@@ -587,6 +622,9 @@ sedacs_status rebuild_layout(sedacs_ctx* ctx) {
   STCHK(build_op(ctx, OP_DT1_1, kZ1, kR2, kdT1, kModeGeneric, 1.f, 0.f, true, false, kR2, 1.f, -1, 0.f, true));
   STCHK(build_op(ctx, OP_DDC0, kdT1, kZ0, kdDc, kModeGeneric, 2.f, 0.f, false, false, kdT1, 2.f));
   STCHK(build_op(ctx, OP_DDC1, kdT1, kZ1, kdDc, kModeGeneric, 2.f, 0.f, false, false, kdT1, 2.f));
+  CUCHK(cudaGetLastError());
+  STCHK(flush_staged(ctx));
+  CUCHK(cudaGetLastError());
   ctx->have_subs = true;
   ctx->z_valid = false;
   ctx->sp2_iters_h.assign(P, 0);
@@ -720,7 +758,7 @@ sedacs_status run_sp2(sedacs_ctx* ctx, double mu, int kmax) {
   launch_sp2_init(ctx->d_sp2, ctx->d_bounds, ctx->d_n_real, mu, ctx->prm.sp2_tol, kmax, L.n_sub, s);
   ctx->launches += 2;
   if (ctx->h_nactive_cap < kmax) {
-    if (ctx->h_nactive) cudaFreeHost(ctx->h_nactive);
+    if (ctx->h_nactive) CUCHK(cudaFreeHost(ctx->h_nactive));
     ctx->h_nactive = nullptr;
     ctx->h_nactive_cap = 0;
     CUCHK(cudaHostAlloc(reinterpret_cast<void**>(&ctx->h_nactive), sizeof(int) * kmax, cudaHostAllocDefault));
@@ -739,7 +777,7 @@ sedacs_status run_sp2(sedacs_ctx* ctx, double mu, int kmax) {
   // subgraph stopped find no active tile and return at once.
   constexpr int kLookahead = 3;
   const int ev0 = ctx->kev_used;
-  cudaMemsetAsync(ctx->d_nactive, 0, sizeof(int) * kmax, s);
+  CUCHK(cudaMemsetAsync(ctx->d_nactive, 0, sizeof(int) * kmax, s));
   for (int k = 0; k < kmax; ++k) {
     if (k >= kLookahead) {
       CUCHK(cudaEventSynchronize(ctx->sp2_ev[k - kLookahead]));
@@ -937,6 +975,7 @@ sedacs_status forces_core(sedacs_ctx* ctx) {
 sedacs_status graph_core(sedacs_ctx* ctx, const long long* gptr, const int* gcol, const double* gval,
                          bool keep_prev = false) {
   cudaStream_t s = ctx->stream;
+  CUCHK(cudaGetLastError());   // (an error of earlier work is reported here, not by the build)
   CUCHK(grow(&ctx->d_row_ptr, &ctx->rows_cap, (long long)ctx->N + 1) == cudaSuccess ? cudaSuccess
                                                                                    : cudaErrorMemoryAllocation);
   long long nnz = 0;
@@ -1268,6 +1307,7 @@ void sedacs_destroy(sedacs_ctx* ctx) {
   for (auto& e : ctx->sp2_ev)
     if (e) cudaEventDestroy(e);
   if (ctx->h_nactive) cudaFreeHost(ctx->h_nactive);
+  if (ctx->stage_pinned) cudaFreeHost(ctx->stage_pinned);
   GnnState& G = ctx->gnn;
   for (void* p : {(void*)G.P, (void*)G.grad, (void*)G.m, (void*)G.v, (void*)G.act, (void*)G.part, (void*)G.ebas,
                   (void*)G.gu, (void*)G.u, (void*)G.pX, (void*)G.pV})

@@ -2,6 +2,7 @@
 // batched GEMM tables and the stream; runs the pipeline of the graph-partitioned solve.
 #pragma once
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/sedacs.h"
@@ -185,6 +186,12 @@ struct sedacs_ctx {
   // SP2 step control: per-step active counts copied into pinned host memory, one event per
   // step, so that the host waits on a step a few launches back instead of draining the stream
   bool have_xgd = false;  // a density graph was given to sedacs_graph_build (d_xgd_*)
+  // Layout uploads staged in one host buffer and sent from pinned memory in one go
+  // (rebuild_layout): (device destination, offset in stage_host, bytes)
+  std::vector<uint8_t> stage_host;
+  std::vector<std::tuple<void*, size_t, size_t>> stage_recs;
+  uint8_t* stage_pinned = nullptr;
+  size_t stage_pinned_cap = 0;
   bool fuse_forces = false;  // the next density's observables pass also contracts the forces
   bool du_ready = false;     // d_dU holds the band-structure force terms of the last density
   int ew_tag = 0;         // tag of the Coulomb potential of d_n at the current geometry
