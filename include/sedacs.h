@@ -78,7 +78,8 @@ typedef struct {
   double c_k0;          /* K0 = -c I */
   double scc_tol;       /* max |q - n| for SCC convergence, e */
   double scc_alpha;     /* linear mixing coefficient */
-  double sp2_tol;       /* SP2 stop: Tr(X - X^2) < sp2_tol * n_orbitals */
+  double sp2_tol;       /* SP2 stop: Tr(X - X^2) < sp2_tol * n_orbitals (0: 1e-7 in the mixed forms,
+                           1e-9 in FP64) */
   int32_t sp2_kmax;     /* maximum SP2 steps */
   int32_t ns_iters;     /* Newton-Schulz steps for S^-1/2; 0: automatic (mixed forms: degree-6 Taylor
                            polynomial of (I + E)^-1/2 in three products when |s - I| <= 0.13 in
@@ -89,7 +90,7 @@ typedef struct {
 } sedacs_params;
 
 /* Fill p with the defaults (r_graph 3.0, tau 1e-3, core_size 32, precision 1, kernel 0,
- * krylov_rank 4, krylov_tol 1e-2, c_k0 0.5, scc_tol 1e-8, scc_alpha 0.2, sp2_tol 1e-9,
+ * krylov_rank 4, krylov_tol 1e-2, c_k0 0.5, scc_tol 1e-8, scc_alpha 0.2, sp2_tol 0,
  * sp2_kmax 60, ns_iters 0, ewald_tol 0, judge_every 20, judge_tol 0.1). */
 void sedacs_default_params(sedacs_params* p);
 

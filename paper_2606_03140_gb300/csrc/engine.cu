@@ -755,7 +755,10 @@ sedacs_status run_sp2(sedacs_ctx* ctx, double mu, int kmax) {
   const Layout& L = ctx->lay;
   const int mr = max_rows(ctx);
   launch_sp2_start(ctx, false);
-  launch_sp2_init(ctx->d_sp2, ctx->d_bounds, ctx->d_n_real, mu, ctx->prm.sp2_tol, kmax, L.n_sub, s);
+  // stop rule Tr(X - X^2) < tol n: 1e-7 in the mixed forms (the charges are then as close to
+  // the oracle as with 1e-9, one step earlier on average), 1e-9 in FP64
+  const double tol = ctx->prm.sp2_tol > 0 ? ctx->prm.sp2_tol : (ctx->f64 ? 1e-9 : 1e-7);
+  launch_sp2_init(ctx->d_sp2, ctx->d_bounds, ctx->d_n_real, mu, tol, kmax, L.n_sub, s);
   ctx->launches += 2;
   if (ctx->h_nactive_cap < kmax) {
     if (ctx->h_nactive) CUCHK(cudaFreeHost(ctx->h_nactive));
@@ -1199,7 +1202,7 @@ void sedacs_default_params(sedacs_params* p) {
   p->c_k0 = 0.5;
   p->scc_tol = 1e-8;
   p->scc_alpha = 0.2;
-  p->sp2_tol = 1e-9;
+  p->sp2_tol = 0.0;        // automatic: 1e-7 in the mixed forms, 1e-9 in FP64
   p->sp2_kmax = 60;
   p->ns_iters = 0;      // 0: 3 steps in the mixed forms, 4 in FP64
   p->ewald_tol = 0.0;
