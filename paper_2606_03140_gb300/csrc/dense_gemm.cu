@@ -81,8 +81,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_persistent(const GemmPa
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + Cfg::kStages * Cfg::kStageBytes + PCfg::kTransBytes);
   uint64_t* empty = full + Cfg::kStages;
   uint64_t* accf = empty + Cfg::kStages;
+  // acce[j]: the epilogue has drained hi*hi accumulator j (j = 0 together with the corrections
+  // accumulator): the next tile's first k-block writes accumulator 0 and the corrections, the
+  // second accumulator 1, the third accumulator 2, so TMEM is handed back in three parts
   uint64_t* acce = accf + 1;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 1);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 3);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool stepping = (p.mode == kModeSp2 || p.mode == kModeRsp);
   constexpr uint32_t kTmemCols = NSPLIT > 1 ? 512 : 128;
@@ -93,7 +96,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_persistent(const GemmPa
       mbar_init(&empty[s], 1);
     }
     mbar_init(accf, 1);
-    mbar_init(acce, kEpiWarps);
+    for (int j = 0; j < 3; ++j) mbar_init(&acce[j], kEpiWarps);
     fence_mbar_init();
   }
   if (warp == 0) {
@@ -154,11 +157,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_persistent(const GemmPa
         if (!tile_live(w)) continue;
         const GemmMat m = p.mats[w.mat];
         const int kb_end = (m.k_real + 63) >> 6;
-        if (ti > 0 && !mbar_wait(acce, (uint32_t)((ti - 1) & 1))) { ok = false; break; }
+        const uint32_t prev = (uint32_t)((ti - 1) & 1);
+        // accumulator parts of the previous tile that the next k-block overwrites (all three at
+        // once with a single accumulator)
+        auto wait_part = [&](int j) -> bool { return ti == 0 || mbar_wait(&acce[j], prev); };
+        if (!wait_part(0) || (NSPLIT == 1 && (!wait_part(1) || !wait_part(2)))) { ok = false; break; }
         tc_fence_after();
         for (int kb = 0; kb < kb_end; ++kb, ++g) {
           const int s = (int)(g % Cfg::kStages);
           const long long round = g / Cfg::kStages;
+          if (NSPLIT > 1 && (kb == 1 || kb == 2)) {
+            if (!wait_part(kb)) { ok = false; break; }
+            tc_fence_after();
+          }
           if (!mbar_wait(&full[s], (uint32_t)(round & 1))) { ok = false; break; }
           tc_fence_after();
           const uint32_t st = smem_u32(smem + s * Cfg::kStageBytes);
@@ -181,6 +192,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_persistent(const GemmPa
           }
           tc_commit(&empty[s]);
         }
+        // parts this tile did not write are still consumed, so every barrier advances per tile
+        if (NSPLIT > 1 && ok) {
+          if (kb_end < 2 && !wait_part(1)) ok = false;
+          if (ok && kb_end < 3 && !wait_part(2)) ok = false;
+        }
+        if (!ok) break;
         tc_commit(accf);
         ++ti;
       }
@@ -278,33 +295,41 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_persistent(const GemmPa
       }
       if (!mbar_wait(accf, (uint32_t)(ti & 1))) { ok = false; break; }
       tc_fence_after();
-      // drain this warp's 64 columns of every accumulator into registers, then hand TMEM back
+      // drain this warp's 64 columns of the accumulators into registers, handing each part of
+      // TMEM back as soon as it is read: accumulator 0 with the corrections, then 1, then 2
       float v[2][32];
       const uint32_t t_row = tmem + ((uint32_t)(qd * 32) << 16);
+      auto release = [&](int j) {
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0)
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce[j])) : "memory");
+      };
 #pragma unroll
       for (int cc = 0; cc < 2; ++cc) {
         const uint32_t col = (uint32_t)(hf * 64 + cc * 32);
         tmem_ld32(t_row + col, v[cc]);
         if (NSPLIT > 1) {
           float v2[32];
-          if (kb_end > 1) {
-            tmem_ld32(t_row + 128 + col, v2);
-#pragma unroll
-            for (int j = 0; j < 32; ++j) v[cc][j] += v2[j];
-          }
-          if (kb_end > 2) {
-            tmem_ld32(t_row + 256 + col, v2);
-#pragma unroll
-            for (int j = 0; j < 32; ++j) v[cc][j] += v2[j];
-          }
           tmem_ld32(t_row + 384 + col, v2);
 #pragma unroll
           for (int j = 0; j < 32; ++j) v[cc][j] += v2[j];
         }
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(acce)) : "memory");
+      release(0);
+#pragma unroll
+      for (int part = 1; part < 3; ++part) {
+        if (NSPLIT > 1 && kb_end > part) {
+#pragma unroll
+          for (int cc = 0; cc < 2; ++cc) {
+            float v2[32];
+            tmem_ld32(t_row + 128 * part + (uint32_t)(hf * 64 + cc * 32), v2);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[cc][j] += v2[j];
+          }
+        }
+        release(part);
+      }
       ++ti;
 
       float* outm = (m.out_off >= 0) ? reinterpret_cast<float*>(p.arena + m.out_off + out_shift) : nullptr;
