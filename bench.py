@@ -229,30 +229,35 @@ def run_ours(args, world, rank, local):
     value = world * N * args.steps / (ms / 1e3)
     e2e = world * N * args.steps / t_e2e
     # roofline of the dominant kernel (SP2 squares on tcgen05): algorithmic FLOPs = 2 n^3 per
-    # symmetric square (n^3 multiply-add pairs), FP32-class product = 6 bf16 tensor-core products
+    # symmetric square (n^3 multiply-add pairs); one FP32-class product = 3 fp16 tensor-core products
+    # (two-plane fp16 form 1) or 6 bf16 products (three-plane form 4); fp16 and bf16 run at one rate
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
     bf16 = peaks.get("bf16_tflops_sustained", 1700.0)
-    nsplit_products = {1: 6, 2: 3, 3: 1}.get(args.precision, 6)
+    nsplit_products = {1: 3, 2: 3, 3: 1, 4: 6}.get(args.precision, 6)
     achieved = (2.0 * k_pairs / max(k_launch, 1)) / (k_ms / max(k_launch, 1) / 1e3) / 1e12 if k_ms > 0 else None
     peak = bf16 / nsplit_products
-    roof = {"kernel": "tc_gemm_persistent (SP2 square, split-bf16 tcgen05)", "bound": "tensor",
+    roof = {"kernel": ("tc_gemm_persistent (SP2 square, " + ("two-plane fp16" if args.precision == 1 else
+                                                             "split-bf16") + " tcgen05)"), "bound": "tensor",
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": (achieved / peak) if achieved else None,
             "traffic": (SP2_TRAFFIC["bytes_per_launch"]
                         if (kernel_sha1() == SP2_TRAFFIC["kernel_sha1"] and args.workload == SP2_TRAFFIC["workload"]
                             and args.precision == SP2_TRAFFIC["precision"]) else None),
             "traffic_unit": "bytes per launch (DRAM read + write, ncu, average over the SP2 launches)",
-            "peak_note": f"measured sustained bf16 {bf16} TF/s / {nsplit_products} split products (of measured)",
+            "peak_note": f"measured sustained bf16 {bf16} TF/s (= fp16 rate) / {nsplit_products} split products "
+                         "(of measured)",
             "launches": k_launch, "kernel_ms": k_ms}
     drift = float(E[-1, 2] - E[0, 2])
     return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {1: "f32 (3-way split bf16 on tcgen05) / f64 sums", 2: "bf16x2 split / f64 sums",
+        "vs_baseline": None, "dtype": {1: "f32-class (SP2: 2-plane fp16 on tcgen05; other products 3-way bf16) / "
+                                          "f64 sums",
+                                       4: "f32 (3-way split bf16 on tcgen05) / f64 sums", 2: "bf16x2 split / f64 sums",
                                        3: "bf16 / f64 sums", 0: "f64"}[args.precision],
         "data": "synthetic (seeded water box, synthetic sp SCC-TB model)",
         "config": {"workload": f"{args.workload}: {N} atoms, cores~32, tau 1e-3, r_graph 3 A, XL-BOMD NVE 300 K, dt {args.dt} fs",

@@ -60,11 +60,15 @@ typedef struct {
   double rep_decay;
 } sedacs_model;
 
-/* Run parameters.  precision: 0 = plain FP64 on the CUDA cores; 1 = FP32-class (every
- * dense product on tcgen05 tensor cores with three-way bf16 splitting, FP32 accumulation);
- * 2 = mixed BF16 (SP2 squares with two-way bf16 splitting; S^-1/2 and the core-row
- * back-transform three-way); 3 = pure bf16 SP2 squares (diagnostic).  In 1-3 the Ewald sums
- * run in FP32 with FP64 reductions; electron counts, energies and forces are summed in FP64.
+/* Run parameters.  precision: 0 = plain FP64 on the CUDA cores; 1 = FP32-class on tcgen05
+ * tensor cores with FP32 accumulation: the SP2 squares in the dual half-precision format of
+ * Finkelstein et al. (2021), x = hi + 2^-11 lo in two fp16 planes (22 significant bits; three
+ * products hi*hi + hi*lo + lo*hi), every other dense product with three-way bf16 splitting
+ * (24 bits, six products); 4 = FP32-class with three-way bf16 splitting in every product,
+ * the SP2 squares included; 2 = mixed BF16 (SP2 squares with two-way bf16 splitting; S^-1/2
+ * and the core-row back-transform three-way); 3 = pure bf16 SP2 squares (diagnostic).  In 1-4
+ * the Ewald sums run in FP32 with FP64 reductions; electron counts, energies and forces are
+ * summed in FP64.
  * kernel: 0 = K0 = -c_k0 I (SI Sec. B); 1 = preconditioned rank-m Krylov (SI Sec. B);
  * 2 = learned preconditioner (message-passing network, see sedacs_gnn_*), judged against 1. */
 typedef struct {

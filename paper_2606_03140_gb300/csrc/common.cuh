@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cstdint>
 #include <cstdio>
 
@@ -46,11 +47,21 @@ enum DevErr : int {
 // (columns 8j .. 8j+7) sits at chunk position j ^ (r & 7).  This is the shared-memory
 // image the tensor core reads with the 128-byte swizzle, so one bulk copy moves a
 // block from global memory to a 1024-byte aligned shared tile unchanged.
-// A value x is kept as up to three bf16 planes hi + mid + lo (x - hi - mid rounded).
+// A value x is kept as up to three bf16 planes hi + mid + lo (x - hi - mid rounded), or
+// (format kPlanesF16x2) as two fp16 planes hi + lo: the dual half-precision representation
+// of Finkelstein et al. (2021), x = hi + 2^-11 lo with hi = fp16(x) and lo = fp16(2^11 (x - hi)).
+// |x - hi| <= 2^-11 |x|, so the scaled lo has the magnitude of x and stays out of the fp16
+// subnormal range wherever hi does; hi + 2^-11 lo carries 22 significant bits.
 // ------------------------------------------------------------------------------------
 constexpr int kBlkRows = 128;
 constexpr int kBlkCols = 64;
 constexpr int kBlkBytes = kBlkRows * kBlkCols * 2;   // 16384
+
+// Plane formats: 1, 2, 3 = that many bf16 planes; kPlanesF16x2 = two fp16 planes (hi, scaled lo).
+constexpr int kPlanesF16x2 = 4;
+constexpr float kF16LoScale = 2048.f;
+constexpr float kF16LoInv = 1.f / 2048.f;
+__host__ __device__ constexpr int planes_of(int fmt) { return fmt == kPlanesF16x2 ? 2 : fmt; }
 
 __host__ __device__ inline long long blocked_offset(int row, int col, int n_cols) {
   const int rb = row >> 7, r = row & 127;
@@ -172,6 +183,10 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+// The same with A = B = fp16 (A and B formats 0).
+__host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
 
 // Split x into bf16 planes hi + mid + lo.
 __device__ __forceinline__ void split3(float x, __nv_bfloat16& hi, __nv_bfloat16& mid, __nv_bfloat16& lo) {
@@ -180,6 +195,35 @@ __device__ __forceinline__ void split3(float x, __nv_bfloat16& hi, __nv_bfloat16
   mid = __float2bfloat16_rn(r1);
   const float r2 = r1 - __bfloat162float(mid);
   lo = __float2bfloat16_rn(r2);
+}
+
+// Split x into the fp16 planes hi and lo (x = hi + 2^-11 lo to 22 bits).
+__device__ __forceinline__ void split_f16x2(float x, __half& hi, __half& lo) {
+  hi = __float2half_rn(x);
+  lo = __float2half_rn((x - __half2float(hi)) * kF16LoScale);
+}
+__device__ __forceinline__ float join_f16x2(__half hi, __half lo) {
+  return fmaf(__half2float(lo), kF16LoInv, __half2float(hi));
+}
+
+// Write 8 consecutive values (one 16-byte granule per plane) in plane format fmt at byte
+// offset off of plane 0.
+__device__ __forceinline__ void write_planes8(uint8_t* arena, long long off, long long plane, int fmt,
+                                              const float* v) {
+  if (fmt == kPlanesF16x2) {
+    __align__(16) __half h[8], l[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) split_f16x2(v[e], h[e], l[e]);
+    *reinterpret_cast<uint4*>(arena + off) = *reinterpret_cast<const uint4*>(h);
+    *reinterpret_cast<uint4*>(arena + off + plane) = *reinterpret_cast<const uint4*>(l);
+    return;
+  }
+  __align__(16) __nv_bfloat16 h[8], m[8], l[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) split3(v[e], h[e], m[e], l[e]);
+  *reinterpret_cast<uint4*>(arena + off) = *reinterpret_cast<const uint4*>(h);
+  if (fmt > 1) *reinterpret_cast<uint4*>(arena + off + plane) = *reinterpret_cast<const uint4*>(m);
+  if (fmt > 2) *reinterpret_cast<uint4*>(arena + off + 2 * plane) = *reinterpret_cast<const uint4*>(l);
 }
 
 __device__ __forceinline__ double warp_sum(double v) {

@@ -67,7 +67,7 @@ struct GemmParams {
   Sp2State* sp2;
   int* err;
   int mode;
-  int nsplit_out;     // tensor path: number of bf16 planes written (0..3)
+  int nsplit_out;     // tensor path: plane format written (0: none, 1-3 bf16 planes, 4 two fp16 planes)
   float alpha, beta;
   float g1, g2;
 };

@@ -1,15 +1,16 @@
 // Batched GEMMs over the per-subgraph matrices.
 //
-//  * tc_gemm_persistent<NSPLIT>: 5th-generation tensor cores, one persistent CTA per SM,
-//    six warps.  A producer lane streams 16 KB operand blocks (already in the swizzled
+//  * tc_gemm_persistent<NSPLIT, F16>: 5th-generation tensor cores, one persistent CTA per SM,
+//    ten warps.  A producer lane streams 16 KB operand blocks (already in the swizzled
 //    shared-memory image, see blocked_offset) with bulk copies into a 2-3 stage ring guarded
 //    by mbarriers, across tile boundaries; an MMA lane issues tcgen05.mma (M=128, N=128,
-//    K=16, bf16 in, fp32 in TMEM) over the split products hi*hi (+ hi*mid + mid*hi (+ hi*lo
-//    + mid*mid + lo*hi)) and commits to the ring's "empty" barriers; four epilogue warps
-//    drain TMEM with tcgen05.ld, hand it back to the MMA lane for the next tile, and run the
+//    K=16, fp32 in TMEM) over the split products: bf16 hi*hi (+ hi*mid + mid*hi (+ hi*lo +
+//    mid*mid + lo*hi)), or with F16 the fp16 hi*hi + hi*lo + lo*hi of the two-plane format;
+//    it commits to the ring's "empty" barriers; eight epilogue warps drain TMEM with
+//    tcgen05.ld, hand it back to the MMA lane in three parts for the next tile, and run the
 //    epilogue (generic alpha*AB^T + beta*I + g1*C1 + g2*C2, or one step of the mu-branch SP2
-//    recursion with its trace partials) writing the fp32 master and the split planes of the
-//    result, overlapped with the next tile's MMAs.
+//    recursion with its trace partials) writing the fp32 master and / or the split planes of
+//    the result, overlapped with the next tile's MMAs.
 //  * f64_gemm: the same problems and epilogues in FP64 on the CUDA cores (64x64 tiles).
 #include "dense.cuh"
 
@@ -32,15 +33,9 @@ __device__ __forceinline__ void prod_planes(int idx, int& pa, int& pb) {
   pb = tab_b[idx];
 }
 
-__device__ __forceinline__ void store_planes8(uint8_t* arena, long long base, long long plane, int nsplit,
+__device__ __forceinline__ void store_planes8(uint8_t* arena, long long base, long long plane, int fmt,
                                               int n_pad, int row, int col, const float* v) {
-  __align__(16) __nv_bfloat16 h[8], m[8], l[8];
-#pragma unroll
-  for (int e = 0; e < 8; ++e) split3(v[e], h[e], m[e], l[e]);
-  const long long off = base + blocked_offset(row, col, n_pad);
-  *reinterpret_cast<uint4*>(arena + off) = *reinterpret_cast<const uint4*>(h);
-  if (nsplit > 1) *reinterpret_cast<uint4*>(arena + off + plane) = *reinterpret_cast<const uint4*>(m);
-  if (nsplit > 2) *reinterpret_cast<uint4*>(arena + off + 2 * plane) = *reinterpret_cast<const uint4*>(l);
+  write_planes8(arena, base + blocked_offset(row, col, n_pad), plane, fmt, v);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -70,8 +65,12 @@ struct TcPCfg {
   static constexpr int kSmem = kStages * kStageBytes + kTransBytes + 1024 + 256;
 };
 
-template <int NSPLIT>
+// F16: operands in the two-plane fp16 format (NSPLIT = 2): fp16 MMAs, the corrections
+// accumulator (hi * lo + lo * hi with the scaled lo) weighted by 2^-11 when drained, and the
+// iterate and the output planes in the same format.
+template <int NSPLIT, bool F16>
 __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_persistent(const GemmParams p, int n_work) {
+  static_assert(!F16 || NSPLIT == 2, "fp16 operands come as two planes");
   using Cfg = TcCfg<NSPLIT>;
   using PCfg = TcPCfg<NSPLIT>;
   if (*reinterpret_cast<volatile int*>(p.err) & kErrTimeout) return;
@@ -149,7 +148,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_persistent(const GemmPa
     }
   } else if (warp == kMmaWarp) {
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_bf16_f32(128, 128);
+      constexpr uint32_t idesc = F16 ? idesc_f16_f32(128, 128) : idesc_bf16_f32(128, 128);
       long long g = 0;
       int ti = 0;
       for (int t = blockIdx.x; t < n_work && ok; t += gridDim.x) {
@@ -226,9 +225,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_persistent(const GemmPa
       // first epilogue input (X for the SP2 / response steps, C1 for the generic form), loaded
       // before the accumulators are ready so that its latency hides behind the MMAs
       const float* in1 = nullptr;
-      const uint8_t* in1p = nullptr;                  // ... or three blocked bf16 planes
+      const uint8_t* in1p = nullptr;                  // ... or its blocked planes
       long long in1_plane = 0;
-      if (NSPLIT == 3 && p.mode == kModeSp2 && m.x_planes) {
+      if ((NSPLIT == 3 || F16) && p.mode == kModeSp2 && m.x_planes) {
         in1p = p.arena + m.a_off + in_shift;
         in1_plane = m.a_plane;
       } else if (NSPLIT == 3 && !stepping && m.c_planes && m.c_off >= 0) {
@@ -247,7 +246,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_persistent(const GemmPa
       auto load_in1 = [&](int col, float (*dst)[8]) {
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          if (in1p) {
+          if (F16 && in1p) {
+            const long long off = blocked_offset(row0 + 8 * i + rsub, col + csub, m.n_pad);
+            const uint4 h = __ldg(reinterpret_cast<const uint4*>(in1p + off));
+            const uint4 l = __ldg(reinterpret_cast<const uint4*>(in1p + off + in1_plane));
+            const __half* hb = reinterpret_cast<const __half*>(&h);
+            const __half* lb = reinterpret_cast<const __half*>(&l);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) dst[i][e] = join_f16x2(hb[e], lb[e]);
+          } else if (in1p) {
             const long long off = blocked_offset(row0 + 8 * i + rsub, col + csub, m.n_pad);
             const uint4 h = __ldg(reinterpret_cast<const uint4*>(in1p + off));
             const uint4 md = __ldg(reinterpret_cast<const uint4*>(in1p + off + in1_plane));
@@ -283,7 +290,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_persistent(const GemmPa
           const long long o0 = blocked_offset(row0 + 8 * i + rsub, colh + csub, m.n_pad);
           const long long o1 = blocked_offset(row0 + 8 * i + rsub, colh + 32 + csub, m.n_pad);
 #pragma unroll
-          for (int pl = 0; pl < 3; ++pl) {
+          for (int pl = 0; pl < (F16 ? 2 : 3); ++pl) {
             asm volatile("prefetch.global.L2 [%0];" ::"l"(in1p + o0 + pl * in1_plane));
             asm volatile("prefetch.global.L2 [%0];" ::"l"(in1p + o1 + pl * in1_plane));
           }
@@ -313,7 +320,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_persistent(const GemmPa
           float v2[32];
           tmem_ld32(t_row + 384 + col, v2);
 #pragma unroll
-          for (int j = 0; j < 32; ++j) v[cc][j] += v2[j];
+          for (int j = 0; j < 32; ++j) v[cc][j] = F16 ? fmaf(v2[j], kF16LoInv, v[cc][j]) : v[cc][j] + v2[j];
         }
       }
       release(0);
@@ -334,6 +341,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_persistent(const GemmPa
 
       float* outm = (m.out_off >= 0) ? reinterpret_cast<float*>(p.arena + m.out_off + out_shift) : nullptr;
       const bool planes = m.outp_off >= 0 && p.nsplit_out > 0;
+      const int fmt = F16 ? kPlanesF16x2 : p.nsplit_out;
       const bool mirror = m.sym_out && !diag_tile;
       float tr_x = 0.f, tr_x2 = 0.f;
 #pragma unroll
@@ -393,7 +401,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_persistent(const GemmPa
             dst[0] = make_float4(out[0], out[1], out[2], out[3]);
             dst[1] = make_float4(out[4], out[5], out[6], out[7]);
           }
-          if (planes) store_planes8(p.arena, m.outp_off + out_shift, m.outp_plane, p.nsplit_out, m.n_pad, grow, gcol, out);
+          if (planes) store_planes8(p.arena, m.outp_off + out_shift, m.outp_plane, fmt, m.n_pad, grow, gcol, out);
           if (mirror) {
             *reinterpret_cast<float4*>(tb + tb_idx(rl, csub)) = make_float4(out[0], out[1], out[2], out[3]);
             *reinterpret_cast<float4*>(tb + tb_idx(rl, csub + 4)) = make_float4(out[4], out[5], out[6], out[7]);
@@ -416,7 +424,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_persistent(const GemmPa
               dst[0] = make_float4(tv[0], tv[1], tv[2], tv[3]);
               dst[1] = make_float4(tv[4], tv[5], tv[6], tv[7]);
             }
-            if (planes) store_planes8(p.arena, m.outp_off + out_shift, m.outp_plane, p.nsplit_out, m.n_pad, trow, tcol, tv);
+            if (planes) store_planes8(p.arena, m.outp_off + out_shift, m.outp_plane, fmt, m.n_pad, trow, tcol, tv);
           }
         }
       }
@@ -540,11 +548,11 @@ __global__ void __launch_bounds__(256) f64_gemm_kernel(const GemmParams p) {
 
 static int g_num_sms = 0;
 
-template <int NSPLIT>
+template <int NSPLIT, bool F16 = false>
 static void launch_tc(const GemmParams& p, int n_work, cudaStream_t s) {
   static bool init = false;
   if (!init) {
-    cudaFuncSetAttribute(tc_gemm_persistent<NSPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(tc_gemm_persistent<NSPLIT, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          TcPCfg<NSPLIT>::kSmem);
     init = true;
   }
@@ -555,7 +563,7 @@ static void launch_tc(const GemmParams& p, int n_work, cudaStream_t s) {
     if (g_num_sms <= 0) g_num_sms = 148;
   }
   const int grid = n_work < g_num_sms ? n_work : g_num_sms;
-  tc_gemm_persistent<NSPLIT><<<grid, kTcThreads, TcPCfg<NSPLIT>::kSmem, s>>>(p, n_work);
+  tc_gemm_persistent<NSPLIT, F16><<<grid, kTcThreads, TcPCfg<NSPLIT>::kSmem, s>>>(p, n_work);
 }
 
 void launch_gemm_tc(const GemmParams& p, int n_work, int nsplit, cudaStream_t s) {
@@ -563,6 +571,7 @@ void launch_gemm_tc(const GemmParams& p, int n_work, int nsplit, cudaStream_t s)
   switch (nsplit) {
     case 1: launch_tc<1>(p, n_work, s); break;
     case 2: launch_tc<2>(p, n_work, s); break;
+    case kPlanesF16x2: launch_tc<2, true>(p, n_work, s); break;
     default: launch_tc<3>(p, n_work, s); break;
   }
 }

@@ -16,13 +16,7 @@ __global__ void split_planes_kernel(const SubView* views, uint8_t* arena, int ns
     float x[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) x[e] = (float)src[c8 + e];
-    __align__(16) __nv_bfloat16 h[8], m[8], l[8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) split3(x[e], h[e], m[e], l[e]);
-    const long long off = v.planes + blocked_offset(row, c8, v.n_pad);
-    *reinterpret_cast<uint4*>(arena + off) = *reinterpret_cast<const uint4*>(h);
-    if (nsplit > 1) *reinterpret_cast<uint4*>(arena + off + v.plane_stride) = *reinterpret_cast<const uint4*>(m);
-    if (nsplit > 2) *reinterpret_cast<uint4*>(arena + off + 2 * v.plane_stride) = *reinterpret_cast<const uint4*>(l);
+    write_planes8(arena, v.planes + blocked_offset(row, c8, v.n_pad), v.plane_stride, nsplit, x);
   }
 }
 
@@ -35,7 +29,7 @@ struct AffineOut {
   const SubView* views;   // nullptr: no such output
   double a, b;
   int master;             // write the row-major master
-  int nsplit;             // planes to write (0: none)
+  int nsplit;             // plane format to write (0: none)
 };
 
 template <typename T>
@@ -88,15 +82,7 @@ __global__ void affine_planes_kernel(const SubView* in_v, AffineOut o1, AffineOu
           for (int e = 0; e < 8; ++e) dst[e] = y[e];
         }
       }
-      if (o.nsplit > 0) {
-        __align__(16) __nv_bfloat16 h[8], m[8], l[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) split3(yf[e], h[e], m[e], l[e]);
-        const long long off = vo.planes + blocked_offset(row, c8, vo.n_pad);
-        *reinterpret_cast<uint4*>(arena + off) = *reinterpret_cast<const uint4*>(h);
-        if (o.nsplit > 1) *reinterpret_cast<uint4*>(arena + off + vo.plane_stride) = *reinterpret_cast<const uint4*>(m);
-        if (o.nsplit > 2) *reinterpret_cast<uint4*>(arena + off + 2 * vo.plane_stride) = *reinterpret_cast<const uint4*>(l);
-      }
+      if (o.nsplit > 0) write_planes8(arena, vo.planes + blocked_offset(row, c8, vo.n_pad), vo.plane_stride, o.nsplit, yf);
     }
   }
 }
@@ -146,15 +132,7 @@ __global__ void poly3_kernel(const SubView* e1, const SubView* e2, const SubView
 #pragma unroll
         for (int e = 0; e < 8; ++e) dst[e] = y[e];
       }
-      if (o.nsplit > 0) {
-        __align__(16) __nv_bfloat16 h[8], m[8], l[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) split3(yf[e], h[e], m[e], l[e]);
-        const long long off = vo.planes + blocked_offset(row, c8, vo.n_pad);
-        *reinterpret_cast<uint4*>(arena + off) = *reinterpret_cast<const uint4*>(h);
-        if (o.nsplit > 1) *reinterpret_cast<uint4*>(arena + off + vo.plane_stride) = *reinterpret_cast<const uint4*>(m);
-        if (o.nsplit > 2) *reinterpret_cast<uint4*>(arena + off + 2 * vo.plane_stride) = *reinterpret_cast<const uint4*>(l);
-      }
+      if (o.nsplit > 0) write_planes8(arena, vo.planes + blocked_offset(row, c8, vo.n_pad), vo.plane_stride, o.nsplit, yf);
     }
   }
 }
@@ -282,7 +260,37 @@ __global__ void sp2_advance_kernel(Sp2State* st, const double* slots, const long
   st[i] = s;
 }
 
+// fp16 two-plane iterates (format kPlanesF16x2) of copy `cur` of each subgraph rewritten in
+// place as three bf16 planes (hi + mid + lo of the fp32 value hi + 2^-11 lo, which is exact in
+// fp32), for the products that take them next.  One warp per row, one granule per lane.
+__global__ void f16x2_to_bf16x3_kernel(const SubView* views, const Sp2State* st, long long copy_stride,
+                                       uint8_t* arena) {
+  const SubView v = views[blockIdx.y];
+  const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= v.rows_pad || v.planes < 0) return;
+  const long long base = v.planes + (long long)st[blockIdx.y].cur * copy_stride;
+  for (int c8 = lane * 8; c8 < v.n_pad; c8 += 256) {
+    const long long off = base + blocked_offset(row, c8, v.n_pad);
+    const uint4 hq = *reinterpret_cast<const uint4*>(arena + off);
+    const uint4 lq = *reinterpret_cast<const uint4*>(arena + off + v.plane_stride);
+    const __half* h = reinterpret_cast<const __half*>(&hq);
+    const __half* l = reinterpret_cast<const __half*>(&lq);
+    float x[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) x[e] = join_f16x2(h[e], l[e]);
+    write_planes8(arena, off, v.plane_stride, 3, x);
+  }
+}
+
 }  // namespace
+
+void launch_f16x2_to_bf16x3(const SubView* views, const Sp2State* st, long long copy_stride, int n_sub, int max_rows,
+                            uint8_t* arena, cudaStream_t s) {
+  if (n_sub <= 0 || max_rows <= 0) return;
+  dim3 g((max_rows + 7) / 8, n_sub);
+  f16x2_to_bf16x3_kernel<<<g, 256, 0, s>>>(views, st, copy_stride, arena);
+}
 
 void launch_split_planes(const SubView* views, int n_sub, int max_rows, uint8_t* arena, int nsplit, bool f64,
                          cudaStream_t s) {

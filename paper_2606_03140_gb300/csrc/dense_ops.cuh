@@ -15,10 +15,15 @@ struct SubView {
   int pad;
 };
 
+// nsplit: plane format (1-3 bf16 planes, or kPlanesF16x2).
 void launch_split_planes(const SubView* views, int n_sub, int max_rows, uint8_t* arena, int nsplit, bool f64,
                          cudaStream_t s);
+// Rewrite the kPlanesF16x2 planes of copy st[i].cur of every subgraph as three bf16 planes.
+void launch_f16x2_to_bf16x3(const SubView* views, const Sp2State* st, long long copy_stride, int n_sub, int max_rows,
+                            uint8_t* arena, cudaStream_t s);
 // out1 = a1 in + b1 I (kind 0), the SP2 start (kind 1) or its first-order change (kind 2) from
-// the subgraph bounds; optional out2 = a2 in + b2 I.  Each output: master and / or nsplit planes.
+// the subgraph bounds; optional out2 = a2 in + b2 I.  Each output: master and / or planes
+// (format nsplit).
 void launch_affine_planes(const SubView* in, const SubView* out1, double a1, double b1, int master1, int nsplit1,
                           const SubView* out2, double a2, double b2, int master2, int nsplit2, int kind,
                           const double* bounds, int n_sub, int max_rows, uint8_t* arena, bool f64, cudaStream_t s);

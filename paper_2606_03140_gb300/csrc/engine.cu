@@ -392,9 +392,11 @@ sedacs_status build_op(sedacs_ctx* ctx, int id, int a, int b, int out, int mode,
     m.k_real = L.n_real[i];
     m.b_from_sp2 = b_from_sp2 ? 1 : 0;
     m.a_from_sp2 = a_from_sp2 ? 1 : 0;
-    // three-plane SP2 iterates carry no fp32 master: the SP2 epilogue and the consumers of X
-    // as an addend (C1) read the planes, whose sum is the fp32 value exactly
-    const bool x3 = !ctx->f64 && ctx->nsplit_sp2 == 3;
+    // three-plane bf16 and two-plane fp16 SP2 iterates carry no fp32 master: the SP2 epilogue
+    // reads the planes (the value the MMAs see), and the consumers of X as an addend (C1) read
+    // the three bf16 planes, whose sum is the fp32 value exactly (fp16 iterates are rewritten
+    // in that format once the recursion has stopped)
+    const bool x3 = !ctx->f64 && (ctx->nsplit_sp2 == 3 || ctx->nsplit_sp2 == kPlanesF16x2);
     if (x3 && mode == kModeSp2) {
       m.x_planes = 1;
       m.out_off = -1;
@@ -736,12 +738,12 @@ void compute_ht(sedacs_ctx* ctx) {
 }
 
 // SP2 start X0 = (emax I - h~) / (emax - emin) (and, for the response, dX0 = -dh~ / (emax - emin)).
-// Three-plane iterates are written as planes only (their sum is the fp32 value); the other
-// forms keep the master the epilogue reads.
+// Three-plane bf16 and two-plane fp16 iterates are written as planes only; the other forms keep
+// the master the epilogue reads.  The response replay (with_dx) takes its own plane format.
 void launch_sp2_start(sedacs_ctx* ctx, bool with_dx) {
   const Layout& L = ctx->lay;
-  const int n2 = ctx->nsplit_sp2;
-  const int x_master = (!ctx->f64 && n2 == 3) ? 0 : 1;
+  const int n2 = with_dx ? ctx->nsplit_rsp : ctx->nsplit_sp2;
+  const int x_master = (!ctx->f64 && (n2 == 3 || n2 == kPlanesF16x2)) ? 0 : 1;
   launch_affine_planes(ctx->d_views[kHt], ctx->d_views[kX], 0.0, 0.0, x_master, n2, nullptr, 0.0, 0.0, 0, 0, 1,
                        ctx->d_bounds, L.n_sub, max_rows(ctx), ctx->arena, ctx->f64, ctx->stream);
   if (with_dx)
@@ -798,6 +800,10 @@ sedacs_status run_sp2(sedacs_ctx* ctx, double mu, int kmax) {
     CUCHK(cudaEventRecord(ctx->sp2_ev[k], s));
     ctx->launches += 1;
   }
+  if (ctx->nsplit_sp2 == kPlanesF16x2) {
+    launch_f16x2_to_bf16x3(ctx->d_views[kX], ctx->d_sp2, ctx->slot[kX].copy_stride, L.n_sub, mr, ctx->arena, s);
+    ctx->launches += 1;
+  }
   if (ctx->kstats) {
     CUCHK(cudaStreamSynchronize(s));
     for (int e = ev0; e + 1 < ctx->kev_used; e += 2) {
@@ -818,10 +824,17 @@ sedacs_status run_sp2(sedacs_ctx* ctx, double mu, int kmax) {
   return SEDACS_OK;
 }
 
+// Plane format of the final SP2 iterate for the products that follow: fp16 iterates are
+// rewritten as three bf16 planes when the recursion stops.
+int x_split_final(const sedacs_ctx* ctx) {
+  const int n2 = ctx->nsplit_sp2, ns = ctx->nsplit_ns;
+  return n2 == kPlanesF16x2 ? ns : std::max(n2, ns);
+}
+
 void back_transform(sedacs_ctx* ctx, bool with_w) {
   const int ns = ctx->nsplit_ns;
   const int z = ctx->zc;
-  run_op(ctx, z == 0 ? OP_T1_0 : OP_T1_1, ctx->nsplit_sp2 > ns ? ctx->nsplit_sp2 : ns, ns);   // T1 = Z_c X
+  run_op(ctx, z == 0 ? OP_T1_0 : OP_T1_1, x_split_final(ctx), ns);                            // T1 = Z_c X
   run_op(ctx, z == 0 ? OP_DC0 : OP_DC1, ns, 0);                                          // D_c = 2 T1 Z
   if (with_w) {
     run_op(ctx, OP_T2, ns, ns);                                                          // T2 = T1 h~
@@ -1032,7 +1045,7 @@ sedacs_status response_core(sedacs_ctx* ctx, const double* d_v, double* d_dq) {
   cudaStream_t s = ctx->stream;
   const Layout& L = ctx->lay;
   const int mr = max_rows(ctx);
-  const int ns = ctx->nsplit_ns, n2 = ctx->nsplit_sp2;
+  const int ns = ctx->nsplit_ns, n2 = ctx->nsplit_rsp;
   const int esz = ctx->f64 ? 8 : 4;
   CUCHK(ctx->ew.potential(d_v, ctx->d_tmp, s));
   cudaMemsetAsync(ctx->arena + ctx->slot[kdH].base, 0, L.sq_total * esz, s);
@@ -1216,7 +1229,7 @@ sedacs_status sedacs_create(int32_t n_atoms, const int32_t* species, const doubl
     if (!(box[a] > model->r_off)) return SEDACS_EINVAL;
   for (int i = 0; i < n_atoms; ++i)
     if (species[i] < 0 || species[i] > 2) return SEDACS_EINVAL;
-  if (params->precision < 0 || params->precision > 3 || params->core_size <= 0) return SEDACS_EINVAL;
+  if (params->precision < 0 || params->precision > 4 || params->core_size <= 0) return SEDACS_EINVAL;
   sedacs_ctx* ctx = new sedacs_ctx();
   ctx->N = n_atoms;
   ctx->species_h.assign(species, species + n_atoms);
@@ -1245,7 +1258,10 @@ sedacs_status sedacs_create(int32_t n_atoms, const int32_t* species, const doubl
   ctx->f64 = params->precision == 0;
   ctx->tile = ctx->f64 ? 64 : 128;
   ctx->nsplit_ns = 3;
-  ctx->nsplit_sp2 = params->precision == 1 ? 3 : (params->precision == 2 ? 2 : 1);
+  // SP2 operand format: 1 = two fp16 planes; 4 = three bf16 planes; 2 = two bf16 planes; 3 = one
+  const int sp2_fmt[5] = {3, kPlanesF16x2, 2, 1, 3};
+  ctx->nsplit_sp2 = sp2_fmt[params->precision];
+  ctx->nsplit_rsp = ctx->nsplit_sp2 == kPlanesF16x2 ? 3 : ctx->nsplit_sp2;
   if (ctx->f64) ctx->nsplit_sp2 = 3;
   const int N = n_atoms;
   auto fail = [&](sedacs_status st, const char* msg) {
@@ -1523,9 +1539,6 @@ sedacs_status sedacs_subgraph_matrix(sedacs_ctx* ctx, int32_t part, int32_t whic
     default: sl = kWc; break;
   }
   const int rows = which >= 4 ? nc : nr;
-  if (which == 1 && !ctx->f64) {
-    // s was overwritten by nothing; masters keep it
-  }
   const long long off = mptr(ctx, sl, part);
   double* tmp = nullptr;
   CUCHK(cudaMalloc(&tmp, sizeof(double) * std::max(1, rows * nr)));

@@ -100,6 +100,8 @@ struct sedacs_ctx {
   bool f64 = false;
   int tile = 128;
   int nsplit_sp2 = 3, nsplit_ns = 3;
+  int nsplit_rsp = 3;    // plane format of the first-order SP2 replay (X and dX): fp16 two-plane
+                         // SP2 forms replay in three bf16 planes (dX can exceed the fp16 range)
   // device vectors
   int* d_err = nullptr;
   int* d_species = nullptr;

@@ -1,5 +1,6 @@
 """Parity at the full size of the benchmark workload (9,000-atom water box), in the
-configuration bench.py times (cores ~32 atoms, precision 1 = split-bf16 tcgen05).
+configuration bench.py times (cores ~32 atoms, precision 1: SP2 squares in two fp16 planes, the
+other products three-way split bf16, on tcgen05).
 
 The oracle cannot solve every subgraph of every step in seconds, so it recomputes sampled
 subgraphs one by one: with zero trial charges (no Coulomb shift) on the distance graph,
