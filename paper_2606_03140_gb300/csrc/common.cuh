@@ -179,6 +179,22 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
   d |= (uint64_t)2 << 61;                          // 128-byte swizzle
   return d;
 }
+// Shared-memory descriptor of an MN-major operand with the 128-byte swizzle: each K row holds
+// 64 consecutive MN elements (128 B), 8-row K groups 1024 B apart, 64-element MN atoms
+// atom_stride bytes apart.  A K-major stored block of a symmetric matrix read this way is the
+// operand's transpose, i.e. the block on the other side of the diagonal.
+__device__ __forceinline__ uint64_t smem_desc_sw128_mn(uint32_t saddr, uint32_t atom_stride) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);          // start address
+  d |= (uint64_t)((atom_stride >> 4) & 0x3FFF) << 16;   // leading byte offset: next MN atom
+  d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset: next 8-row K group
+  d |= (uint64_t)1 << 46;                          // descriptor version for tcgen05
+  d |= (uint64_t)2 << 61;                          // 128-byte swizzle
+  return d;
+}
+// Instruction descriptor bits marking A / B as MN-major.
+constexpr uint32_t kIdescTransA = 1u << 15, kIdescTransB = 1u << 16;
+
 // Instruction descriptor: kind::f16, A = B = bf16, D = f32, both K-major, M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);

@@ -67,7 +67,10 @@ struct TcPCfg {
 
 // F16: operands in the two-plane fp16 format (NSPLIT = 2): fp16 MMAs, the corrections
 // accumulator (hi * lo + lo * hi with the scaled lo) weighted by 2^-11 when drained, and the
-// iterate and the output planes in the same format.
+// iterate and the output planes in the same format.  In the SP2 step the symmetric iterate is
+// kept as its upper 128x128 tiles only: an operand block left of the diagonal, (t, kb) with
+// kb / 2 < t, is read as the transpose of the stored block rows of tile (kb / 2, t) (two 8 KB
+// halves, MN-major descriptors), and the epilogue writes no mirrored tile.
 template <int NSPLIT, bool F16>
 __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_persistent(const GemmParams p, int n_work) {
   static_assert(!F16 || NSPLIT == 2, "fp16 operands come as two planes");
@@ -87,6 +90,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_persistent(const GemmPa
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 3);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool stepping = (p.mode == kModeSp2 || p.mode == kModeRsp);
+  const bool upper_only = F16 && p.mode == kModeSp2;
   constexpr uint32_t kTmemCols = NSPLIT > 1 ? 512 : 128;
 
   if (threadIdx.x == 0) {
@@ -134,10 +138,31 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_persistent(const GemmPa
           uint8_t* st = smem + s * Cfg::kStageBytes;
           const long long aoff = ((long long)w.tm * nkb + kb) * kBlkBytes;
           const long long boff = ((long long)w.tn * nkb + kb) * kBlkBytes;
+          if (upper_only) {
+            // operand rows t, columns kb: stored block, or rows kb of the stored tile (kb / 2, t)
+            auto load_sym = [&](uint8_t* dst, const uint8_t* src, long long plane, int t) {
+              if ((kb >> 1) < t) {
+                const long long o = ((long long)(kb >> 1) * nkb + 2 * t) * kBlkBytes + (kb & 1) * (kBlkBytes / 2);
 #pragma unroll
-          for (int pl = 0; pl < NSPLIT; ++pl) {
-            bulk_g2s(st + pl * kBlkBytes, A + pl * m.a_plane + aoff, kBlkBytes, &full[s]);
-            bulk_g2s(st + (NSPLIT + pl) * kBlkBytes, B + pl * m.b_plane + boff, kBlkBytes, &full[s]);
+                for (int pl = 0; pl < NSPLIT; ++pl) {
+                  bulk_g2s(dst + pl * kBlkBytes, src + pl * plane + o, kBlkBytes / 2, &full[s]);
+                  bulk_g2s(dst + pl * kBlkBytes + kBlkBytes / 2, src + pl * plane + o + kBlkBytes, kBlkBytes / 2,
+                           &full[s]);
+                }
+              } else {
+                const long long o = ((long long)t * nkb + kb) * kBlkBytes;
+#pragma unroll
+                for (int pl = 0; pl < NSPLIT; ++pl) bulk_g2s(dst + pl * kBlkBytes, src + pl * plane + o, kBlkBytes, &full[s]);
+              }
+            };
+            load_sym(st, A, m.a_plane, w.tm);
+            load_sym(st + NSPLIT * kBlkBytes, B, m.b_plane, w.tn);
+          } else {
+#pragma unroll
+            for (int pl = 0; pl < NSPLIT; ++pl) {
+              bulk_g2s(st + pl * kBlkBytes, A + pl * m.a_plane + aoff, kBlkBytes, &full[s]);
+              bulk_g2s(st + (NSPLIT + pl) * kBlkBytes, B + pl * m.b_plane + boff, kBlkBytes, &full[s]);
+            }
           }
         }
       }
@@ -172,21 +197,25 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_persistent(const GemmPa
           if (!mbar_wait(&full[s], (uint32_t)(round & 1))) { ok = false; break; }
           tc_fence_after();
           const uint32_t st = smem_u32(smem + s * Cfg::kStageBytes);
+          // operands left of the diagonal arrive transposed (MN-major), see the producer
+          const bool a_t = upper_only && (kb >> 1) < w.tm, b_t = upper_only && (kb >> 1) < w.tn;
+          const uint32_t id = idesc | (a_t ? kIdescTransA : 0u) | (b_t ? kIdescTransB : 0u);
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
 #pragma unroll
             for (int pr = 0; pr < Cfg::kNumProd; ++pr) {
               int pa, pb;
               prod_planes(pr, pa, pb);
-              const uint64_t ad = smem_desc_sw128(st + pa * kBlkBytes + kk * 32);
-              const uint64_t bd = smem_desc_sw128(st + (NSPLIT + pb) * kBlkBytes + kk * 32);
+              const uint32_t sa = st + pa * kBlkBytes, sb = st + (NSPLIT + pb) * kBlkBytes;
+              const uint64_t ad = a_t ? smem_desc_sw128_mn(sa + kk * 2048, kBlkBytes / 2) : smem_desc_sw128(sa + kk * 32);
+              const uint64_t bd = b_t ? smem_desc_sw128_mn(sb + kk * 2048, kBlkBytes / 2) : smem_desc_sw128(sb + kk * 32);
               const int hsel = kb % 3;
               const uint32_t acc_col = (NSPLIT == 1) ? 0u : (pr == 0 ? 128u * hsel : 384u);
               uint32_t accum;
               if (NSPLIT == 1) accum = (kb | kk) != 0 ? 1u : 0u;
               else if (pr == 0) accum = (kb >= 3 || kk != 0) ? 1u : 0u;
               else accum = (pr == 1 && (kb | kk) == 0) ? 0u : 1u;
-              tc_mma_bf16(tmem + acc_col, ad, bd, idesc, accum);
+              tc_mma_bf16(tmem + acc_col, ad, bd, id, accum);
             }
           }
           tc_commit(&empty[s]);
@@ -342,7 +371,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_persistent(const GemmPa
       float* outm = (m.out_off >= 0) ? reinterpret_cast<float*>(p.arena + m.out_off + out_shift) : nullptr;
       const bool planes = m.outp_off >= 0 && p.nsplit_out > 0;
       const int fmt = F16 ? kPlanesF16x2 : p.nsplit_out;
-      const bool mirror = m.sym_out && !diag_tile;
+      const bool mirror = m.sym_out && !diag_tile && !upper_only;
       float tr_x = 0.f, tr_x2 = 0.f;
 #pragma unroll
       for (int cc = 0; cc < 2; ++cc) {

@@ -260,26 +260,58 @@ __global__ void sp2_advance_kernel(Sp2State* st, const double* slots, const long
   st[i] = s;
 }
 
-// fp16 two-plane iterates (format kPlanesF16x2) of copy `cur` of each subgraph rewritten in
-// place as three bf16 planes (hi + mid + lo of the fp32 value hi + 2^-11 lo, which is exact in
-// fp32), for the products that take them next.  One warp per row, one granule per lane.
+// fp16 two-plane SP2 iterates (format kPlanesF16x2) of copy `cur` of each subgraph rewritten as
+// three bf16 planes (hi + mid + lo of the fp32 value hi + 2^-11 lo, which is exact in fp32) for
+// the products that take them next.  The recursion keeps only the upper 128x128 tiles of the
+// symmetric iterate, so pass 0 fills each 128x64 block left of the diagonal ((cb / 2) < rb) from
+// the transpose of rows 64 (cb & 1) .. of the stored tile (cb / 2, rb), through shared memory;
+// pass 1 then converts the stored blocks in place.  One CTA per block.
 __global__ void f16x2_to_bf16x3_kernel(const SubView* views, const Sp2State* st, long long copy_stride,
-                                       uint8_t* arena) {
+                                       uint8_t* arena, int pass) {
+  __shared__ float tr[64][129];
   const SubView v = views[blockIdx.y];
-  const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (row >= v.rows_pad || v.planes < 0) return;
+  if (v.planes < 0) return;
+  const int nkb = v.n_pad >> 6, nrb = v.rows_pad >> 7;
+  const int rb = blockIdx.x / nkb, cb = blockIdx.x % nkb;
+  if (rb >= nrb) return;
+  const bool lower = (cb >> 1) < rb;
+  if (lower != (pass == 0)) return;
+  const long long ps = v.plane_stride;
   const long long base = v.planes + (long long)st[blockIdx.y].cur * copy_stride;
-  for (int c8 = lane * 8; c8 < v.n_pad; c8 += 256) {
-    const long long off = base + blocked_offset(row, c8, v.n_pad);
+  const long long dst = base + ((long long)rb * nkb + cb) * kBlkBytes;
+  auto load8 = [&](long long off, float* x) {
     const uint4 hq = *reinterpret_cast<const uint4*>(arena + off);
-    const uint4 lq = *reinterpret_cast<const uint4*>(arena + off + v.plane_stride);
+    const uint4 lq = *reinterpret_cast<const uint4*>(arena + off + ps);
     const __half* h = reinterpret_cast<const __half*>(&hq);
     const __half* l = reinterpret_cast<const __half*>(&lq);
-    float x[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) x[e] = join_f16x2(h[e], l[e]);
-    write_planes8(arena, off, v.plane_stride, 3, x);
+  };
+  if (!lower) {
+    for (int g = threadIdx.x; g < kBlkBytes / 16; g += blockDim.x) {   // elementwise: any granule order
+      float x[8];
+      load8(dst + (long long)g * 16, x);
+      write_planes8(arena, dst + (long long)g * 16, ps, 3, x);
+    }
+    return;
+  }
+  // source: 64 rows x 128 columns, blocks (cb / 2, 2 rb) and (cb / 2, 2 rb + 1), rows 64 (cb & 1) ..
+  const long long src = base + ((long long)(cb >> 1) * nkb + 2 * rb) * kBlkBytes + (cb & 1) * (kBlkBytes / 2);
+  for (int g = threadIdx.x; g < 1024; g += blockDim.x) {
+    const int sr = g >> 4, half = (g >> 3) & 1, j = g & 7;
+    float x[8];
+    load8(src + (long long)half * kBlkBytes + sr * 128 + ((j ^ (sr & 7)) << 4), x);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) tr[sr][half * 64 + j * 8 + e] = x[e];
+  }
+  __syncthreads();
+  // destination row r (source column), columns 8 j .. 8 j + 7 (source rows)
+  for (int g = threadIdx.x; g < 1024; g += blockDim.x) {
+    const int r = g >> 3, j = g & 7;
+    float x[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) x[e] = tr[8 * j + e][r];
+    write_planes8(arena, dst + r * 128 + ((j ^ (r & 7)) << 4), ps, 3, x);
   }
 }
 
@@ -288,8 +320,8 @@ __global__ void f16x2_to_bf16x3_kernel(const SubView* views, const Sp2State* st,
 void launch_f16x2_to_bf16x3(const SubView* views, const Sp2State* st, long long copy_stride, int n_sub, int max_rows,
                             uint8_t* arena, cudaStream_t s) {
   if (n_sub <= 0 || max_rows <= 0) return;
-  dim3 g((max_rows + 7) / 8, n_sub);
-  f16x2_to_bf16x3_kernel<<<g, 256, 0, s>>>(views, st, copy_stride, arena);
+  dim3 g((max_rows / 128) * (max_rows / 64), n_sub);
+  for (int pass = 0; pass < 2; ++pass) f16x2_to_bf16x3_kernel<<<g, 256, 0, s>>>(views, st, copy_stride, arena, pass);
 }
 
 void launch_split_planes(const SubView* views, int n_sub, int max_rows, uint8_t* arena, int nsplit, bool f64,

@@ -18,7 +18,8 @@ struct SubView {
 // nsplit: plane format (1-3 bf16 planes, or kPlanesF16x2).
 void launch_split_planes(const SubView* views, int n_sub, int max_rows, uint8_t* arena, int nsplit, bool f64,
                          cudaStream_t s);
-// Rewrite the kPlanesF16x2 planes of copy st[i].cur of every subgraph as three bf16 planes.
+// Rewrite the kPlanesF16x2 planes of copy st[i].cur of every subgraph, stored as its upper
+// 128x128 tiles, as the full matrix in three bf16 planes (two launches).
 void launch_f16x2_to_bf16x3(const SubView* views, const Sp2State* st, long long copy_stride, int n_sub, int max_rows,
                             uint8_t* arena, cudaStream_t s);
 // out1 = a1 in + b1 I (kind 0), the SP2 start (kind 1) or its first-order change (kind 2) from

@@ -802,7 +802,7 @@ sedacs_status run_sp2(sedacs_ctx* ctx, double mu, int kmax) {
   }
   if (ctx->nsplit_sp2 == kPlanesF16x2) {
     launch_f16x2_to_bf16x3(ctx->d_views[kX], ctx->d_sp2, ctx->slot[kX].copy_stride, L.n_sub, mr, ctx->arena, s);
-    ctx->launches += 1;
+    ctx->launches += 2;
   }
   if (ctx->kstats) {
     CUCHK(cudaStreamSynchronize(s));
