@@ -235,12 +235,10 @@ __global__ void sp2_init_kernel(Sp2State* st, const double* bounds, const int* n
 
 // One step of the recursion control: t_k = Tr(X) - Tr(X^2) from the diagonal-tile slots,
 // branch of the image y, stop after the first step with t_k < tol (or kmax steps).
-__global__ void sp2_advance_kernel(Sp2State* st, const double* slots, const long long* tr_off,
-                                   const int* n_diag, int* n_active, int n) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+__device__ int sp2_advance_one(Sp2State* st, const double* slots, const long long* tr_off, const int* n_diag,
+                               int i) {
   Sp2State s = st[i];
-  if (!s.active) return;
+  if (!s.active) return 0;
   double a = 0.0, b = 0.0;
   for (int q = 0; q < 4 * n_diag[i]; ++q) {     // fixed order: tiles, then warps
     a += slots[tr_off[i] + 2 * q];
@@ -256,8 +254,22 @@ __global__ void sp2_advance_kernel(Sp2State* st, const double* slots, const long
   // asymptotic regime (rounding noise floor of the arithmetic in use)
   const bool floor_hit = s.iters >= 4 && s.t2 < s.floor_guard && s.t >= s.t2;
   if (s.t < s.tol || floor_hit || s.iters >= s.kmax) s.active = 0;
-  else atomicAdd(n_active, 1);
   st[i] = s;
+  return s.active;
+}
+
+// One block; *n_active receives the number of subgraphs still active (it may point to mapped
+// host memory, which the host reads once the stream has passed this launch).
+__global__ void sp2_advance_kernel(Sp2State* st, const double* slots, const long long* tr_off,
+                                   const int* n_diag, int* n_active, int n) {
+  __shared__ int count;
+  if (threadIdx.x == 0) count = 0;
+  __syncthreads();
+  int mine = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) mine += sp2_advance_one(st, slots, tr_off, n_diag, i);
+  if (mine) atomicAdd(&count, mine);
+  __syncthreads();
+  if (threadIdx.x == 0) *reinterpret_cast<volatile int*>(n_active) = count;
 }
 
 // fp16 two-plane SP2 iterates (format kPlanesF16x2) of copy `cur` of each subgraph rewritten as
@@ -378,7 +390,7 @@ void launch_sp2_init(Sp2State* st, const double* bounds, const int* n_real, doub
 void launch_sp2_advance(Sp2State* st, const double* slots, const long long* tr_off, const int* n_diag,
                         int* n_active, int n, cudaStream_t s) {
   if (n <= 0) return;
-  sp2_advance_kernel<<<(n + 127) / 128, 128, 0, s>>>(st, slots, tr_off, n_diag, n_active, n);
+  sp2_advance_kernel<<<1, 1024, 0, s>>>(st, slots, tr_off, n_diag, n_active, n);
 }
 
 }  // namespace sedacs

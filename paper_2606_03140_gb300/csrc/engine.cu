@@ -766,11 +766,10 @@ sedacs_status run_sp2(sedacs_ctx* ctx, double mu, int kmax) {
     if (ctx->h_nactive) CUCHK(cudaFreeHost(ctx->h_nactive));
     ctx->h_nactive = nullptr;
     ctx->h_nactive_cap = 0;
-    CUCHK(cudaHostAlloc(reinterpret_cast<void**>(&ctx->h_nactive), sizeof(int) * kmax, cudaHostAllocDefault));
+    // mapped: the control kernel writes each step's active count straight into it
+    CUCHK(cudaHostAlloc(reinterpret_cast<void**>(&ctx->h_nactive), sizeof(int) * kmax, cudaHostAllocMapped));
+    CUCHK(cudaHostGetDevicePointer(reinterpret_cast<void**>(&ctx->h_nactive_dev), ctx->h_nactive, 0));
     ctx->h_nactive_cap = kmax;
-    cudaFree(ctx->d_nactive);
-    ctx->d_nactive = nullptr;
-    CUCHK(cudaMalloc(&ctx->d_nactive, sizeof(int) * kmax));
   }
   while ((int)ctx->sp2_ev.size() < kmax) {
     cudaEvent_t e;
@@ -782,7 +781,6 @@ sedacs_status run_sp2(sedacs_ctx* ctx, double mu, int kmax) {
   // subgraph stopped find no active tile and return at once.
   constexpr int kLookahead = 3;
   const int ev0 = ctx->kev_used;
-  CUCHK(cudaMemsetAsync(ctx->d_nactive, 0, sizeof(int) * kmax, s));
   for (int k = 0; k < kmax; ++k) {
     if (k >= kLookahead) {
       CUCHK(cudaEventSynchronize(ctx->sp2_ev[k - kLookahead]));
@@ -795,8 +793,7 @@ sedacs_status run_sp2(sedacs_ctx* ctx, double mu, int kmax) {
       cudaEventRecord(ctx->kev[ctx->kev_used + 1], s);
       ctx->kev_used += 2;
     }
-    launch_sp2_advance(ctx->d_sp2, ctx->d_slots, ctx->d_tr_off, ctx->d_n_diag, ctx->d_nactive + k, L.n_sub, s);
-    CUCHK(cudaMemcpyAsync(ctx->h_nactive + k, ctx->d_nactive + k, sizeof(int), cudaMemcpyDeviceToHost, s));
+    launch_sp2_advance(ctx->d_sp2, ctx->d_slots, ctx->d_tr_off, ctx->d_n_diag, ctx->h_nactive_dev + k, L.n_sub, s);
     CUCHK(cudaEventRecord(ctx->sp2_ev[k], s));
     ctx->launches += 1;
   }

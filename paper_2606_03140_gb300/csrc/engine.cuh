@@ -197,7 +197,8 @@ struct sedacs_ctx {
   bool fuse_forces = false;  // the next density's observables pass also contracts the forces
   bool du_ready = false;     // d_dU holds the band-structure force terms of the last density
   int ew_tag = 0;         // tag of the Coulomb potential of d_n at the current geometry
-  int* h_nactive = nullptr;
+  int* h_nactive = nullptr;        // mapped pinned: active subgraphs after each SP2 step
+  int* h_nactive_dev = nullptr;    // its device alias
   int h_nactive_cap = 0;
   std::vector<cudaEvent_t> sp2_ev;
   int kev_used = 0;
