@@ -137,7 +137,12 @@ __global__ void poly3_kernel(const SubView* e1, const SubView* e2, const SubView
   }
 }
 
-// Gershgorin: per row (one warp), d - r and d + r of the valid block.
+// Gershgorin: per row (one warp), d - r and d + r of the valid block.  FP64 form: every
+// magnitude is added in FP64.  FP32 form: each lane sums its n / 32 magnitudes in FP32 and the
+// lanes combine in FP64, so that the row costs two FP64 conversions per lane (the FP64 pipe is
+// narrow); the radius is then widened by k 2^-23 of itself, more than the relative rounding
+// error (k - 1) 2^-24 of a lane's FP32 sum of k = ceil(n / 32) positive terms, so that the disc
+// still contains the exact one.
 template <typename T>
 __global__ void gersh_rows_kernel(const SubView* views, const uint8_t* arena, double* lo, double* hi,
                                   const long long* row_base) {
@@ -146,9 +151,8 @@ __global__ void gersh_rows_kernel(const SubView* views, const uint8_t* arena, do
   const int lane = threadIdx.x & 31;
   if (row >= v.n_real) return;
   const T* src = reinterpret_cast<const T*>(arena + v.master) + (long long)row * v.n_pad;
-  double s = 0.0, d = 0.0;
-  // four consecutive columns per lane and step (rows are 16-byte aligned, padding is zero);
-  // the four magnitudes are added in T, the running sum in FP64
+  T s_t = 0, d_t = 0;
+  // four consecutive columns per lane and step (rows are 16-byte aligned, padding is zero)
   for (int c4 = lane * 4; c4 < v.n_real; c4 += 128) {
     T x[4];
     if (sizeof(T) == 4) {
@@ -158,17 +162,17 @@ __global__ void gersh_rows_kernel(const SubView* views, const uint8_t* arena, do
 #pragma unroll
       for (int e = 0; e < 4; ++e) x[e] = src[c4 + e];
     }
-    T part = 0;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      const bool dg = (c4 + e) == row;
-      if (dg) d = (double)x[e];
-      else part += (c4 + e) < v.n_real ? fabs(x[e]) : (T)0;
+      const int c = c4 + e;
+      const T a = c < v.n_real ? x[e] : (T)0;
+      if (c == row) d_t = a;
+      else s_t += fabs(a);
     }
-    s += (double)part;
   }
-  s = warp_sum(s);
-  d = warp_sum(d);
+  double s = warp_sum((double)s_t);
+  const double d = warp_sum((double)d_t);
+  if (sizeof(T) == 4) s *= 1.0 + (double)((v.n_real + 31) / 32) * 0x1p-23;
   if (lane == 0) {
     lo[row_base[blockIdx.y] + row] = d - s;
     hi[row_base[blockIdx.y] + row] = d + s;
