@@ -974,7 +974,7 @@ sedacs_status forces_core(sedacs_ctx* ctx) {
   CUCHK(ctx->ew.gradient(ctx->d_tmp, ctx->d_n, ctx->d_F, s, ctx->ew_tag));
   add_kernel<<<nblk(3 * ctx->N, 256), 256, 0, s>>>(ctx->d_dU, ctx->d_F, 3 * ctx->N);
   launch_repulsion(ctx->model, ctx->d_R, ctx->d_species, sk_geom(ctx), ctx->d_pptr, ctx->d_pcol, ctx->N, ctx->d_erep,
-                   ctx->d_dU, s);
+                   ctx->d_dU, ctx->f64, s);
   neg_kernel<<<nblk(3 * ctx->N, 256), 256, 0, s>>>(ctx->d_dU, ctx->d_F, 3 * ctx->N);
   nan_scan_kernel<<<nblk(3 * ctx->N, 256), 256, 0, s>>>(ctx->d_F, 3 * ctx->N, ctx->d_err);
   dot_kernel<<<1, 1024, 0, s>>>(ctx->d_erep, nullptr, ctx->N, ctx->d_scal + 3);

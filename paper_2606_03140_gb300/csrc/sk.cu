@@ -350,8 +350,10 @@ __global__ void gd_kernel(const ModelDev m, const long long* sub_ptr, const int*
 }
 
 // Repulsion energy per atom (1/2 sum) and its gradient, over the pair CSR (images within r_off).
-// Warp per atom A, lanes over its pair-list entries; FP64 throughout, lane sums combined by a
-// fixed shuffle tree.
+// Warp per atom A, lanes over its pair-list entries, lane sums combined by a fixed shuffle tree.
+// T = double: FP64 throughout.  T = float (the FP32 forms): each image term in FP32 from the
+// FP64 minimum-image displacement, the sums over pairs in FP64.
+template <typename T>
 __global__ void repulsion_kernel(const ModelDev m, const double* R, const int* species, SkGeom g,
                                  const long long* pptr, const int* pcol, int N, double* erep_atom, double* dU) {
   const int A = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -359,28 +361,39 @@ __global__ void repulsion_kernel(const ModelDev m, const double* R, const int* s
   if (A >= N) return;
   double e = 0.0, ga[3] = {0.0, 0.0, 0.0};
   const int sa = species[A];
+  const double inv_box[3] = {1.0 / g.box[0], 1.0 / g.box[1], 1.0 / g.box[2]};
+  const T r_off = (T)m.r_off, r_on = (T)m.r_on, inv_decay = (T)(1.0 / m.rep_decay);
   for (long long p = pptr[A] + lane; p < pptr[A + 1]; p += 32) {
     const int B = pcol[p];
     const double amp = m.rep_a[sa][species[B]];
     if (amp == 0.0) continue;
     double d0[3];
-    min_image(R, A, B, g.box, d0);
+    if (sizeof(T) == 8) {
+      min_image(R, A, B, g.box, d0);
+    } else {
+      // FP32 form: the minimum image by multiplication (the displacement is needed to FP32 only)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const double x = R[3 * B + c] - R[3 * A + c];
+        d0[c] = x - g.box[c] * rint(x * inv_box[c]);
+      }
+    }
     for (int ix = -g.nimg[0]; ix <= g.nimg[0]; ++ix)
       for (int iy = -g.nimg[1]; iy <= g.nimg[1]; ++iy)
         for (int iz = -g.nimg[2]; iz <= g.nimg[2]; ++iz) {
-          const double d[3] = {d0[0] + ix * g.box[0], d0[1] + iy * g.box[1], d0[2] + iz * g.box[2]};
-          const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-          if (r >= m.r_off || r == 0.0) continue;
-          double sw = 1.0, dsw = 0.0;
-          if (r > m.r_on) {
-            const double w = m.r_off - m.r_on, t = (r - m.r_on) / w;
+          const T d[3] = {(T)(d0[0] + ix * g.box[0]), (T)(d0[1] + iy * g.box[1]), (T)(d0[2] + iz * g.box[2])};
+          const T r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+          if (r >= r_off || r == (T)0) continue;
+          T sw = 1, dsw = 0;
+          if (r > r_on) {
+            const T w = r_off - r_on, t = (r - r_on) / w;
             sw = 1 - 10 * t * t * t + 15 * t * t * t * t - 6 * t * t * t * t * t;
             dsw = (-30 * t * t + 60 * t * t * t - 30 * t * t * t * t) / w;
           }
-          const double ex = exp(-r / m.rep_decay);
-          e += 0.5 * amp * ex * sw;
-          const double de = amp * ex * (dsw - sw / m.rep_decay);
-          for (int c = 0; c < 3; ++c) ga[c] -= de * d[c] / r;
+          const T ex = exp(-r * inv_decay);
+          e += 0.5 * amp * (double)(ex * sw);
+          const T de = (T)amp * ex * (dsw - sw * inv_decay);
+          for (int c = 0; c < 3; ++c) ga[c] -= (double)(de * d[c] / r);
         }
   }
   e = warp_sum(e);
@@ -458,8 +471,9 @@ void launch_gd(const ModelDev& m, const long long* sub_ptr, const int* sub_atoms
 }
 
 void launch_repulsion(const ModelDev& m, const double* R, const int* species, const SkGeom& g, const long long* pptr,
-                      const int* pcol, int N, double* erep_atom, double* dU, cudaStream_t s) {
-  repulsion_kernel<<<(N + 3) / 4, 128, 0, s>>>(m, R, species, g, pptr, pcol, N, erep_atom, dU);
+                      const int* pcol, int N, double* erep_atom, double* dU, bool f64, cudaStream_t s) {
+  if (f64) repulsion_kernel<double><<<(N + 3) / 4, 128, 0, s>>>(m, R, species, g, pptr, pcol, N, erep_atom, dU);
+  else repulsion_kernel<float><<<(N + 3) / 4, 128, 0, s>>>(m, R, species, g, pptr, pcol, N, erep_atom, dU);
 }
 
 }  // namespace sedacs

@@ -31,6 +31,6 @@ void launch_gd(const ModelDev& m, const long long* sub_ptr, const int* sub_atoms
                const void* Dc, bool f64, const long long* dc_off, const int* n_pad, const long long* gd_ptr, int* gd_col,
                double* gd_val, cudaStream_t s);
 void launch_repulsion(const ModelDev& m, const double* R, const int* species, const SkGeom& g, const long long* pptr,
-                      const int* pcol, int N, double* erep_atom, double* dU, cudaStream_t s);
+                      const int* pcol, int N, double* erep_atom, double* dU, bool f64, cudaStream_t s);
 
 }  // namespace sedacs
