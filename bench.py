@@ -55,8 +55,8 @@ METRIC = "atoms*QMD-steps/s at |dq|<=1e-5 e vs FP64 oracle (mixed vs plain, one 
 # over the SP2 launches of 2 timed steps of the 9,000-atom water workload in the mixed form (one
 # ncu capture, profiles/tc_gemm_sp2_traffic_water9000.md).  Reported only while the kernel
 # source is the one the counters were taken on.
-SP2_TRAFFIC = {"bytes_per_launch": 506.7e6, "workload": "water9000", "precision": 1,
-               "kernel_sha1": "fa7afaacd8c46a32a3324ab33f7cd7edc8eac0c7"}
+SP2_TRAFFIC = {"bytes_per_launch": 182.9e6, "workload": "water9000", "precision": 1,
+               "kernel_sha1": "e871c95712a1e99b93bfd72c7d410d65e2468ce3"}
 
 
 def kernel_sha1() -> str:
