@@ -152,7 +152,9 @@ __global__ void gersh_rows_kernel(const SubView* views, const uint8_t* arena, do
   if (row >= v.n_real) return;
   const T* src = reinterpret_cast<const T*>(arena + v.master) + (long long)row * v.n_pad;
   T s_t = 0, d_t = 0;
-  // four consecutive columns per lane and step (rows are 16-byte aligned, padding is zero)
+  // four consecutive columns per lane and step (rows are 16-byte aligned, padding is zero);
+  // unrolled so that a lane's loads of one row are in flight together
+#pragma unroll 4
   for (int c4 = lane * 4; c4 < v.n_real; c4 += 128) {
     T x[4];
     if (sizeof(T) == 4) {

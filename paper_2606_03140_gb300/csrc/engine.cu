@@ -913,8 +913,7 @@ sedacs_status density_core(sedacs_ctx* ctx, double* mu_io, bool allow_resolve = 
   phase_end(ctx, 0, 2);
   phase_begin(ctx, 0);
   if (!ctx->z_valid) compute_z(ctx);
-  if (!ctx->f64) launch_split_planes(ctx->d_views[kH], ctx->lay.n_sub, max_rows(ctx), ctx->arena, ctx->nsplit_ns, false, s);
-  compute_ht(ctx);
+  compute_ht(ctx);                      // h's planes were written by gather_hs
   CUCHK(cudaStreamSynchronize(s));
   phase_end(ctx, 0, 3);
   double mu = *mu_io;

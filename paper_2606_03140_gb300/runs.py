@@ -21,15 +21,17 @@ def ground_state(workload: str, precision: int, seed_v: int = 20260703, quick: b
 
     Returns (system, model, ctx, R, V, n, info) with ctx ready for sedacs_xlbomd_init (kernel
     K0).  The ground state comes from the kernel-accelerated quasi-Newton SCC (SI Sec. C, rank-4
-    Krylov) in the mixed form; the plain FP64 form (precision 0) receives its charges, mu and
-    density graph, so both forms start from the same state.  quick=True starts from zero charges
-    (same per-step work, no SCC)."""
+    Krylov) in the three-plane bf16 form (precision 4, 24-bit products); a context of the
+    requested form (FP64 plain, or the two-plane fp16 SP2 form 1) then receives its charges, mu
+    and density graph, so all forms start from the same state.
+    quick=True starts from zero charges (same per-step work, no SCC)."""
     s = I.workload(workload)
     model = I.default_model()
     R = np.ascontiguousarray(s.R.copy())
     n = np.zeros(s.n_atoms)
     V = np.ascontiguousarray(I.maxwell_boltzmann(s.species, 300.0, seed_v, model))
-    prm = S.sedacs_default_params(core_size=core_size, precision=precision if precision > 0 else 1,
+    scc_precision = 4 if precision in (0, 1) else precision
+    prm = S.sedacs_default_params(core_size=core_size, precision=scc_precision,
                                   scc_tol=2e-5, kernel=1, krylov_rank=4)
     ctx = S.sedacs_create(s.species, s.box, model, prm)
     S.sedacs_graph_build(ctx, R)
@@ -48,10 +50,10 @@ def ground_state(workload: str, precision: int, seed_v: int = 20260703, quick: b
             S.sedacs_destroy(ctx)
             raise NoGroundState(f"{workload}: SCC ground state not reached (max residual {res2}); the "
                                 "zero-temperature SCC does not converge for this workload")
-    if precision == 0:
+    if precision != scc_precision:
         gd = S.sedacs_density_graph_get(ctx, s.n_atoms)
         S.sedacs_destroy(ctx)
-        prm = S.sedacs_default_params(core_size=core_size, precision=0)
+        prm = S.sedacs_default_params(core_size=core_size, precision=precision)
         ctx = S.sedacs_create(s.species, s.box, model, prm)
         S.sedacs_graph_build(ctx, R, gd=gd)
         S.sedacs_partition(ctx, R)
