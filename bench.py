@@ -56,15 +56,39 @@ METRIC = "atoms*QMD-steps/s at |dq|<=1e-5 e vs FP64 oracle (mixed vs plain, one 
 # ncu capture, profiles/tc_gemm_sp2_traffic_water9000.md).  Reported only while the kernel
 # source is the one the counters were taken on.
 SP2_TRAFFIC = {"bytes_per_launch": 182.9e6, "workload": "water9000", "precision": 1,
-               "kernel_sha1": "e871c95712a1e99b93bfd72c7d410d65e2468ce3"}
+               "kernel_sha1": "5b91c84eede22b3ba5e372166adf3648e1512de0"}
+
+
+def strip_comments(src: str) -> str:
+    """C/C++ source without comments and blank lines (string literals kept)."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c == '"':
+            j = i + 1
+            while j < n and src[j] != '"':
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            while i < n and src[i] != "\n":
+                i += 1
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    return "\n".join(line.rstrip() for line in "".join(out).splitlines() if line.strip())
 
 
 def kernel_sha1() -> str:
+    """sha1 of the SP2 kernel's source (dense_gemm.cu, dense.cuh, common.cuh), comments stripped."""
     import hashlib
     h = hashlib.sha1()
     for f in ("dense_gemm.cu", "dense.cuh", "common.cuh"):
-        with open(os.path.join(ROOT, "paper_2606_03140_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2606_03140_gb300", "csrc", f), encoding="utf-8") as fh:
+            h.update(strip_comments(fh.read()).encode())
     return h.hexdigest()
 UNIT = "atom-steps/s"
 

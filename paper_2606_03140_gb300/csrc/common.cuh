@@ -39,7 +39,7 @@ enum DevErr : int {
 };
 
 // ------------------------------------------------------------------------------------
-// Blocked split-bf16 operand layout ("UMMA-blocked").
+// Blocked split-plane operand layout ("UMMA-blocked").
 //
 // A matrix of n_rows x n_cols (both multiples of 128 / 64) is stored as blocks of
 // 128 rows x 64 columns, block (rb, kb) at byte offset (rb * (n_cols / 64) + kb) * 16384.

@@ -1,5 +1,5 @@
 // Batched dense kernels on the per-subgraph matrices: problem descriptors shared by the
-// tensor-core (split-bf16, tcgen05) and the FP64 (SIMT) paths.
+// tensor-core (split bf16 or fp16 planes, tcgen05) and the FP64 (SIMT) paths.
 #pragma once
 #include "common.cuh"
 
@@ -9,8 +9,9 @@ namespace sedacs {
 //   C = alpha * A * B^T + beta * I + g1 * C1 + g2 * C2      (generic mode)
 // (B^T: B is read by rows, so for the symmetric operands of the method B^T = B; C1, C2 are
 // masters added in the epilogue, so a product with I + E is formed as C + C E exactly).  Offsets are bytes from
-// the arena base.  For the tensor-core path A and B are blocked split-bf16 planes and the
-// master output is fp32 row-major; for the FP64 path every matrix is fp64 row-major.
+// the arena base.  For the tensor-core path A and B are blocked split planes (bf16, or the
+// two-plane fp16 format) and the master output is fp32 row-major; for the FP64 path every
+// matrix is fp64 row-major.
 struct GemmMat {
   long long a_off, b_off;        // operand 0-th plane (tensor path) or matrix (fp64 path)
   long long a_plane, b_plane;    // bytes between planes
@@ -30,9 +31,10 @@ struct GemmMat {
   int a_from_sp2;
   int c_from_sp2;                // generic mode: C1 taken from the SP2 result buffer
   int sym_out;                   // result is symmetric: only tiles tn >= tm are run, each
-                                 // off-diagonal tile is also written transposed
-  int x_planes;                  // SP2 mode, three planes: the epilogue takes X from A's planes
-                                 // (hi + mid + lo reproduces the fp32 value exactly), no master
+                                 // off-diagonal tile is also written transposed (not in the
+                                 // two-plane fp16 SP2 step, which keeps the upper tiles only)
+  int x_planes;                  // SP2 mode, three bf16 or two fp16 planes: the epilogue takes X
+                                 // from A's planes (the value the MMAs see), no master
   int c_planes;                  // generic mode: C1 is three blocked bf16 planes at c_off
   long long c_plane;             // bytes between the planes of C1
 };

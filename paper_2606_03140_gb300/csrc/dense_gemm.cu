@@ -39,7 +39,7 @@ __device__ __forceinline__ void store_planes8(uint8_t* arena, long long base, lo
 }
 
 // ------------------------------------------------------------------------------------------
-// Persistent, warp-specialised split-bf16 GEMM.  One CTA per SM walks the work list (128x128
+// Persistent, warp-specialised split-plane GEMM.  One CTA per SM walks the work list (128x128
 // output tiles) with a stride of gridDim.x.  The producer warp (one lane) streams the operand
 // blocks of consecutive tiles through the stage ring without pausing at tile boundaries; the
 // MMA warp (one lane) issues the MMAs of a tile once the epilogue has drained the previous
