@@ -37,7 +37,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", type=int, default=1)
+    ap.add_argument("--precision", type=int, default=1, choices=[0, 1, 2, 3, 4],
+                    help="0 plain FP64; 1 FP32-class (SP2 squares in two fp16 planes, other products "
+                         "three-way bf16); 4 FP32-class three-way bf16 throughout; 2, 3 diagnostics")
     ap.add_argument("--workload", default="water9000")
     ap.add_argument("--dt", type=float, default=0.25)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -80,7 +80,9 @@ def _energy_stats(E, n_atoms: int, dt_fs: float, skip: int):
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--workload", default="water9000")
-    ap.add_argument("--precision", type=int, default=1)
+    ap.add_argument("--precision", type=int, default=1, choices=[0, 1, 2, 3, 4],
+                    help="0 plain FP64; 1 FP32-class (SP2 squares in two fp16 planes, other products "
+                         "three-way bf16); 4 FP32-class three-way bf16 throughout; 2, 3 diagnostics")
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--dt", type=float, default=0.25, help="fs")
     ap.add_argument("--kernel", type=int, default=0, choices=[0, 1, 2])
