@@ -92,6 +92,8 @@ def kernel_sha1() -> str:
         with open(os.path.join(ROOT, "paper_2606_03140_gb300", "csrc", f), encoding="utf-8") as fh:
             h.update(strip_comments(fh.read()).encode())
     return h.hexdigest()
+
+
 UNIT = "atom-steps/s"
 
 
@@ -138,10 +140,16 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
+        return self.summarise(self.lines, self.t_mark)
+
+    @staticmethod
+    def summarise(lines, t_mark: float) -> dict:
+        """Median SM clock, maximum clock and the throttle reasons seen active, over the
+        (time, csv line) samples taken at or after t_mark."""
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for t, ln in self.lines:
-            if t < self.t_mark:
+        for t, ln in lines:
+            if t < t_mark:
                 continue
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
