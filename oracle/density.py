@@ -15,13 +15,14 @@ What is computed, in the paper's order:
 4. The Fermi operator D = [exp(beta (h~ - mu I)) + I]^(-1) (Eq. 2) through the
    eigen-decomposition of h~ (the paper allows direct diagonalisation, Sec. "Density
    Matrix Evaluation on Partitioned Graphs"); spin factor 2, closed shell.
-5. One chemical potential mu for the whole system with Tr[D S] = N_e (Eq. 2).  The
-   collected count N(mu) = 2 sum_i sum_k w_ik f(eps_ik - mu) (w_ik the core Mulliken
-   weight of state k of subgraph i) misses N_e at mid-gap by the graph truncation
-   error, so mu is read as the middle of the collected gap (``solve_mu``): the
-   states below it carry N_e to within half an electron.  At Te = 300 K and these
-   gaps the Fermi function is a step to machine precision for every state more than
-   0.03 Ha from mu.
+5. One chemical potential mu for the whole system with Tr[D S] = N_e (Eq. 2, with the
+   trace read as the collected count): N(mu) = 2 sum_i sum_k w_ik f(eps_ik - mu) = N_e,
+   w_ik the core Mulliken weight of state k of subgraph i, f the Fermi function at Te
+   (``solve_mu``, bisection).  The graph truncation leaves the T -> 0 count at mid-gap
+   off N_e; the finite-temperature rule absorbs that miss in the Fermi tails of the
+   states nearest to mu (for the water boxes: mu sits ~9 kT above the flat lone-pair
+   band).  ``t0_miss`` reports the T -> 0 count at mu minus N_e, ``in_gap_weight`` the
+   core weight of states within 0.05 Ha of mu.
 6. Collection of the core rows (Eq. 3 / SI Eq. A): D_c = 2 Z C f C^T Z and the
    energy-weighted W_c = 2 Z C (f eps) C^T Z, restricted to core orbitals.
 7. Net Mulliken charges dq_I = sum_{mu in I} sum_nu D_mu,nu S_nu,mu - Z_I
@@ -30,11 +31,15 @@ What is computed, in the paper's order:
    F = -[Tr(D dH[n]) - Tr(W dS) + (dq - n/2)^T dgamma n + dE_rep] at fixed n (Eq. NEQ).
 8. Atom-condensed density graph G^D_IJ = max over the (I,J) block of |D| (Sec.
    "Dynamic Graph Adaption").
+9. Electronic entropy of the collected Fermi occupations,
+   S_e = -2 k_B sum_ik w_ik [f ln f + (1 - f) ln(1 - f)]; the free-energy term -T S_e is
+   reported beside the shadow energy (``ts_entropy``), not inside its ``total``.
 
 Pinned by tests: Z s Z = I; idempotency D S D = 2 D and Tr(D S) = N_e in the full
 (single partition) limit; subgraph result equal to full diagonalisation when every
-halo is the whole system; charge neutrality; mu inside the gap on a brute-force
-grid; forces equal to a central finite difference of U in the full limit.
+halo is the whole system; charge neutrality; mu against a brute-force scan of the
+collected count on a truncated graph; G^D against an explicit loop over the full core
+rows; forces equal to a central finite difference of U in the full limit.
 """
 from __future__ import annotations
 
@@ -120,6 +125,9 @@ class DensityResult:
     subs: list = field(default_factory=list)
     gd: tuple | None = None      # (ptr, col, val) atom-condensed density graph
     in_gap_weight: float = 0.0   # sum of core weights of states within +-0.05 Ha of mu
+    t0_miss: float = 0.0         # T -> 0 collected count at mu minus N_e (graph truncation)
+    entropy: float = 0.0         # S_e / k_B of the collected occupations (spin factor 2)
+    Te: float = 300.0
 
 
 def subgraph_setup(atoms, n_core, R, species, box, model, V):
@@ -141,21 +149,26 @@ def subgraph_setup(atoms, n_core, R, species, box, model, V):
                             bounds=gershgorin(Ht))
 
 
-def solve_mu_bisection(eps_list, w_list, n_e: float, beta: float) -> float:
-    """Literal bisection on N(mu) = 2 sum w f(eps - mu) = N_e at inverse temperature beta.
+def collected_count(eps_list, w_list, mu: float, beta: float) -> float:
+    """N(mu) = 2 sum_i sum_k w_ik f(eps_ik - mu) at inverse temperature beta (Eq. 2)."""
+    return 2.0 * sum(float(np.dot(w, fermi(np.asarray(e) - mu, beta))) for e, w in zip(eps_list, w_list))
 
-    Start [min eps - 1, max eps + 1]; stop when |N - N_e| < 1e-10 or the interval is
-    narrower than 1e-14 Ha; return the midpoint.  Kept as a diagnostic: with the
-    graph truncation the collected count at mid-gap misses N_e by a small amount and
-    this rule then pins mu onto a band edge.
+
+def solve_mu(eps_list, w_list, n_e: float, beta: float) -> float:
+    """Global chemical potential of Eq. 2: bisection on N(mu) = N_e.
+
+    N(mu) is non-decreasing in mu (core weights of the collected states are positive up
+    to the truncation; the test keeps the bracket).  Start [min eps - 1, max eps + 1];
+    stop when |N - N_e| < 1e-11 or the interval is narrower than 1e-15 Ha; return the
+    midpoint.
     """
     lo = min(float(np.min(e)) for e in eps_list) - 1.0
     hi = max(float(np.max(e)) for e in eps_list) + 1.0
     mid = 0.5 * (lo + hi)
-    for _ in range(200):
+    for _ in range(400):
         mid = 0.5 * (lo + hi)
-        nel = 2.0 * sum(float(np.dot(w, fermi(e - mid, beta))) for e, w in zip(eps_list, w_list))
-        if abs(nel - n_e) < 1e-10 or hi - lo < 1e-14:
+        nel = collected_count(eps_list, w_list, mid, beta)
+        if abs(nel - n_e) < 1e-11 or hi - lo < 1e-15:
             break
         if nel < n_e:
             lo = mid
@@ -164,47 +177,23 @@ def solve_mu_bisection(eps_list, w_list, n_e: float, beta: float) -> float:
     return mid
 
 
-def count_window(n_e: float) -> float:
-    """Half-width kappa of the electron-count window around N_e used to locate the gap edges.
-
-    The graph truncation leaves the collected count at mid-gap off N_e by an amount that
-    grows with the system (about 2.5e-5 e per atom in the water boxes); kappa = 1/2 + 1e-4 N_e
-    keeps that excess inside the window while staying far below the weight of a band."""
-    return 0.5 + 1e-4 * n_e
-
-
-def solve_mu(eps_list, w_list, n_e: float, kappa: float | None = None) -> tuple[float, float, float]:
-    """Global chemical potential at the middle of the collected gap (T -> 0 reading of Eq. 2).
-
-    The T -> 0 count N0(mu) = 2 sum_ik w_ik theta(mu - eps_ik) is a staircase in mu.
-    The highest occupied level eps_H is the state whose inclusion first brings the
-    count to >= N_e - kappa; the lowest unoccupied level eps_L is the first state whose
-    inclusion takes it above N_e + kappa (kappa = ``count_window(N_e)``).
-    mu = (eps_H + eps_L) / 2.  States between them carry less than 2 kappa electrons in
-    total (in-gap halo states).
-    Returns (mu, eps_H, eps_L).
-    """
-    if kappa is None:
-        kappa = count_window(n_e)
-    e = np.concatenate([np.asarray(x, dtype=np.float64) for x in eps_list])
-    w = np.concatenate([np.asarray(x, dtype=np.float64) for x in w_list])
-    order = np.argsort(e, kind="stable")
-    e, w = e[order], w[order]
-    c = 2.0 * np.cumsum(w)
-    ih = np.nonzero(c >= n_e - kappa)[0]
-    il = np.nonzero(c > n_e + kappa)[0]
-    e_h = float(e[ih[0]]) if ih.shape[0] else float(e[-1])
-    e_l = float(e[il[0]]) if il.shape[0] else float(e[-1]) + 1.0
-    return 0.5 * (e_h + e_l), e_h, e_l
+def entropy_density(f: np.ndarray) -> np.ndarray:
+    """-[f ln f + (1 - f) ln(1 - f)] with 0 ln 0 = 0."""
+    f = np.asarray(f, dtype=np.float64)
+    out = np.zeros_like(f)
+    m = (f > 0.0) & (f < 1.0)
+    g = f[m]
+    out[m] = -(g * np.log(g) + (1.0 - g) * np.log1p(-g))
+    return out
 
 
 def density(R, species, box, model, n, cores, halo_lists, Te: float = 300.0, mu: float | None = None,
             mode: str = "fermi", sp2_tol: float = 1e-9, V: np.ndarray | None = None) -> DensityResult:
     """Graph-partitioned density at trial charges n: charges, band energy, mu, core rows of D and W.
 
-    mode "fermi": Fermi occupations at Te (default); "sp2": the mu-branch SP2 polynomial
-    of ``sp2_mu_occupations`` on every eigenvalue (same function as the GPU recursion),
-    with Gershgorin bounds of h~.
+    mode "fermi": Fermi occupations at Te (default), mu from Eq. 2 (``solve_mu``) unless
+    given; "sp2": the mu-branch SP2 polynomial of ``sp2_mu_occupations`` on every eigenvalue
+    (same function as the T -> 0 GPU recursion), with Gershgorin bounds of h~, at a given mu.
     """
     R = np.asarray(R, dtype=np.float64)
     species = np.asarray(species)
@@ -214,8 +203,12 @@ def density(R, species, box, model, n, cores, halo_lists, Te: float = 300.0, mu:
     for core, halo in zip(cores, halo_lists):
         atoms = np.concatenate([core, halo]).astype(np.int64)
         subs.append(subgraph_setup(atoms, len(core), R, species, box, model, V))
-    beta = 1.0 / (KB_HA * Te)
     n_e = float(np.sum(np.asarray(model.z_val)[species]))
+    if mode == "sp2" and mu is None:
+        raise ValueError("the T -> 0 SP2 occupations take a given chemical potential")
+    if mode == "fermi" and not Te > 0.0:
+        raise ValueError("Fermi occupations need Te > 0")
+    beta = 1.0 / (KB_HA * Te) if Te > 0.0 else math.inf
 
     def occ_for(mu_):
         out = []
@@ -232,12 +225,14 @@ def density(R, species, box, model, n, cores, halo_lists, Te: float = 300.0, mu:
         return out
 
     if mu is None:
-        mu, _, _ = solve_mu([sg.eps for sg in subs], [sg.w for sg in subs], n_e)
+        mu = solve_mu([sg.eps for sg in subs], [sg.w for sg in subs], n_e, beta)
     occs = occ_for(mu)
     q = np.zeros(R.shape[0])
     e_band = 0.0
     nel = 0.0
     gap_w = 0.0
+    t0 = 0.0
+    ent = 0.0
     z = np.asarray(model.z_val)
     gd_rows = {}
     for sg, f in zip(subs, occs):
@@ -258,6 +253,8 @@ def density(R, species, box, model, n, cores, halo_lists, Te: float = 300.0, mu:
             vals = np.array([np.max(row[:, sg.off[b]:sg.off[b + 1]]) for b in range(len(sg.atoms))])
             gd_rows[I] = (sg.atoms.astype(np.int32), vals)
         gap_w += float(np.sum(sg.w[np.abs(sg.eps - mu) < 0.05]))
+        t0 += 2.0 * float(np.sum(sg.w[sg.eps < mu]))
+        ent += 2.0 * float(np.dot(sg.w, entropy_density(f)))
     N = R.shape[0]
     ptr = np.zeros(N + 1, dtype=np.int64)
     cols, vals = [], []
@@ -269,7 +266,7 @@ def density(R, species, box, model, n, cores, halo_lists, Te: float = 300.0, mu:
         ptr[I + 1] = ptr[I] + len(c)
     gd = (ptr, np.concatenate(cols).astype(np.int32), np.concatenate(vals))
     return DensityResult(mu=float(mu), q=q, e_band=e_band, n_electrons=nel, V=V, subs=subs, gd=gd,
-                         in_gap_weight=gap_w)
+                         in_gap_weight=gap_w, t0_miss=t0 - n_e, entropy=ent, Te=Te)
 
 
 def repulsion(R, species, box, model, with_grad: bool = False):
@@ -302,11 +299,14 @@ def repulsion(R, species, box, model, with_grad: bool = False):
 
 
 def shadow_energy(res: DensityResult, n, R, species, box, model) -> dict:
-    """U = Tr[D H0] + 1/2 (2 dq - n)^T gamma n + E_rep  (Eq. "Shadow_Energy" with SCC-DFTB)."""
+    """U = Tr[D H0] + 1/2 (2 dq - n)^T gamma n + E_rep  (Eq. "Shadow_Energy" with SCC-DFTB).
+
+    ``ts_entropy`` = -T S_e of the collected Fermi occupations, the electronic free-energy
+    term at finite Te; it is reported beside ``total`` and not added to it."""
     e_coul = float(np.dot(res.q - 0.5 * np.asarray(n), res.V))
     e_rep = repulsion(R, species, box, model)
     return {"band": res.e_band, "coulomb": e_coul, "repulsion": e_rep,
-            "total": res.e_band + e_coul + e_rep}
+            "total": res.e_band + e_coul + e_rep, "ts_entropy": -KB_HA * res.Te * res.entropy}
 
 
 def forces(res: DensityResult, n, R, species, box, model) -> np.ndarray:

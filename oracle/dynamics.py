@@ -8,8 +8,10 @@ Test infrastructure only (see ``oracle/__init__``).
   the cores stay fixed.  Converged when max |q - n| <= tol.
 * Kernel-accelerated quasi-Newton SCC (SI Sec. C): n <- n - (K0 J)^-1 K0 (q - n) with
   the rank-m approximation of (K0 J)^-1.
-* Response (SI Sec. B, Eq. "dfdv"): J v = dq/dn v - v at fixed mu, from first-order
-  perturbation theory on every subgraph (sum over states, T -> 0 in the gap).
+* Response (SI Sec. B, Eq. "dfdv"): J v = dq/dn v - v, from first-order perturbation
+  theory on every subgraph at the Fermi occupations of Te (sum over state pairs with the
+  divided differences (f_j - f_k)/(eps_j - eps_k), -beta f (1 - f) for equal levels), and
+  with the canonical shift of mu that keeps the collected electron count fixed.
 * Low-rank kernel (SI Sec. B, Eqs. "PreKernel", "LowRankEEOM"): v_j an orthonormalised
   preconditioned Krylov basis starting at K0 f, f_vj = K0 J v_j, O_ij = f_vi . f_vj,
   M = O^-1, K f ~ sum_ij v_i M_ij f_vj^T K0 f; stops at rank m or when the relative
@@ -21,7 +23,8 @@ Test infrastructure only (see ``oracle/__init__``).
 
 Pinned by tests: the SCC fixed point is independent of the mixer; full-rank Krylov equals
 the dense J^-1 (finite-difference Jacobian) on a tiny box; responses equal a central finite
-difference; energy fluctuation of the dynamics scales with dt^2 and shows no drift.
+difference at fixed mu and, canonical, with mu solved again; energy fluctuation of the
+dynamics scales with dt^2 and shows no drift.
 """
 from __future__ import annotations
 
@@ -29,6 +32,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
+from . import KB_HA
 from . import density as dn
 from . import ewald, graph
 
@@ -84,27 +88,44 @@ def scc(R, species, box, model, gp: GraphParams, n0=None, max_iter: int = 300, t
     return n, res, it, hist
 
 
-def charge_response(res: dn.DensityResult, v, R, species, box, model):
-    """dq/dn v at fixed mu and fixed subgraphs (first-order perturbation, sum over states)."""
+def divided_differences(eps: np.ndarray, f: np.ndarray, beta: float) -> np.ndarray:
+    """F[j, k] = (f_j - f_k) / (eps_j - eps_k), and -beta f_j (1 - f_j) where the levels coincide."""
+    de = eps[:, None] - eps[None, :]
+    df = f[:, None] - f[None, :]
+    close = np.abs(de) < 1e-12
+    safe = np.where(close, 1.0, de)
+    deriv = -beta * 0.5 * ((f * (1.0 - f))[:, None] + (f * (1.0 - f))[None, :])
+    return np.where(close, deriv, df / safe)
+
+
+def charge_response(res: dn.DensityResult, v, R, species, box, model, canonical: bool = True):
+    """dq/dn v on fixed subgraphs (first-order perturbation, sum over state pairs).
+
+    dV = gamma v, dh = 1/2 (s dV + dV s) on every subgraph, dh~ = Z dh Z; in the eigenbasis
+    dP_jk = F[j, k] (x_j^T dh~ x_k) with the divided differences of the Fermi function at
+    Te; dD_c = 2 Z_c dP Z.  canonical: add dmu * dq/dmu with dq/dmu from
+    dP/dmu = X diag(beta f (1 - f)) X^T, dmu chosen so that sum dq = 0 (fixed electron count)."""
     dV = ewald.coulomb_potential(R, species, model.hubbard_u, box, v)
+    beta = 1.0 / (KB_HA * res.Te)
     dq = np.zeros(R.shape[0])
+    dqmu = np.zeros(R.shape[0])
     for sg in res.subs:
         vorb = np.repeat(dV[sg.atoms], sg.norb)
         dh = 0.5 * sg.S * (vorb[:, None] + vorb[None, :])
         X = sg.X                                   # eigenvectors of h~ (C = Z X)
         dht = X.T @ (sg.Z @ dh @ sg.Z) @ X         # perturbation in the eigenbasis
-        occ = sg.occ > 0.5
-        e = sg.eps
-        denom = e[occ][None, :] - e[~occ][:, None]      # [virt, occ]  eps_a - eps_i
-        coef = dht[np.ix_(~occ, occ)] / denom            # (x_i^T dh x_a) / (eps_a - eps_i)
-        Xo, Xv = X[:, occ], X[:, ~occ]
-        dP = Xv @ coef @ Xo.T
-        dP = dP + dP.T
-        dD = 2.0 * sg.Z @ dP @ sg.Z
+        dP = X @ (divided_differences(sg.eps, sg.occ, beta) * dht) @ X.T
+        dPmu = (X * (beta * sg.occ * (1.0 - sg.occ))[None, :]) @ X.T
         nco = int(sg.off[sg.n_core])
-        pop = np.sum(dD[:nco, :] * sg.S[:, :nco].T, axis=1)
-        for a in range(sg.n_core):
-            dq[int(sg.atoms[a])] = float(np.sum(pop[sg.off[a]:sg.off[a + 1]]))
+        for P_, out in ((dP, dq), (dPmu, dqmu)):
+            dD = 2.0 * sg.Z @ P_ @ sg.Z
+            pop = np.sum(dD[:nco, :] * sg.S[:, :nco].T, axis=1)
+            for a in range(sg.n_core):
+                out[int(sg.atoms[a])] = float(np.sum(pop[sg.off[a]:sg.off[a + 1]]))
+    if canonical:
+        s_mu = float(np.sum(dqmu))
+        if s_mu > 0.0:
+            dq = dq - (float(np.sum(dq)) / s_mu) * dqmu
     return dq
 
 

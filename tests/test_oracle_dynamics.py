@@ -30,11 +30,18 @@ def test_charge_response_equals_finite_difference(tiny):
     _, _, hal = dyn.graph_and_halos(s.R, s.box, gp, cores, None)
     r0 = dn.density(s.R, s.species, s.box, m, n, cores, hal)
     v = I.random_charges(12, 5, 1.0)
-    dq = dyn.charge_response(r0, v, s.R, s.species, s.box, m)
     e = 1e-4
+    # at fixed mu
+    dq = dyn.charge_response(r0, v, s.R, s.species, s.box, m, canonical=False)
     qp = dn.density(s.R, s.species, s.box, m, n + e * v, cores, hal, mu=r0.mu).q
     qm = dn.density(s.R, s.species, s.box, m, n - e * v, cores, hal, mu=r0.mu).q
     assert np.max(np.abs(dq - (qp - qm) / (2 * e))) < 1e-7
+    # canonical: mu solved again from Eq. 2 on both sides of the difference
+    dqc = dyn.charge_response(r0, v, s.R, s.species, s.box, m)
+    qp = dn.density(s.R, s.species, s.box, m, n + e * v, cores, hal).q
+    qm = dn.density(s.R, s.species, s.box, m, n - e * v, cores, hal).q
+    assert np.max(np.abs(dqc - (qp - qm) / (2 * e))) < 1e-7
+    assert abs(dqc.sum()) < 1e-10
 
 
 def test_full_rank_krylov_equals_dense_inverse_jacobian(tiny):
@@ -47,8 +54,8 @@ def test_full_rank_krylov_equals_dense_inverse_jacobian(tiny):
     e = 1e-5
     for j in range(12):
         ej = np.zeros(12); ej[j] = e
-        qp = dn.density(s.R, s.species, s.box, m, n + ej, cores, hal, mu=r0.mu).q
-        qm = dn.density(s.R, s.species, s.box, m, n - ej, cores, hal, mu=r0.mu).q
+        qp = dn.density(s.R, s.species, s.box, m, n + ej, cores, hal).q
+        qm = dn.density(s.R, s.species, s.box, m, n - ej, cores, hal).q
         J[:, j] = (qp - qm) / (2 * e)
     J -= np.eye(12)
     f = r0.q - n
@@ -56,7 +63,6 @@ def test_full_rank_krylov_equals_dense_inverse_jacobian(tiny):
     assert np.max(np.abs(u - np.linalg.solve(J, f))) < 1e-6 * np.max(np.abs(np.linalg.solve(J, f)))
 
 
-@pytest.mark.slow
 def test_xlbomd_energy_fluctuation_scales_dt2(tiny):
     """Sec. "Dynamic Graph Adaption": amplitude ~x4 per doubling of dt, no drift."""
     s, m, gp = tiny

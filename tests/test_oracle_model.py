@@ -119,3 +119,50 @@ def test_ewald_gradient_finite_difference():
         fd = (a @ ewald.coulomb_potential(Rp, s.species, m.hubbard_u, s.box, n)
               - a @ ewald.coulomb_potential(Rm, s.species, m.hubbard_u, s.box, n)) / (2 * h)
         assert abs(fd - G[A, c]) < 1e-8
+
+
+def _dimer_model():
+    # distinct constants per bond type and, for sp sigma, per ordered element pair (s on i, p on j),
+    # so that a swapped pp sigma / pp pi, a swapped s-on-i / s-on-j constant or a flipped sign all show
+    v0 = [[[0.0] * 4 for _ in range(3)] for _ in range(3)]
+    for i in range(3):
+        for j in range(3):
+            v0[i][j] = [-1.1 - 0.05 * (i + j), 1.3 + 0.2 * i + 0.05 * j, 1.7 + 0.03 * (i + j), -0.45 - 0.02 * (i + j)]
+    return I.SKModel(v0=tuple(tuple(tuple(x) for x in row) for row in v0))
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_aligned_dimer_closed_form_blocks(axis):
+    """Slater-Koster table for a pair on a Cartesian axis (Slater & Koster 1954): with the
+    bond along +e_a (atom 1 - atom 0), H[s0, s1] = V_ss, H[s0, p_a1] = +V_sp(s on 0),
+    H[p_a0, s1] = -V_sp(s on 1), H[p_a0, p_a1] = V_pp sigma, H[p_b0, p_b1] = V_pp pi (b != a),
+    every other entry of the block zero; S the same with the overlap scale."""
+    m = _dimer_model()
+    r = 1.9
+    sp = np.array([2, 1])          # O at R0, C at R1
+    R = np.array([[7.0, 7.0, 7.0], [7.0, 7.0, 7.0]])
+    R[1, axis] += r
+    H, S, norb, off = sk.hs_blocks_for_atoms(np.arange(2), R, sp, np.array([30.0] * 3), m)
+    g = math.exp(-r / m.decay)
+    for M, scale in ((H, 1.0), (S, m.overlap_scale)):
+        v = lambda a, b, X: scale * m.v0[a][b][X] * g
+        blk = M[0:4, 4:8]
+        ref = np.zeros((4, 4))
+        ref[0, 0] = v(2, 1, 0)
+        ref[0, 1 + axis] = v(2, 1, 1)          # s on O (atom 0), p on C
+        ref[1 + axis, 0] = -v(1, 2, 1)         # s on C (atom 1), p on O
+        for b in range(3):
+            ref[1 + b, 1 + b] = v(2, 1, 2) if b == axis else v(2, 1, 3)
+        assert np.max(np.abs(blk - ref)) < 1e-14
+        assert np.max(np.abs(M[4:8, 0:4] - ref.T)) < 1e-14
+    # on-site diagonal and unit overlap diagonal
+    assert np.allclose(np.diag(H), [m.eps_s[2]] + [m.eps_p[2]] * 3 + [m.eps_s[1]] + [m.eps_p[1]] * 3, atol=0)
+    assert np.allclose(np.diag(S), 1.0, atol=0)
+    # reversing the bond direction flips only the s-p entries
+    R2 = R.copy()
+    R2[1, axis] -= 2 * r
+    H2, _, _, _ = sk.hs_blocks_for_atoms(np.arange(2), R2, sp, np.array([30.0] * 3), m)
+    flip = np.ones((4, 4))
+    flip[0, 1:] = -1.0
+    flip[1:, 0] = -1.0
+    assert np.max(np.abs(H2[0:4, 4:8] - flip * H[0:4, 4:8])) < 1e-14
