@@ -43,7 +43,7 @@ typedef enum {
   SEDACS_ENOCONV = 4,    /* SCC did not converge within max_iter */
   SEDACS_ETIMEOUT = 5,   /* a bounded device wait gave up (kernel returned early) */
   SEDACS_ENUMERIC = 6,   /* NaN / Inf found in a result */
-  SEDACS_EPRECISION = 7, /* chemical potential could not be placed in a gap */
+  SEDACS_EPRECISION = 7, /* the chemical potential of Eq. 2 was not found (no bracket / no convergence) */
   SEDACS_ECAPACITY = 8   /* a fixed-size device buffer was too small */
 } sedacs_status;
 
@@ -61,14 +61,14 @@ typedef struct {
 } sedacs_model;
 
 /* Run parameters.  precision: 0 = plain FP64 on the CUDA cores; 1 = FP32-class on tcgen05
- * tensor cores with FP32 accumulation: the SP2 squares in the dual half-precision format of
- * Finkelstein et al. (2021), x = hi + 2^-11 lo in two fp16 planes (22 significant bits; three
- * products hi*hi + hi*lo + lo*hi), every other dense product with three-way bf16 splitting
- * (24 bits, six products); 4 = FP32-class with three-way bf16 splitting in every product,
- * the SP2 squares included; 2 = mixed BF16 (SP2 squares with two-way bf16 splitting; S^-1/2
- * and the core-row back-transform three-way); 3 = pure bf16 SP2 squares (diagnostic).  In 1-4
- * the Ewald sums run in FP32 with FP64 reductions; electron counts, energies and forces are
- * summed in FP64.
+ * tensor cores with FP32 accumulation: the products of the Fermi-operator recursion (and the
+ * T -> 0 SP2 squares) in the dual half-precision format of Finkelstein et al. (2021),
+ * x = hi + 2^-11 lo in two fp16 planes (22 significant bits; three products hi*hi + hi*lo +
+ * lo*hi), every other dense product with three-way bf16 splitting (24 bits, six products);
+ * 4 = FP32-class with three-way bf16 splitting in every product; 2 = mixed BF16 (recursion
+ * products with two-way bf16 splitting; S^-1/2 and the core-row back-transform three-way);
+ * 3 = pure bf16 recursion products (diagnostic).  In 1-4 the Ewald sums run in FP32 with FP64
+ * reductions; electron counts, energies and forces are summed in FP64.
  * kernel: 0 = K0 = -c_k0 I (SI Sec. B); 1 = preconditioned rank-m Krylov (SI Sec. B);
  * 2 = learned preconditioner (message-passing network, see sedacs_gnn_*), judged against 1. */
 typedef struct {
@@ -91,11 +91,22 @@ typedef struct {
   double ewald_tol;     /* relative accuracy of the Ewald sums (0: 1e-12 FP64, 1e-8 mixed) */
   int32_t judge_every;  /* kernel 2: every judge_every MD steps compare with the Krylov kernel */
   double judge_tol;     /* kernel 2: relative error above which the Krylov kernel takes over */
+  double Te;            /* electronic temperature, K.  Te > 0: the Fermi operator of Eq. 2 at
+                           beta = 1 / (k_B Te) by the recursive tanh-doubling expansion, and mu
+                           from the collected count (Eq. 2: Tr[D S] = N_e).  Te = 0: the T -> 0
+                           mu-branch SP2 recursion at a chemical potential the caller gives. */
+  int32_t mu_given;     /* Te > 0: 1 = use the mu passed to the density calls as given (no Eq. 2 solve) */
+  double fermi_lin;     /* Te > 0: after a Fermi pass at mu0 the count is brought to N_e by the mu step
+                           dmu of its second-order expansion (D += beta dmu D_s + (beta dmu)^2 / 2 D_t,
+                           with dF/dmu = beta (F - F^2) and d2F/dmu2 = beta^2 (F - F^2)(I - 2F)) when
+                           |beta dmu| is at most this; otherwise another pass runs (0: 3e-2 in the
+                           FP32-class forms, 1.5e-3 in FP64) */
 } sedacs_params;
 
 /* Fill p with the defaults (r_graph 3.0, tau 1e-3, core_size 32, precision 1, kernel 0,
  * krylov_rank 4, krylov_tol 1e-2, c_k0 0.5, scc_tol 1e-8, scc_alpha 0.2, sp2_tol 0,
- * sp2_kmax 60, ns_iters 0, ewald_tol 0, judge_every 20, judge_tol 0.1). */
+ * sp2_kmax 60, ns_iters 0, ewald_tol 0, judge_every 20, judge_tol 0.1, Te 300, mu_given 0,
+ * fermi_lin 0). */
 void sedacs_default_params(sedacs_params* p);
 
 /* Create a context for N atoms of the given species in an orthorhombic periodic box
@@ -146,12 +157,15 @@ sedacs_status sedacs_parts_get(sedacs_ctx* ctx, int64_t* sub_ptr, int32_t* sub_a
 sedacs_status sedacs_coulomb_potential(sedacs_ctx* ctx, const double* R, const double* b, double* V);
 
 /* ---- a4-a9: graph-partitioned density (Eqs. 1-3) at trial charges n for the current
- * graph and subgraphs.  Per subgraph: gather h = H0 + 1/2 (S V + V S) and s, Z = s^-1/2
- * (Newton-Schulz), h~ = Z h Z, the mu-branch SP2 recursion for the T -> 0 Fermi operator,
- * core rows D_c = 2 Z_c X Z and W_c = 2 Z_c X h~ Z; then Mulliken charges, band energy and
- * the density graph.  mu: in = chemical potential (Hartree), used as given, or NaN to place
- * it at the middle of the collected gap; out = the value used.  q [N] out, e_band out (Hartree),
- * sp2_iters [n_parts] out (nullable). */
+ * graph and subgraphs.  Per subgraph: gather h = H0 + 1/2 (S V + V S) and s, Z = s^-1/2,
+ * h~ = Z h Z, the Fermi operator X = [exp(beta (h~ - mu I)) + I]^-1 (Eq. 2; Te > 0: recursive
+ * tanh-doubling expansion on the tensor cores; Te = 0: the mu-branch SP2 recursion), core
+ * rows D_c = 2 Z_c X Z and W_c = 2 Z_c X h~ Z; then Mulliken charges, band energy and the
+ * density graph.  mu (Hartree): Te > 0: in = starting guess of the Eq. 2 solve (NaN: none),
+ * out = the chemical potential whose collected count Tr[D S] equals N_e (with mu_given = 1:
+ * used as given); Te = 0: used as given (NaN -> SEDACS_EINVAL).  No mu in the search bracket
+ * -> SEDACS_EPRECISION.  q [N] out, e_band out (Hartree), sp2_iters [n_parts] out (nullable:
+ * SP2 steps when Te = 0, else the tanh doublings of the last pass in every entry). */
 sedacs_status sedacs_subgraph_density(sedacs_ctx* ctx, const double* R, const double* n, double* mu, double* q,
                                       double* e_band, int32_t* sp2_iters);
 /* Energies of the last density call: e[0] band Tr[D H0], e[1] Coulomb 1/2 (2q - n)^T gamma n,
@@ -167,8 +181,11 @@ sedacs_status sedacs_density_graph_get(sedacs_ctx* ctx, int64_t* ptr, int32_t* c
 sedacs_status sedacs_subgraph_matrix(sedacs_ctx* ctx, int32_t part, int32_t which, double* out, int32_t* n,
                                      int32_t* n_core_orb);
 
-/* ---- a11: charge response dq/dn v at fixed mu (SI Sec. B, Eq. "dfdv"), by first-order
- * perturbation of the SP2 recursion on every subgraph, at the state of the last density call. */
+/* ---- a11: charge response dq/dn v (SI Sec. B, Eq. "dfdv") on the subgraphs of the last
+ * density call.  Te > 0: canonical (mu moves so that the collected count stays N_e), by a
+ * central difference of two density passes at n +- eps v (eps max|v| = 1e-3 e in the FP32-class
+ * forms, 1e-4 e in FP64); the arena's h and h~ then hold the last perturbed pass.  Te = 0: at
+ * fixed mu by first-order perturbation of the SP2 recursion. */
 sedacs_status sedacs_charge_response(sedacs_ctx* ctx, const double* v, double* dq);
 /* Kernel action u ~ K f = J^-1 f (SI Sec. B): K0 = -c I (kernel 0) or the preconditioned
  * rank-m Krylov approximation (kernel 1); *rank receives the rank used. */
@@ -177,9 +194,8 @@ sedacs_status sedacs_kernel_apply(sedacs_ctx* ctx, const double* f, double* u, i
 /* ---- a12: self-consistent charges (Sec. "Determining the Subgraphs", SI Sec. C).  Starting
  * from n (inout), iterates graph -> halos -> density -> n update until max |q - n| <= scc_tol
  * (linear mixing, or the kernel quasi-Newton step n <- n - K (q - n) once max |q - n| < 0.1 when
- * kernel = 1 (rank-m Krylov) or 2 (learned)).  When max |q - n| has not fallen by 10 % over 8
- * iterations, mu is placed in the middle of the current gap again (a kept mu can end up at a band
- * edge as the charges move the levels).
+ * kernel = 1 (rank-m Krylov) or 2 (learned)).  Every density call solves Eq. 2 for mu (Te > 0),
+ * starting from the previous iteration's value.
  * Cores must exist (sedacs_partition / sedacs_set_cores).  mu inout as in sedacs_subgraph_density. */
 sedacs_status sedacs_scc_step(sedacs_ctx* ctx, const double* R, double* n, int32_t max_iter, double* mu,
                               double* resid_max, int32_t* iters);
@@ -222,16 +238,23 @@ sedacs_status sedacs_gnn_train(sedacs_ctx* ctx, const double* X, const double* V
  * Krylov kernel during XL-BOMD with kernel 2. */
 sedacs_status sedacs_kernel_judge(sedacs_ctx* ctx, double* last_error, int32_t* fallbacks);
 
+/* Diagnostics of the last density call (Te > 0): info[0] collected electron count minus N_e
+ * after the mu solve, info[1] dN/dmu at the accepted pass (e/Ha), info[2] the linear mu step
+ * applied after it (Ha), info[3] Fermi-operator passes, info[4] tanh doublings per pass, then per
+ * pass the triple (mu, N_e - N(mu), dN/dmu) (zeros past the last pass).  n_info entries are written. */
+sedacs_status sedacs_density_info(sedacs_ctx* ctx, double* info, int32_t n_info);
+
 /* Wall time (ms, CUDA events on the context stream) of the phases of the last call:
- * t[0] graph+halos, t[1] Coulomb, t[2] gather, t[3] S^-1/2 + h~, t[4] SP2, t[5] collect,
+ * t[0] graph+halos, t[1] Coulomb, t[2] gather, t[3] S^-1/2 + h~, t[4] Fermi operator, t[5] collect,
  * t[6] forces, t[7] kernel + update.  Also the number of kernels launched since the last
  * sedacs_reset_counters() in *launches. */
 sedacs_status sedacs_phase_times(sedacs_ctx* ctx, double* t, int64_t* launches);
 sedacs_status sedacs_reset_counters(sedacs_ctx* ctx);
-/* Per-launch timing of the SP2 square kernel: on != 0 records CUDA events around every launch
- * on the context stream.  Returns the accumulated kernel time (ms), number of launches and
- * the algorithmic work of those launches (sum over subgraphs of steps * n^3 multiply-add
- * pairs, n the orbital count: one symmetric square per step) since the last reset. */
+/* Per-launch timing of the Fermi-operator products (Te > 0: the tanh-doubling recursion; Te = 0:
+ * the SP2 squares): on != 0 records CUDA events around every launch on the context stream.
+ * Returns the accumulated kernel time (ms), number of launches and the algorithmic work of
+ * those launches in flops, counting a symmetric product of two n x n matrices (upper triangle)
+ * as n^3 (n the orbital count of the subgraph), since the last reset. */
 sedacs_status sedacs_kernel_stats(sedacs_ctx* ctx, int32_t on, double* sp2_ms, int64_t* sp2_launches,
                                   double* sp2_flops);
 

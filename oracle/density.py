@@ -269,8 +269,11 @@ def density(R, species, box, model, n, cores, halo_lists, Te: float = 300.0, mu:
                          in_gap_weight=gap_w, t0_miss=t0 - n_e, entropy=ent, Te=Te)
 
 
-def repulsion(R, species, box, model, with_grad: bool = False):
-    """E_rep = 1/2 sum_{I,J,L}' A_IJ exp(-r/rep_decay) sw(r) over pairs within r_off (Ha, Ha/A)."""
+def repulsion(R, species, box, model, with_grad: bool = False, rows=None):
+    """E_rep = 1/2 sum_{I,J,L}' A_IJ exp(-r/rep_decay) sw(r) over pairs within r_off (Ha, Ha/A).
+
+    rows: sum only the terms of these atoms (energy: their halves of the pair terms; gradient:
+    their rows, which are complete)."""
     R = np.asarray(R, dtype=np.float64)
     A = model.rep_array()
     N = R.shape[0]
@@ -279,7 +282,7 @@ def repulsion(R, species, box, model, with_grad: bool = False):
     if not np.any(A):
         return (E, G) if with_grad else E
     shifts = sk.image_shifts(box, model.r_off)
-    for i in range(N):
+    for i in (range(N) if rows is None else [int(x) for x in rows]):
         d0 = R - R[i]
         d0 = d0 - box * np.round(d0 / box)
         for L in shifts:
@@ -309,8 +312,11 @@ def shadow_energy(res: DensityResult, n, R, species, box, model) -> dict:
             "total": res.e_band + e_coul + e_rep, "ts_entropy": -KB_HA * res.Te * res.entropy}
 
 
-def forces(res: DensityResult, n, R, species, box, model) -> np.ndarray:
+def forces(res: DensityResult, n, R, species, box, model, atoms=None) -> np.ndarray:
     """F = -[Tr(D dH[n]) - Tr(W dS) + (dq - n/2)^T dgamma n + dE_rep] in Ha/A at fixed n (Eq. NEQ).
+
+    atoms: compute only the rows of these atoms (every pair term that touches one of them is
+    kept, the others skipped; the other rows are returned as 0).
 
     The trace runs over the collected (core-row) D and W: for every subgraph, every
     core atom A and every subgraph atom B (each periodic image within r_off), the
@@ -321,20 +327,23 @@ def forces(res: DensityResult, n, R, species, box, model) -> np.ndarray:
     N = R.shape[0]
     dU = np.zeros((N, 3))
     V = res.V
+    want = np.ones(N, dtype=bool) if atoms is None else np.isin(np.arange(N), atoms)
     shifts = sk.image_shifts(box, model.r_off)
     for sg in res.subs:
-        atoms = sg.atoms
-        sp = species[atoms]
+        sg_atoms = sg.atoms
+        if not np.any(want[sg_atoms]):
+            continue
+        sp = species[sg_atoms]
         for a in range(sg.n_core):
-            A = int(atoms[a])
+            A = int(sg_atoms[a])
             ra = slice(sg.off[a], sg.off[a + 1])
             na = int(sg.norb[a])
-            d0 = R[atoms] - R[A]
+            d0 = R[sg_atoms] - R[A]
             d0 = d0 - box * np.round(d0 / box)
             for L in shifts:
                 d = d0 + L
                 r2 = np.sum(d * d, axis=1)
-                bs = np.nonzero((r2 < model.r_off**2) & (r2 > 0.0))[0]
+                bs = np.nonzero((r2 < model.r_off**2) & (r2 > 0.0) & (want[A] | want[sg_atoms]))[0]
                 if bs.shape[0] == 0:
                     continue
                 _, dH = sk.pair_blocks(model, np.full(bs.shape[0], sp[a]), sp[bs], d[bs], with_grad=True)
@@ -345,17 +354,21 @@ def forces(res: DensityResult, n, R, species, box, model) -> np.ndarray:
                     rb = slice(sg.off[b], sg.off[b + 1])
                     Dblk = sg.D_rows[ra, rb]
                     Wblk = sg.W_rows[ra, rb]
-                    vab = 0.5 * (V[A] + V[int(atoms[b])])
+                    vab = 0.5 * (V[A] + V[int(sg_atoms[b])])
                     g = np.einsum("mn,cmn->c", Dblk, dH[p, :, :na, :nb]) \
                         + vab * np.einsum("mn,cmn->c", Dblk, dS[p, :, :na, :nb]) \
                         - np.einsum("mn,cmn->c", Wblk, dS[p, :, :na, :nb])
                     dU[A] -= g
-                    dU[int(atoms[b])] += g
+                    dU[int(sg_atoms[b])] += g
     n = np.asarray(n, dtype=np.float64)
-    dU += ewald.coulomb_gradient(R, species, model.hubbard_u, box, res.q - 0.5 * n, n)
-    _, grep = repulsion(R, species, box, model, with_grad=True)
+    rows = None if atoms is None else np.asarray(atoms, dtype=np.int64)
+    dU += ewald.coulomb_gradient(R, species, model.hubbard_u, box, res.q - 0.5 * n, n, rows=rows)
+    _, grep = repulsion(R, species, box, model, with_grad=True, rows=rows)
     dU += grep
-    return -dU
+    out = -dU
+    if atoms is not None:
+        out[~want] = 0.0
+    return out
 
 
 def full_partition(N: int):

@@ -66,8 +66,10 @@ def _a_matrix(species_i, species_j, hubbard_u):
     return 1.0 / np.sqrt(2.0 * (sig_i[:, None] ** 2 + sig_j[None, :] ** 2))
 
 
-def coulomb_potential(R_A, species, hubbard_u, box_A, b, eta=None, rc_bohr=None, chunk=256):
-    """V = gamma @ b (b shape [N] or [N, m]); Hartree per unit charge.  Plain Ewald sums."""
+def coulomb_potential(R_A, species, hubbard_u, box_A, b, eta=None, rc_bohr=None, chunk=256, rows=None):
+    """V = gamma @ b (b shape [N] or [N, m]); Hartree per unit charge.  Plain Ewald sums.
+
+    rows: evaluate V only at these atoms (the other entries stay 0); the sums run over every atom."""
     R = np.asarray(R_A, dtype=np.float64) / BOHR_A
     box = np.asarray(box_A, dtype=np.float64) / BOHR_A
     b = np.asarray(b, dtype=np.float64)
@@ -83,13 +85,14 @@ def coulomb_potential(R_A, species, hubbard_u, box_A, b, eta=None, rc_bohr=None,
     vol = float(np.prod(box))
     u = np.asarray(hubbard_u, dtype=np.float64)
     V = np.zeros_like(B)
+    rows = np.arange(N) if rows is None else np.asarray(rows, dtype=np.int64)
     # real space, every image within rc (I = J, L = 0 excluded)
     nimg = [int(math.floor((rc + 0.5 * L) / L)) for L in box]
     shifts = np.array([[i, j, k] for i in range(-nimg[0], nimg[0] + 1)
                        for j in range(-nimg[1], nimg[1] + 1)
                        for k in range(-nimg[2], nimg[2] + 1)], dtype=np.float64) * box
-    for s in range(0, N, chunk):
-        I = np.arange(s, min(N, s + chunk))
+    for s in range(0, rows.shape[0], chunk):
+        I = rows[s:s + chunk]
         a = _a_matrix(species[I], species, u)
         d0 = R[None, :, :] - R[I, None, :]
         d0 -= box * np.round(d0 / box)
@@ -110,10 +113,10 @@ def coulomb_potential(R_A, species, hubbard_u, box_A, b, eta=None, rc_bohr=None,
         Sc = c.T @ B                                    # [nk, m]  Re S(k)
         Ss = sn.T @ B                                   # [nk, m]  Im S(k)
         ww = w[s:s + 2048][:, None]
-        V += c @ (ww * Sc) + sn @ (ww * Ss)
+        V[rows] += c[rows] @ (ww * Sc) + sn[rows] @ (ww * Ss)
     # background and self terms
-    V += -math.pi / (eta * eta * vol) * B.sum(axis=0)[None, :]
-    V += (u[species] - 2.0 * eta / math.sqrt(math.pi))[:, None] * B
+    V[rows] += -math.pi / (eta * eta * vol) * B.sum(axis=0)[None, :]
+    V[rows] += (u[species[rows]] - 2.0 * eta / math.sqrt(math.pi))[:, None] * B[rows]
     return V[:, 0] if vec else V
 
 
@@ -123,8 +126,8 @@ def gamma_matrix(R_A, species, hubbard_u, box_A, eta=None):
     return coulomb_potential(R_A, species, hubbard_u, box_A, np.eye(N), eta=eta)
 
 
-def coulomb_gradient(R_A, species, hubbard_u, box_A, a_vec, b_vec, chunk=256):
-    """d/dR_A of E = sum_IJ a_I gamma_IJ b_J for every atom A, in Hartree / Angstrom.
+def coulomb_gradient(R_A, species, hubbard_u, box_A, a_vec, b_vec, chunk=256, rows=None):
+    """d/dR_A of E = sum_IJ a_I gamma_IJ b_J for every atom A (or the atoms in rows), in Hartree / Angstrom.
 
     Real space: dE/dR_A = -sum_{J,L'} (a_A b_J + a_J b_A) phi'(d) d_hat, d = R_J - R_A + L;
     reciprocal: (4 pi / V) sum_k w(k) k [a_A Im(S_b e^{-ik.R_A}) + b_A Im(S_a e^{-ik.R_A})].
@@ -138,13 +141,14 @@ def coulomb_gradient(R_A, species, hubbard_u, box_A, a_vec, b_vec, chunk=256):
     vol = float(np.prod(box))
     u = np.asarray(hubbard_u, dtype=np.float64)
     G = np.zeros((N, 3))
+    rows = np.arange(N) if rows is None else np.asarray(rows, dtype=np.int64)
     nimg = [int(math.floor((rc + 0.5 * L) / L)) for L in box]
     shifts = np.array([[i, j, k] for i in range(-nimg[0], nimg[0] + 1)
                        for j in range(-nimg[1], nimg[1] + 1)
                        for k in range(-nimg[2], nimg[2] + 1)], dtype=np.float64) * box
     sq = 2.0 / math.sqrt(math.pi)
-    for s in range(0, N, chunk):
-        I = np.arange(s, min(N, s + chunk))
+    for s in range(0, rows.shape[0], chunk):
+        I = rows[s:s + chunk]
         a = _a_matrix(species[I], species, u)
         coef = a_vec[I, None] * b_vec[None, :] + a_vec[None, :] * b_vec[I, None]
         d0 = R[None, :, :] - R[I, None, :]
@@ -170,5 +174,5 @@ def coulomb_gradient(R_A, species, hubbard_u, box_A, a_vec, b_vec, chunk=256):
         imb = c * Sb_im[None, :] - sn * Sb_re[None, :]
         ima = c * Sa_im[None, :] - sn * Sa_re[None, :]
         ww = w[s:s + 2048]
-        G += (a_vec[:, None] * imb + b_vec[:, None] * ima) @ (ww[:, None] * kk)
+        G[rows] += (a_vec[rows, None] * imb[rows] + b_vec[rows, None] * ima[rows]) @ (ww[:, None] * kk)
     return G / BOHR_A

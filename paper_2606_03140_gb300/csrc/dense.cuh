@@ -69,9 +69,10 @@ struct GemmParams {
   Sp2State* sp2;
   int* err;
   int mode;
-  int nsplit_out;     // tensor path: plane format written (0: none, 1-3 bf16 planes, 4 two fp16 planes)
-  float alpha, beta;
-  float g1, g2;
+  int nsplit_out;     // tensor path: plane format written (0: none, 1-3 bf16 planes, 4 two fp16 planes;
+                      // the fp16-operand kernel writes two fp16 planes unless 3 is asked for)
+  double alpha, beta; // epilogue coefficients (FP64 in the FP64 path, rounded to FP32 on the tensor path)
+  double g1, g2;
 };
 
 // Host launchers (dense.cu)

@@ -370,7 +370,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_persistent(const GemmPa
 
       float* outm = (m.out_off >= 0) ? reinterpret_cast<float*>(p.arena + m.out_off + out_shift) : nullptr;
       const bool planes = m.outp_off >= 0 && p.nsplit_out > 0;
-      const int fmt = F16 ? kPlanesF16x2 : p.nsplit_out;
+      const int fmt = (F16 && p.nsplit_out != 3) ? kPlanesF16x2 : p.nsplit_out;
+      const float e_alpha = (float)p.alpha, e_beta = (float)p.beta, e_g1 = (float)p.g1, e_g2 = (float)p.g2;
       const bool mirror = m.sym_out && !diag_tile && !upper_only;
       float tr_x = 0.f, tr_x2 = 0.f;
 #pragma unroll
@@ -420,7 +421,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_persistent(const GemmPa
                 tr_x2 += acc[e];
               }
             } else {
-              r = p.alpha * acc[e] + (grow == gcol + e ? p.beta : 0.f) + p.g1 * pre[i][e] + p.g2 * sec[e];
+              r = e_alpha * acc[e] + (grow == gcol + e ? e_beta : 0.f) + e_g1 * pre[i][e] + e_g2 * sec[e];
             }
             out[e] = ok_ij ? r : 0.f;
           }
@@ -547,11 +548,11 @@ __global__ void __launch_bounds__(256) f64_gemm_kernel(const GemmParams p) {
         const double sum = acc[i][j] + cm[(long long)row * ld + col];
         v = branch_sq ? sum : 2.0 * x - sum;
       } else {
-        v = (double)p.alpha * acc[i][j] + (row == col ? (double)p.beta : 0.0);
+        v = p.alpha * acc[i][j] + (row == col ? p.beta : 0.0);
         if (m.c_off >= 0)
-          v += (double)p.g1 * reinterpret_cast<const double*>(
+          v += p.g1 * reinterpret_cast<const double*>(
                    p.arena + m.c_off + (m.c_from_sp2 ? cur * m.buf_stride : 0))[(long long)row * ld + col];
-        if (m.c2_off >= 0) v += (double)p.g2 * reinterpret_cast<const double*>(p.arena + m.c2_off)[(long long)row * ld + col];
+        if (m.c2_off >= 0) v += p.g2 * reinterpret_cast<const double*>(p.arena + m.c2_off)[(long long)row * ld + col];
       }
       if (outm) {
         outm[(long long)row * ld + col] = ok ? v : 0.0;

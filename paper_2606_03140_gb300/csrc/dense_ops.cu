@@ -387,6 +387,18 @@ void launch_sp2_replay_init(Sp2State* st, const double* bounds, const int* n_rea
   sp2_replay_init_kernel<<<(n + 127) / 128, 128, 0, s>>>(st, bounds, n_real, steps, mu, n);
 }
 
+__global__ void buffer_index_kernel(Sp2State* st, int cur, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  st[i].cur = cur;
+  st[i].active = 0;
+}
+
+void launch_buffer_index(Sp2State* st, int cur, int n, cudaStream_t s) {
+  if (n <= 0) return;
+  buffer_index_kernel<<<(n + 127) / 128, 128, 0, s>>>(st, cur, n);
+}
+
 void launch_sp2_init(Sp2State* st, const double* bounds, const int* n_real, double mu, double tol, int kmax, int n,
                      cudaStream_t s) {
   if (n <= 0) return;

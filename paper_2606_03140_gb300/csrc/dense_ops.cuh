@@ -36,6 +36,9 @@ void launch_gershgorin(const SubView* views, int n_sub, int max_rows, const uint
                        const long long* row_base, double* bounds, bool f64, cudaStream_t s);
 void launch_sp2_replay_init(Sp2State* st, const double* bounds, const int* n_real, const int* steps, double mu, int n,
                             cudaStream_t s);
+// Point every subgraph's buffer index (read by the *_from_sp2 operands) at copy `cur` and
+// mark the recursion inactive (after the finite-temperature Fermi pass).
+void launch_buffer_index(Sp2State* st, int cur, int n, cudaStream_t s);
 void launch_sp2_init(Sp2State* st, const double* bounds, const int* n_real, double mu, double tol, int kmax, int n,
                      cudaStream_t s);
 void launch_sp2_advance(Sp2State* st, const double* slots, const long long* tr_off, const int* n_diag,

@@ -5,6 +5,7 @@
 #include <limits>
 
 #include "engine.cuh"
+#include "fermi_coeffs.h"
 
 using namespace sedacs;
 
@@ -130,6 +131,36 @@ __global__ void fill_hist_kernel(double* hist, const double* n, int N) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < N)
     for (int k = 0; k < 6; ++k) hist[k * (long long)N + i] = n[i];
+}
+
+__global__ void rows_axpy_kernel(void* y, const void* x, double a, long long n, int f64) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  if (f64) reinterpret_cast<double*>(y)[t] += a * reinterpret_cast<const double*>(x)[t];
+  else reinterpret_cast<float*>(y)[t] += (float)(a * (double)reinterpret_cast<const float*>(x)[t]);
+}
+
+__global__ void absmax_kernel(const double* a, int N, double* out) {
+  __shared__ double red[1024];
+  double m = 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) m = fmax(m, fabs(a[i]));
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = red[0];
+}
+
+__global__ void add_const_kernel(double* y, double c, int N) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) y[i] += c;
+}
+
+__global__ void lin2_kernel(double* y, const double* a, const double* b, double cb, int N) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) y[i] = a[i] + cb * b[i];
 }
 
 __global__ void matrix_to_f64_kernel(const uint8_t* arena, long long off, bool f64, int rows, int cols, int ld,
@@ -363,24 +394,25 @@ sedacs_status flush_staged(sedacs_ctx* ctx) {
   return SEDACS_OK;
 }
 
-sedacs_status build_op(sedacs_ctx* ctx, int id, int a, int b, int out, int mode, float alpha, float beta,
-                       bool b_from_sp2, bool a_from_sp2 = false, int c1 = -1, float g1 = 0.f, int c2 = -1,
-                       float g2 = 0.f, bool c_from_sp2 = false, bool sym = false) {
+sedacs_status build_op(sedacs_ctx* ctx, int id, int a, int b, int out, int mode, double alpha, double beta,
+                       bool b_from_sp2, bool a_from_sp2 = false, int c1 = -1, double g1 = 0.0, int c2 = -1,
+                       double g2 = 0.0, bool c_from_sp2 = false, bool sym = false, int ca = 0, int cb = 0,
+                       int cout = 0, int cc1 = 0) {
   const Layout& L = ctx->lay;
   std::vector<GemmMat> mats(L.n_sub);
   std::vector<GemmWork> work;
   const bool rows_out = ctx->slot[out].rows;
   for (int i = 0; i < L.n_sub; ++i) {
     GemmMat m{};
-    m.a_off = ctx->f64 ? mptr(ctx, a, i) : pptr_(ctx, a, i);
-    m.b_off = ctx->f64 ? mptr(ctx, b, i) : pptr_(ctx, b, i);
+    m.a_off = ctx->f64 ? mptr(ctx, a, i, ca) : pptr_(ctx, a, i, ca);
+    m.b_off = ctx->f64 ? mptr(ctx, b, i, cb) : pptr_(ctx, b, i, cb);
     m.a_plane = ctx->slot[a].plane_stride;
     m.b_plane = ctx->slot[b].plane_stride;
-    m.out_off = mptr(ctx, out, i);
-    m.outp_off = ctx->f64 ? -1 : pptr_(ctx, out, i);
+    m.out_off = mptr(ctx, out, i, cout);
+    m.outp_off = ctx->f64 ? -1 : pptr_(ctx, out, i, cout);
     m.outp_plane = ctx->slot[out].plane_stride;
     m.x_off = (mode == kModeRsp) ? mptr(ctx, kR2, i) : mptr(ctx, kX, i);
-    m.c_off = (mode == kModeRsp) ? mptr(ctx, kR1, i) : (c1 >= 0 ? mptr(ctx, c1, i) : -1);
+    m.c_off = (mode == kModeRsp) ? mptr(ctx, kR1, i) : (c1 >= 0 ? mptr(ctx, c1, i, cc1) : -1);
     m.c2_off = (c2 >= 0) ? mptr(ctx, c2, i) : -1;
     m.c_from_sp2 = c_from_sp2 ? 1 : 0;
     m.sym_out = sym && !rows_out ? 1 : 0;
@@ -424,6 +456,7 @@ sedacs_status build_op(sedacs_ctx* ctx, int id, int a, int b, int out, int mode,
   op.g1 = g1;
   op.g2 = g2;
   op.mode = mode;
+  op.sym = sym && !rows_out;
   return SEDACS_OK;
 }
 
@@ -452,6 +485,74 @@ sedacs_status upload_vec(sedacs_ctx* ctx, T** dst, const std::vector<T>& v) {
   CUCHK(ensure(ctx, reinterpret_cast<void**>(dst), sizeof(T) * std::max<size_t>(1, v.size())));
   if (!v.empty()) CUCHK(cudaMemcpyAsync(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, ctx->stream));
   CUCHK(cudaStreamSynchronize(ctx->stream));   // v may be a temporary
+  return SEDACS_OK;
+}
+
+// ---- finite-temperature Fermi operator: GEMM tables ---------------------------------------------
+// The recursion (run_fermi) uses the scratch slots of the S^-1/2 and h~ stages, free once h~
+// is formed: z in kP; Z2 / V in kY0 and Z4 / V2 in kY1 (masters: the Horner epilogues add them);
+// the Horner partial sums alternate between kT and kR1; U ping-pongs between the two copies of
+// kX, and the last doubling writes F = (I + U) / 2 into kX copy 0 (three bf16 planes and the
+// master, the format the core-row back-transform reads); s = F - F^2 goes to kR2 copy 0.
+const double* fermi_tanh(const sedacs_ctx* ctx) { return ctx->f64 ? kTanhF64 : kTanhMixed; }
+const double* fermi_inv(const sedacs_ctx* ctx) { return ctx->f64 ? kInvF64 : kInvMixed; }
+int horner_slot(int j) { return (j & 1) ? kT : kR1; }
+
+sedacs_status build_fermi_ops(sedacs_ctx* ctx) {
+  ctx->fermi_j = ctx->f64 ? 5 : 3;      // tanh degree 4 j + 3: 23 (FP64), 15
+  ctx->fermi_m = ctx->f64 ? 7 : 4;      // (1 + v)^-1 degree 2 m + 1: 15 (FP64), 9
+  const int J = ctx->fermi_j, M = ctx->fermi_m;
+  const double* a = fermi_tanh(ctx);
+  const double* c = fermi_inv(ctx);
+  const bool T = true, F = false;
+  // start: Z2 = z z, Z4 = Z2 Z2
+  STCHK(build_op(ctx, OP_F_Z2, kP, kP, kY0, kModeGeneric, 1.0, 0.0, F, F, -1, 0.0, -1, 0.0, F, T));
+  STCHK(build_op(ctx, OP_F_Z4, kY0, kY0, kY1, kModeGeneric, 1.0, 0.0, F, F, -1, 0.0, -1, 0.0, F, T));
+  // q(Z2) = sum_k a_k Z2^k = B_0 + Z4 (B_1 + Z4 (... B_J)), B_j = a_2j + a_2j+1 Z2:
+  // T_1 = B_{J-1} + Z4 B_J = a_2J+1 (Z2 Z4) + a_2J Z4 + a_2J-1 Z2 + a_2J-2 I
+  STCHK(build_op(ctx, OP_F_ST1, kY0, kY1, horner_slot(1), kModeGeneric, a[2 * J + 1], a[2 * J - 2], F, F, kY1,
+                 a[2 * J], kY0, a[2 * J - 1], F, T));
+  // T_j = B_{J-j} + Z4 T_{j-1}
+  for (int j = 2; j <= J; ++j)
+    STCHK(build_op(ctx, OP_F_SH0 + (j - 2), kY1, horner_slot(j - 1), horner_slot(j), kModeGeneric, 1.0,
+                   a[2 * (J - j)], F, F, kY0, a[2 * (J - j) + 1], -1, 0.0, F, T));
+  // U_0 = z q into either copy of kX
+  for (int cu = 0; cu < 2; ++cu)
+    STCHK(build_op(ctx, OP_F_U0_0 + cu, kP, horner_slot(J), kX, kModeGeneric, 1.0, 0.0, F, F, -1, 0.0, -1, 0.0, F,
+                   T, 0, 0, cu));
+  // doubling: V = U U (from either copy), V2 = V V
+  for (int cu = 0; cu < 2; ++cu)
+    STCHK(build_op(ctx, OP_F_V_0 + cu, kX, kX, kY0, kModeGeneric, 1.0, 0.0, F, F, -1, 0.0, -1, 0.0, F, T, cu, cu, 0));
+  STCHK(build_op(ctx, OP_F_V2, kY0, kY0, kY1, kModeGeneric, 1.0, 0.0, F, F, -1, 0.0, -1, 0.0, F, T));
+  // r(V) = sum_k c_k V^k = B_0 + V2 (B_1 + ... V2 B_M), B_j = c_2j + c_2j+1 V:
+  // T_1 = c_2M+1 (V V2) + c_2M V2 + c_2M-1 V + c_2M-2 I, T_j = B_{M-j} + V2 T_{j-1}
+  STCHK(build_op(ctx, OP_F_IT1, kY0, kY1, horner_slot(1), kModeGeneric, c[2 * M + 1], c[2 * M - 2], F, F, kY1,
+                 c[2 * M], kY0, c[2 * M - 1], F, T));
+  for (int j = 2; j <= M; ++j)
+    STCHK(build_op(ctx, OP_F_IH0 + (j - 2), kY1, horner_slot(j - 1), horner_slot(j), kModeGeneric, 1.0,
+                   c[2 * (M - j)], F, F, kY0, c[2 * (M - j) + 1], -1, 0.0, F, T));
+  // U' = 2 U r(V) into the other copy; the last doubling (from copy 1): F = U r(V) + I / 2
+  for (int cu = 0; cu < 2; ++cu)
+    STCHK(build_op(ctx, OP_F_UP_0 + cu, kX, horner_slot(M), kX, kModeGeneric, 2.0, 0.0, F, F, -1, 0.0, -1, 0.0, F, T,
+                   cu, 0, 1 - cu));
+  STCHK(build_op(ctx, OP_F_FIN, kX, horner_slot(M), kX, kModeGeneric, 1.0, 0.5, F, F, -1, 0.0, -1, 0.0, F, T, 1, 0,
+                 0));
+  // s = F - F^2 (F in copy 0, where the SP2 state's buffer index points after a pass)
+  STCHK(build_op(ctx, OP_F_S, kX, kX, kR2, kModeGeneric, -1.0, 0.0, T, T, kX, 1.0, -1, 0.0, T, T));
+  // core rows of F into the response slots: dT1 = Z_c F = F_c + E_z,c F
+  STCHK(build_op(ctx, OP_F_FT1_0, kZ0, kX, kdT1, kModeGeneric, 1.0, 0.0, T, F, kX, 1.0, -1, 0.0, T));
+  STCHK(build_op(ctx, OP_F_FT1_1, kZ1, kX, kdT1, kModeGeneric, 1.0, 0.0, T, F, kX, 1.0, -1, 0.0, T));
+  // energy-weighted rows of s: T2 = dT1 h~, Ws = 2 (T2 + T2 E_z) into kT1
+  STCHK(build_op(ctx, OP_F_T2S, kdT1, kHt, kT2, kModeGeneric, 1.0, 0.0, F));
+  STCHK(build_op(ctx, OP_F_WS0, kT2, kZ0, kT1, kModeGeneric, 2.0, 0.0, F, F, kT2, 2.0));
+  STCHK(build_op(ctx, OP_F_WS1, kT2, kZ1, kT1, kModeGeneric, 2.0, 0.0, F, F, kT2, 2.0));
+  // second-order term: t = s (I - 2F) = s - 2 s F into kR1 copy 1; d^2 F / dmu^2 = beta^2 t
+  STCHK(build_op(ctx, OP_F_T, kR2, kX, kR1, kModeGeneric, -2.0, 0.0, T, T, kR2, 1.0, -1, 0.0, T, T, 0, 0, 1));
+  STCHK(build_op(ctx, OP_F_TT1_0, kZ0, kR1, kdT2, kModeGeneric, 1.0, 0.0, F, F, kR1, 1.0, -1, 0.0, F, F, 0, 1, 0, 1));
+  STCHK(build_op(ctx, OP_F_TT1_1, kZ1, kR1, kdT2, kModeGeneric, 1.0, 0.0, F, F, kR1, 1.0, -1, 0.0, F, F, 0, 1, 0, 1));
+  STCHK(build_op(ctx, OP_F_DT0, kdT2, kZ0, kdDt, kModeGeneric, 2.0, 0.0, F, F, kdT2, 2.0));
+  STCHK(build_op(ctx, OP_F_DT1, kdT2, kZ1, kdDt, kModeGeneric, 2.0, 0.0, F, F, kdT2, 2.0));
+  STCHK(build_op(ctx, OP_F_T2T, kdT2, kHt, kT2, kModeGeneric, 1.0, 0.0, F));
   return SEDACS_OK;
 }
 
@@ -503,14 +604,16 @@ sedacs_status rebuild_layout(sedacs_ctx* ctx) {
     L.max_npad = std::max(L.max_npad, L.n_pad[i]);
     L.max_mpad = std::max(L.max_mpad, L.m_pad[i]);
   }
+  ctx->sum_n3 = 0.0;
+  for (int i = 0; i < P; ++i) ctx->sum_n3 += (double)L.n_real[i] * L.n_real[i] * L.n_real[i];
   // arena slots
   const int esz = ctx->f64 ? 8 : 4;
   const bool planes = !ctx->f64;
   long long off = 0;
   for (int k = 0; k < kNumSlots; ++k) {
     Slot& S = ctx->slot[k];
-    S.rows = (k == kT1 || k == kDc || k == kT2 || k == kWc || k == kdT1 || k == kdDc);
-    S.planes = planes && !(k == kDc || k == kWc || k == kdDc);
+    S.rows = (k == kT1 || k == kDc || k == kT2 || k == kWc || k == kdT1 || k == kdDc || k == kdT2 || k == kdDt);
+    S.planes = planes && !(k == kDc || k == kWc || k == kdDc || k == kdDt);
     S.copies = (k == kX || k == kR1 || k == kR2) ? 2 : 1;
     const long long el = S.rows ? L.rw_total : L.sq_total;
     S.master_bytes = (el * esz + 1023) / 1024 * 1024;
@@ -529,7 +632,7 @@ sedacs_status rebuild_layout(sedacs_ctx* ctx) {
   // views and per-subgraph offset arrays
   for (int k = 0; k < kNumSlots; ++k) STCHK(stage_views(ctx, k, 0, &ctx->d_views[k]));
   STCHK(stage_views(ctx, kX, 1, &ctx->d_views_x1));
-  std::vector<long long> hoff(P), soff(P), dco(P), wco(P), rbase(P), troff(P), ddco(P), dhoff(P);
+  std::vector<long long> hoff(P), soff(P), dco(P), wco(P), rbase(P), troff(P), ddco(P), dhoff(P), dtco(P);
   std::vector<int> npad(P), nreal(P), ndiag(P);
   long long rb = 0;
   for (int i = 0; i < P; ++i) {
@@ -538,6 +641,7 @@ sedacs_status rebuild_layout(sedacs_ctx* ctx) {
     dco[i] = mptr(ctx, kDc, i);
     wco[i] = mptr(ctx, kWc, i);
     ddco[i] = mptr(ctx, kdDc, i);
+    dtco[i] = mptr(ctx, kdDt, i);
     dhoff[i] = mptr(ctx, kdH, i);
     rbase[i] = rb;
     rb += L.n_pad[i];
@@ -551,6 +655,7 @@ sedacs_status rebuild_layout(sedacs_ctx* ctx) {
   STCHK(stage_vec(ctx, &ctx->d_dcoff, dco));
   STCHK(stage_vec(ctx, &ctx->d_wcoff, wco));
   STCHK(stage_vec(ctx, &ctx->d_dcoff_d, ddco));
+  STCHK(stage_vec(ctx, &ctx->d_dcoff_t, dtco));
   STCHK(stage_vec(ctx, &ctx->d_dhoff, dhoff));
   STCHK(stage_vec(ctx, &ctx->d_rowbase, rbase));
   STCHK(stage_vec(ctx, &ctx->d_tr_off, troff));
@@ -624,6 +729,7 @@ sedacs_status rebuild_layout(sedacs_ctx* ctx) {
   STCHK(build_op(ctx, OP_DT1_1, kZ1, kR2, kdT1, kModeGeneric, 1.f, 0.f, true, false, kR2, 1.f, -1, 0.f, true));
   STCHK(build_op(ctx, OP_DDC0, kdT1, kZ0, kdDc, kModeGeneric, 2.f, 0.f, false, false, kdT1, 2.f));
   STCHK(build_op(ctx, OP_DDC1, kdT1, kZ1, kdDc, kModeGeneric, 2.f, 0.f, false, false, kdT1, 2.f));
+  STCHK(build_fermi_ops(ctx));
   CUCHK(cudaGetLastError());
   STCHK(flush_staged(ctx));
   CUCHK(cudaGetLastError());
@@ -637,14 +743,15 @@ sedacs_status rebuild_layout(sedacs_ctx* ctx) {
 // ---- dense stages ------------------------------------------------------------------------------
 int max_rows(const sedacs_ctx* ctx) { return ctx->lay.max_npad; }
 
-void gather_hs(sedacs_ctx* ctx) {
+void gather_hs(sedacs_ctx* ctx, const double* V = nullptr) {
   cudaStream_t s = ctx->stream;
+  if (!V) V = ctx->d_V;
   const Layout& L = ctx->lay;
   const int esz = ctx->f64 ? 8 : 4;
   cudaMemsetAsync(ctx->arena + ctx->slot[kS].base, 0, L.sq_total * esz, s);
   cudaMemsetAsync(ctx->arena + ctx->slot[kH].base, 0, L.sq_total * esz, s);
   launch_gather(ctx->model, ctx->d_sub_ptr, ctx->d_sub_atoms, ctx->d_orb_off, ctx->d_species, ctx->d_pptr,
-                ctx->d_pcol, ctx->d_h0b, ctx->d_sb, ctx->d_loc, ctx->N, ctx->d_V, ctx->d_hoff, ctx->d_soff,
+                ctx->d_pcol, ctx->d_h0b, ctx->d_sb, ctx->d_loc, ctx->N, V, ctx->d_hoff, ctx->d_soff,
                 ctx->d_n_pad, ctx->arena, L.n_sub, ctx->d_sub_of_row, ctx->sub_ptr_h[L.n_sub], 0, ctx->f64, s);
   ctx->launches += 3;
   if (!ctx->f64) {
@@ -855,52 +962,239 @@ sedacs_status observe(sedacs_ctx* ctx, bool with_forces, double* n_count) {
   return SEDACS_OK;
 }
 
-// T -> 0 electron count at trial mu (SP2 + D_c rows + populations).
-sedacs_status count_at(sedacs_ctx* ctx, double mu, int kmax, double* nel) {
-  STCHK(run_sp2(ctx, mu, kmax));
-  back_transform(ctx, false);
-  return observe(ctx, false, nel);
-}
+// ---- finite-temperature Fermi operator (Eq. 2) and the chemical potential ------------------------
+// F = [exp(beta (h~ - mu I)) + I]^-1 = (I + U) / 2 with U = tanh(beta (mu I - h~) / 2).  The pass
+// starts at the temperature 2^n Te, where every eigenvalue of z = beta_0 (mu I - h~) / 2,
+// beta_0 = beta / 2^n, lies in [-1, 1] and tanh(z) is the odd polynomial z q(z^2) of fermi_coeffs.h
+// (Z2 = z z, Z4 = Z2 Z2, Horner in Z4), and halves the temperature n times by the doubling identity
+// tanh(2a) = 2 tanh(a) / (1 + tanh(a)^2): U <- 2 U r(U^2), r(V) ~ (I + V)^-1 on the spectrum [0, 1]
+// of V = U^2 (V2 = V V, Horner in V2).  This is a recursive Fermi-operator expansion in the sense of
+// Sec. "Density Matrix Evaluation on Partitioned Graphs": every product is a symmetric n x n product of
+// functions of h~, run on the tensor cores (upper tiles).  A rounding error e in U near a level at mu
+// grows like the level's own U (relative error kept), i.e. it acts as a level shift of about
+// e x_max, x_max the spectral reach from mu.
+constexpr double kKbHa = 3.166811563e-6;   // Boltzmann constant, Hartree / K
+double beta_of(const sedacs_ctx* ctx) { return 1.0 / (kKbHa * ctx->prm.Te); }
 
-// Half-width of the electron-count window that locates the gap edges: the graph truncation
-// leaves the mid-gap count off N_e by an amount growing with the system (~2.5e-5 e/atom in
-// water), kept inside kappa = 1/2 + 1e-4 N_e.
-double count_window(double ne) { return 0.5 + 1e-4 * ne; }
-
-// mu at the middle of the collected gap: the smallest mu with N0 >= N_e - kappa (top of the
-// occupied levels) and the smallest mu with N0 > N_e + kappa (bottom of the empty ones).
-sedacs_status solve_mu(sedacs_ctx* ctx, double* mu_out) {
-  double lo = 1e300, hi = -1e300;
+// Doublings n for a pass at mu: 2^n >= beta x_max / 1.9 puts every eigenvalue of z in [-0.95, 0.95]
+// (Gershgorin bounds of h~ per subgraph; the margin covers the small shifts of the response passes).
+int fermi_doublings(const sedacs_ctx* ctx, double mu) {
+  double xmax = 0.0;
   for (int i = 0; i < ctx->lay.n_sub; ++i) {
     if (ctx->lay.n_real[i] == 0) continue;
+    xmax = std::max(xmax, std::max(mu - ctx->bounds_h[2 * i], ctx->bounds_h[2 * i + 1] - mu));
+  }
+  const double need = beta_of(ctx) * xmax / 1.9;
+  int n = 1;
+  while (std::ldexp(1.0, n) < need && n < 60) ++n;
+  return n;
+}
+
+// One launch of a Fermi-recursion product, with per-launch CUDA events when kernel statistics are
+// on; a symmetric product counts n^3 flops per subgraph (upper triangle), a core-row product is
+// not counted.
+void run_fop(sedacs_ctx* ctx, int id, int nin, int nout) {
+  const bool rec = ctx->kstats && ctx->kev_used + 2 <= (int)ctx->kev.size();
+  if (rec) cudaEventRecord(ctx->kev[ctx->kev_used], ctx->stream);
+  run_op(ctx, id, nin, nout);
+  if (rec) {
+    cudaEventRecord(ctx->kev[ctx->kev_used + 1], ctx->stream);
+    ctx->kev_used += 2;
+    if (ctx->ops[id].sym) ctx->k_flops += ctx->sum_n3;
+  }
+}
+
+// Collect the per-launch times recorded since the events were last read.
+void drain_kstats(sedacs_ctx* ctx, int ev0) {
+  if (!ctx->kstats || ctx->kev_used == ev0) return;
+  cudaStreamSynchronize(ctx->stream);
+  for (int e = ev0; e + 1 < ctx->kev_used; e += 2) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->kev[e], ctx->kev[e + 1]);
+    ctx->k_ms += ms;
+    ctx->k_launches += 1;
+  }
+  ctx->kev_used = ev0;
+}
+
+// One pass: F at (mu, beta) into kX copy 0, every buffer index pointing there.
+void run_fermi(sedacs_ctx* ctx, double mu, int nd) {
+  cudaStream_t s = ctx->stream;
+  const Layout& L = ctx->lay;
+  const int nf = ctx->f64 ? 0 : ctx->nsplit_fermi;
+  const double b0 = std::ldexp(beta_of(ctx), -nd);
+  launch_affine_planes(ctx->d_views[kHt], ctx->d_views[kP], -0.5 * b0, 0.5 * b0 * mu, ctx->f64 ? 1 : 0, nf, nullptr,
+                       0.0, 0.0, 0, 0, 0, nullptr, L.n_sub, max_rows(ctx), ctx->arena, ctx->f64, s);   // z
+  ctx->launches += 1;
+  run_fop(ctx, OP_F_Z2, nf, nf);
+  run_fop(ctx, OP_F_Z4, nf, nf);
+  run_fop(ctx, OP_F_ST1, nf, nf);
+  for (int j = 2; j <= ctx->fermi_j; ++j) run_fop(ctx, OP_F_SH0 + (j - 2), nf, nf);
+  // U_0 goes to the copy from which n doublings end in copy 0
+  int cu = nd & 1;
+  run_fop(ctx, OP_F_U0_0 + cu, nf, nf);
+  for (int k = 0; k < nd; ++k) {
+    run_fop(ctx, OP_F_V_0 + cu, nf, nf);
+    run_fop(ctx, OP_F_V2, nf, nf);
+    run_fop(ctx, OP_F_IT1, nf, nf);
+    for (int j = 2; j <= ctx->fermi_m; ++j) run_fop(ctx, OP_F_IH0 + (j - 2), nf, nf);
+    if (k == nd - 1) {
+      run_fop(ctx, OP_F_FIN, nf, ctx->f64 ? 0 : 3);    // cu == 1 here: F = U r(V) + I / 2, bf16 planes
+    } else {
+      run_fop(ctx, OP_F_UP_0 + cu, nf, nf);
+      cu = 1 - cu;
+    }
+  }
+  launch_buffer_index(ctx->d_sp2, 0, L.n_sub, s);
+  ctx->launches += 1;
+  ctx->fermi_n = nd;
+}
+
+// Populations of the core rows at dc_off (per atom, the FP64 sum over each core atom's orbitals
+// and its subgraph) into pop, band-energy partials into eb, and their sum into d_scal[k].
+void core_pops(sedacs_ctx* ctx, const long long* dc_off, double* pop, double* eb, int k) {
+  cudaStream_t s = ctx->stream;
+  launch_observables(ctx->model, ctx->d_R, ctx->d_species, sk_geom(ctx), ctx->d_sub_ptr, ctx->d_sub_atoms,
+                     ctx->d_orb_off, ctx->part.perm, ctx->d_core_sub, ctx->d_core_local, ctx->n_core_total,
+                     ctx->d_pptr, ctx->d_pcol, ctx->d_h0b, ctx->d_sb, ctx->d_loc, ctx->N, ctx->d_V, ctx->arena,
+                     ctx->arena, dc_off, dc_off, ctx->d_n_pad, pop, eb, ctx->d_dU, 0, ctx->f64, s);
+  dot_kernel<<<1, 1024, 0, s>>>(pop, nullptr, ctx->N, ctx->d_scal + k);
+  ctx->launches += 2;
+}
+
+// s = F - F^2 and the core rows D_s = 2 Z_c s Z (kdT1 -> kdDc); d/dmu of F is beta s.
+void fermi_s_rows(sedacs_ctx* ctx) {
+  const int ns = ctx->nsplit_ns;
+  run_fop(ctx, OP_F_S, ctx->f64 ? 0 : 3, ctx->f64 ? 0 : 3);
+  run_op(ctx, ctx->zc == 0 ? OP_DT1_0 : OP_DT1_1, 3, ns);
+  run_op(ctx, ctx->zc == 0 ? OP_DDC0 : OP_DDC1, ns, 0);
+}
+
+// t = s (I - 2F) and its core rows D_t = 2 Z_c t Z (kdT2 -> kdDt); d^2 F / dmu^2 is beta^2 t.
+void fermi_t_rows(sedacs_ctx* ctx) {
+  const int ns = ctx->nsplit_ns;
+  run_fop(ctx, OP_F_T, ctx->f64 ? 0 : 3, ctx->f64 ? 0 : 3);
+  run_op(ctx, ctx->zc == 0 ? OP_F_TT1_0 : OP_F_TT1_1, 3, ns);
+  run_op(ctx, ctx->zc == 0 ? OP_F_DT0 : OP_F_DT1, ns, 0);
+}
+
+
+void rows_axpy(sedacs_ctx* ctx, int sy, int sx, double a) {
+  const long long n = ctx->lay.rw_total;
+  rows_axpy_kernel<<<nblk(n, 256), 256, 0, ctx->stream>>>(ctx->arena + ctx->slot[sy].base,
+                                                         ctx->arena + ctx->slot[sx].base, a, n, ctx->f64 ? 1 : 0);
+  ctx->launches += 1;
+}
+
+// Eq. 2: mu with the collected count N(mu) = sum_i Tr_core[D_i S_i] = N_e, by safeguarded Newton
+// steps on full passes inside a bracket that starts at the spectral bounds, bisecting when a step
+// leaves it.  The mu derivatives of the Fermi function are exact matrix functions of F:
+// dF/dmu = beta s, s = F - F^2, and d^2F/dmu^2 = beta^2 t, t = s (I - 2F).  A pass at mu0 whose
+// count, expanded to second order, reaches N_e within |beta dmu| <= fermi_lin is accepted with
+// D_c += beta dmu D_s + (beta dmu)^2 / 2 D_t and the same for W_c (third-order remainder).  Leaves
+// D_c, W_c of the final density in kDc, kWc; mu_io in: guess (NaN: none), out: mu.
+sedacs_status fermi_density(sedacs_ctx* ctx, double* mu_io) {
+  cudaStream_t s = ctx->stream;
+  const Layout& L = ctx->lay;
+  const int ns = ctx->nsplit_ns, N = ctx->N;
+  const double beta = beta_of(ctx), ne = ctx->n_electrons;
+  const double lin = ctx->prm.fermi_lin > 0 ? ctx->prm.fermi_lin : (ctx->f64 ? 1.5e-3 : 3e-2);
+  double lo = 1e300, hi = -1e300;
+  for (int i = 0; i < L.n_sub; ++i) {
+    if (L.n_real[i] == 0) continue;
     lo = std::min(lo, ctx->bounds_h[2 * i]);
     hi = std::max(hi, ctx->bounds_h[2 * i + 1]);
   }
-  const double ne = ctx->n_electrons, kap = count_window(ne), delta = 1e-3;
-  const int kt = 40;
-  double a = lo, b = hi, nel = 0.0;
-  while (b - a > delta) {
-    const double m = 0.5 * (a + b);
-    STCHK(count_at(ctx, m, kt, &nel));
-    if (nel >= ne - kap) b = m; else a = m;
+  double a = lo - 0.05, b = hi + 0.05;     // N(a) ~ 0 < N_e < N(b) ~ all orbitals
+  const bool given = ctx->prm.mu_given != 0 && std::isfinite(*mu_io);
+  double mu = std::isfinite(*mu_io) ? (given ? *mu_io : std::min(std::max(*mu_io, a), b)) : 0.5 * (lo + hi);
+  double dmu = 0.0, np = 0.0;
+  double* pop_s = ctx->d_rsp + 6LL * N;      // kept for the response calls (their dN/dmu weights)
+  double* scr = ctx->d_rsp + 7LL * N;
+  double* pop_t = ctx->d_rsp + 5LL * N;
+  int pass = 0;
+  bool done = false;
+  double step_old = b - a, step_prev = b - a;
+  ctx->fermi_hist.clear();
+  const int ev0 = ctx->kev_used;
+  while (!done && pass < 80) {
+    ++pass;
+    run_fermi(ctx, mu, fermi_doublings(ctx, mu));
+    back_transform(ctx, false);                                   // T1 = Z_c F, D_c
+    if (given) { done = true; break; }
+    core_pops(ctx, ctx->d_dcoff, ctx->d_pop, ctx->d_eband, 9);     // N(mu)
+    fermi_s_rows(ctx);
+    core_pops(ctx, ctx->d_dcoff_d, pop_s, scr, 10);                // sum of D_s populations
+    fermi_t_rows(ctx);
+    core_pops(ctx, ctx->d_dcoff_t, pop_t, scr, 14);                // sum of D_t populations
+    double sc[6];
+    CUCHK(cudaMemcpyAsync(sc, ctx->d_scal + 9, sizeof(sc), cudaMemcpyDeviceToHost, s));
+    CUCHK(cudaStreamSynchronize(s));
+    const double nel = sc[0];
+    np = beta * sc[1];
+    const double n2 = beta * beta * sc[5];
+    const double dn = ne - nel;
+    ctx->fermi_hist.insert(ctx->fermi_hist.end(), {mu, dn, np});
+    if (!std::isfinite(nel) || !std::isfinite(np)) { ctx->err = "non-finite electron count"; return SEDACS_ENUMERIC; }
+    if (np > 0.0) {
+      // root of np d + n2 d^2 / 2 = dn next to the Newton step dn / np
+      double d = dn / np;
+      for (int it = 0; it < 4; ++it) {
+        const double gp = np + n2 * d;
+        if (!(gp > 0.0)) break;
+        d -= (np * d + 0.5 * n2 * d * d - dn) / gp;
+      }
+      if (std::isfinite(d) && std::fabs(beta * d) <= lin) { dmu = d; done = true; break; }
+    }
+    // a count already within its rounding noise (a clean gap: dN/dmu ~ 0) is accepted as it is
+    if (std::fabs(dn) <= (ctx->f64 ? 1e-9 : 1e-7) * ne) { dmu = 0.0; done = true; break; }
+    if (dn > 0.0) a = mu; else b = mu;
+    if (b - a < 1e-13) { dmu = 0.0; done = true; break; }
+    // Newton only while it lands inside the bracket and at least halves the step before last
+    // (in a gap dN/dmu is tiny and, in the FP32-class forms, rounding noise): else bisect
+    const double step = np > 0.0 ? dn / np : std::numeric_limits<double>::infinity();
+    const double next = mu + step;
+    const bool newton = (next > a && next < b) && std::fabs(step) < 0.5 * std::fabs(step_old);
+    step_old = step_prev;
+    if (newton) {
+      step_prev = step;
+      mu = next;
+    } else {
+      step_prev = 0.5 * (b - a);
+      mu = 0.5 * (a + b);
+    }
   }
-  const double mu_h = b;
-  a = mu_h;
-  b = hi;
-  while (b - a > delta) {
-    const double m = 0.5 * (a + b);
-    STCHK(count_at(ctx, m, kt, &nel));
-    if (nel > ne + kap) b = m; else a = m;
+  drain_kstats(ctx, ev0);
+  if (!done) { ctx->err = "chemical potential of Eq. 2 not found within 80 Fermi passes"; return SEDACS_EPRECISION; }
+  run_op(ctx, OP_T2, ns, ns);                                      // W_c = 2 Z_c F h~ Z
+  run_op(ctx, ctx->zc == 0 ? OP_WC0 : OP_WC1, ns, 0);
+  if (dmu != 0.0) {
+    const double c1 = beta * dmu, c2 = 0.5 * c1 * c1;
+    rows_axpy(ctx, kDc, kdDc, c1);
+    rows_axpy(ctx, kDc, kdDt, c2);
+    run_op(ctx, OP_F_T2S, ns, ns);                                 // W_s = 2 Z_c s h~ Z -> kT1
+    run_op(ctx, ctx->zc == 0 ? OP_F_WS0 : OP_F_WS1, ns, 0);
+    rows_axpy(ctx, kWc, kT1, c1);
+    run_op(ctx, OP_F_T2T, ns, ns);                                 // W_t = 2 Z_c t h~ Z -> kT1
+    run_op(ctx, ctx->zc == 0 ? OP_F_WS0 : OP_F_WS1, ns, 0);
+    rows_axpy(ctx, kWc, kT1, c2);
   }
-  const double mu_l = a;
-  *mu_out = 0.5 * (mu_h + mu_l);
+  ctx->fermi_dndmu = np;
+  ctx->fermi_dmu = dmu;
+  ctx->fermi_passes = pass;
+  *mu_io = mu + dmu;
   return SEDACS_OK;
 }
 
-// allow_resolve: place mu again when the count leaves the window (internal SCC / MD loops,
-// or a caller that asked for mu = NaN); a mu given by the caller is used as given.
-sedacs_status density_core(sedacs_ctx* ctx, double* mu_io, bool allow_resolve = true) {
+// mu_io: Te > 0: in = guess for the Eq. 2 solve (NaN: none), out = the solution (or, with
+// mu_given, the value used); Te = 0: the chemical potential of the T -> 0 SP2 recursion, as given.
+sedacs_status density_core(sedacs_ctx* ctx, double* mu_io) {
   if (!ctx->have_subs) { ctx->err = "no subgraphs: call sedacs_graph_build and sedacs_partition first"; return SEDACS_EINVAL; }
+  const bool finite_t = ctx->prm.Te > 0.0;
+  if (!finite_t && !std::isfinite(*mu_io)) {
+    ctx->err = "Te = 0 (T -> 0 SP2) needs a chemical potential";
+    return SEDACS_EINVAL;
+  }
   cudaStream_t s = ctx->stream;
   STCHK(prepare_geometry(ctx));
   phase_begin(ctx, 0);
@@ -915,25 +1209,23 @@ sedacs_status density_core(sedacs_ctx* ctx, double* mu_io, bool allow_resolve = 
   if (!ctx->z_valid) compute_z(ctx);
   compute_ht(ctx);                      // h's planes were written by gather_hs
   CUCHK(cudaStreamSynchronize(s));
+  ctx->ht_stale = false;
   phase_end(ctx, 0, 3);
   double mu = *mu_io;
   double nel = 0.0;
   phase_begin(ctx, 0);
-  if (std::isnan(mu)) STCHK(solve_mu(ctx, &mu));
-  STCHK(run_sp2(ctx, mu, ctx->prm.sp2_kmax));
+  if (finite_t) {
+    STCHK(fermi_density(ctx, &mu));
+  } else {
+    STCHK(run_sp2(ctx, mu, ctx->prm.sp2_kmax));
+  }
   phase_end(ctx, 0, 4);
   phase_begin(ctx, 0);
-  back_transform(ctx, true);
+  if (!finite_t) back_transform(ctx, true);
   // when forces follow (XL-BOMD), the same pass also contracts the force blocks
   const bool fused = ctx->fuse_forces;
   STCHK(observe(ctx, fused, &nel));
-  if (allow_resolve && std::fabs(nel - ctx->n_electrons) > count_window(ctx->n_electrons)) {
-    // mu left the gap (the levels moved): place it again
-    STCHK(solve_mu(ctx, &mu));
-    STCHK(run_sp2(ctx, mu, ctx->prm.sp2_kmax));
-    back_transform(ctx, true);
-    STCHK(observe(ctx, fused, &nel));
-  }
+  ctx->fermi_count_err = nel - ctx->n_electrons;
   ctx->du_ready = fused;
   launch_gd(ctx->model, ctx->d_sub_ptr, ctx->d_sub_atoms, ctx->d_orb_off, ctx->d_species, ctx->part.perm,
             ctx->d_core_sub, ctx->d_core_local, ctx->n_core_total, ctx->arena, ctx->f64, ctx->d_dcoff, ctx->d_n_pad,
@@ -954,9 +1246,13 @@ sedacs_status density_core(sedacs_ctx* ctx, double* mu_io, bool allow_resolve = 
   ctx->e_coul = sc[2];
   ctx->mu = mu;
   *mu_io = mu;
-  std::vector<Sp2State> st(ctx->lay.n_sub);
-  CUCHK(cudaMemcpy(st.data(), ctx->d_sp2, sizeof(Sp2State) * ctx->lay.n_sub, cudaMemcpyDeviceToHost));
-  for (int i = 0; i < ctx->lay.n_sub; ++i) ctx->sp2_iters_h[i] = st[i].iters;
+  if (finite_t) {
+    std::fill(ctx->sp2_iters_h.begin(), ctx->sp2_iters_h.end(), ctx->fermi_n);
+  } else {
+    std::vector<Sp2State> st(ctx->lay.n_sub);
+    CUCHK(cudaMemcpy(st.data(), ctx->d_sp2, sizeof(Sp2State) * ctx->lay.n_sub, cudaMemcpyDeviceToHost));
+    for (int i = 0; i < ctx->lay.n_sub; ++i) ctx->sp2_iters_h[i] = st[i].iters;
+  }
   ctx->have_density = true;
   ctx->have_gd = true;
   ctx->have_forces = false;
@@ -1033,10 +1329,10 @@ double dev_dot(sedacs_ctx* ctx, const double* a, const double* b) {
   return host_scalar(ctx, ctx->d_scal + 8);
 }
 
-// dq = dq/dn v at fixed mu: dV = gamma v, dh = 1/2 (s dV + dV s), dh~ = Z dh Z, first-order
+// Te = 0: dq = dq/dn v at fixed mu: dV = gamma v, dh = 1/2 (s dV + dV s), dh~ = Z dh Z, first-order
 // SP2 replay dX (same branch sequence and step count as the last density call), then
 // dD_c = 2 Z_c dX Z and dq_A = sum dD_AB . S_AB.
-sedacs_status response_core(sedacs_ctx* ctx, const double* d_v, double* d_dq) {
+sedacs_status response_sp2(sedacs_ctx* ctx, const double* d_v, double* d_dq) {
   if (!ctx->have_density) { ctx->err = "no density: call sedacs_subgraph_density first"; return SEDACS_EINVAL; }
   cudaStream_t s = ctx->stream;
   const Layout& L = ctx->lay;
@@ -1075,6 +1371,85 @@ sedacs_status response_core(sedacs_ctx* ctx, const double* d_v, double* d_dq) {
                      ctx->f64, s);
   ctx->launches += 1;
   return check_dev_err(ctx);
+}
+
+
+
+// Te > 0: canonical dq = dq/dn v on the subgraphs of the last density call, by the central difference
+// of two density passes at the potentials V(n) +- eps gamma v (the Hamiltonian is linear in V):
+// each pass gathers h, forms h~ = Z h Z, runs the Fermi pass at the last mu with the last doubling
+// count, and takes its collected charges with the linear mu step that restores N_e (the same first-
+// order rule as the density calls), so the response conserves the electron count (canonical, the mu
+// shift of Eq. 2).  eps max|v| = 1e-3 e (FP32-class forms) or 1e-4 e (FP64).
+sedacs_status response_fermi(sedacs_ctx* ctx, const double* d_v, double* d_dq) {
+  cudaStream_t s = ctx->stream;
+  const int N = ctx->N, ns = ctx->nsplit_ns;
+  const double beta = beta_of(ctx), ne = ctx->n_electrons;
+  double* dV = ctx->d_rsp;
+  double* Vp = ctx->d_rsp + 1LL * N;
+  double* qp = ctx->d_rsp + 2LL * N;
+  double* qm = ctx->d_rsp + 3LL * N;
+  double* ps = ctx->d_rsp + 4LL * N;
+  double* eb = ctx->d_rsp + 5LL * N;
+  absmax_kernel<<<1, 1024, 0, s>>>(d_v, N, ctx->d_scal + 11);
+  ctx->launches += 1;
+  const double vmax = host_scalar(ctx, ctx->d_scal + 11);
+  if (!(vmax > 0.0)) {
+    CUCHK(cudaMemsetAsync(d_dq, 0, sizeof(double) * N, s));
+    return SEDACS_OK;
+  }
+  CUCHK(ctx->ew.potential(d_v, dV, s));
+  ctx->launches += 6;
+  // A uniform potential shift moves every level and mu together and has no canonical response
+  // (h~ changes by c I).  Removing the dN/dmu-weighted mean of dV (weights: the populations of
+  // D_s of the last density call) leaves the part that moves charge, so the one linear mu step
+  // per side stays small.
+  if (ctx->fermi_dndmu > 0.0) {
+    const double* w = ctx->d_rsp + 6LL * N;
+    dot_kernel<<<1, 1024, 0, s>>>(w, dV, N, ctx->d_scal + 12);
+    dot_kernel<<<1, 1024, 0, s>>>(w, nullptr, N, ctx->d_scal + 13);
+    ctx->launches += 2;
+    double sw[2];
+    CUCHK(cudaMemcpyAsync(sw, ctx->d_scal + 12, sizeof(sw), cudaMemcpyDeviceToHost, s));
+    CUCHK(cudaStreamSynchronize(s));
+    if (sw[1] > 0.0) {
+      add_const_kernel<<<nblk(N, 128), 128, 0, s>>>(dV, -sw[0] / sw[1], N);
+      ctx->launches += 1;
+    }
+  }
+  const double eps = (ctx->f64 ? 1e-4 : 1e-3) / vmax;
+  const int nd = ctx->fermi_n > 0 ? ctx->fermi_n : fermi_doublings(ctx, ctx->mu);
+  const int ev0 = ctx->kev_used;
+  for (int side = 0; side < 2; ++side) {
+    double* q = side == 0 ? qp : qm;
+    lin2_kernel<<<nblk(N, 128), 128, 0, s>>>(Vp, ctx->d_V, dV, side == 0 ? eps : -eps, N);
+    ctx->launches += 1;
+    gather_hs(ctx, Vp);
+    compute_ht(ctx);
+    run_fermi(ctx, ctx->mu, nd);
+    run_op(ctx, ctx->zc == 0 ? OP_F_FT1_0 : OP_F_FT1_1, 3, ns);   // dT1 = Z_c F
+    run_op(ctx, ctx->zc == 0 ? OP_DDC0 : OP_DDC1, ns, 0);         // 2 dT1 Z
+    core_pops(ctx, ctx->d_dcoff_d, q, eb, 9);
+    fermi_s_rows(ctx);
+    core_pops(ctx, ctx->d_dcoff_d, ps, eb, 10);
+    double sc[2];
+    CUCHK(cudaMemcpyAsync(sc, ctx->d_scal + 9, sizeof(sc), cudaMemcpyDeviceToHost, s));
+    CUCHK(cudaStreamSynchronize(s));
+    const double dmu = sc[1] > 0.0 ? (ne - sc[0]) / (beta * sc[1]) : 0.0;
+    axpy2_kernel<<<nblk(N, 128), 128, 0, s>>>(q, ps, beta * dmu, N);
+    ctx->launches += 1;
+  }
+  drain_kstats(ctx, ev0);
+  sub_kernel<<<nblk(N, 128), 128, 0, s>>>(d_dq, qp, qm, N);
+  scale_kernel<<<nblk(N, 128), 128, 0, s>>>(d_dq, d_dq, 0.5 / eps, N);
+  ctx->launches += 2;
+  ctx->ht_stale = true;
+  return check_dev_err(ctx);
+}
+
+sedacs_status response_core(sedacs_ctx* ctx, const double* d_v, double* d_dq) {
+  if (!ctx->have_density) { ctx->err = "no density: call sedacs_subgraph_density first"; return SEDACS_EINVAL; }
+  return ctx->prm.Te > 0.0 ? response_fermi(ctx, d_v, d_dq) : response_sp2(ctx, d_v, d_dq);
 }
 
 // u ~ (K0 J)^-1 K0 f with K0 = -c I (SI Sec. B, Eqs. "PreKernel"-"LowRankEEOM").
@@ -1215,6 +1590,9 @@ void sedacs_default_params(sedacs_params* p) {
   p->sp2_kmax = 60;
   p->ns_iters = 0;      // 0: 3 steps in the mixed forms, 4 in FP64
   p->ewald_tol = 0.0;
+  p->Te = 300.0;
+  p->mu_given = 0;
+  p->fermi_lin = 0.0;   // automatic: 5e-3 in the FP32-class forms, 1e-4 in FP64
 }
 
 sedacs_status sedacs_create(int32_t n_atoms, const int32_t* species, const double box[3], const sedacs_model* model,
@@ -1225,7 +1603,8 @@ sedacs_status sedacs_create(int32_t n_atoms, const int32_t* species, const doubl
     if (!(box[a] > model->r_off)) return SEDACS_EINVAL;
   for (int i = 0; i < n_atoms; ++i)
     if (species[i] < 0 || species[i] > 2) return SEDACS_EINVAL;
-  if (params->precision < 0 || params->precision > 4 || params->core_size <= 0) return SEDACS_EINVAL;
+  if (params->precision < 0 || params->precision > 4 || params->core_size <= 0 || !(params->Te >= 0.0))
+    return SEDACS_EINVAL;
   sedacs_ctx* ctx = new sedacs_ctx();
   ctx->N = n_atoms;
   ctx->species_h.assign(species, species + n_atoms);
@@ -1258,6 +1637,7 @@ sedacs_status sedacs_create(int32_t n_atoms, const int32_t* species, const doubl
   const int sp2_fmt[5] = {3, kPlanesF16x2, 2, 1, 3};
   ctx->nsplit_sp2 = sp2_fmt[params->precision];
   ctx->nsplit_rsp = ctx->nsplit_sp2 == kPlanesF16x2 ? 3 : ctx->nsplit_sp2;
+  ctx->nsplit_fermi = ctx->nsplit_sp2;
   if (ctx->f64) ctx->nsplit_sp2 = 3;
   const int N = n_atoms;
   auto fail = [&](sedacs_status st, const char* msg) {
@@ -1276,6 +1656,7 @@ sedacs_status sedacs_create(int32_t n_atoms, const int32_t* species, const doubl
   if (cudaMalloc(&ctx->d_vel, sizeof(double) * 3 * N) != cudaSuccess) return fail(SEDACS_ENOMEM, "alloc");
   if (cudaMalloc(&ctx->d_hist, sizeof(double) * 6 * N) != cudaSuccess) return fail(SEDACS_ENOMEM, "alloc");
   if (cudaMalloc(&ctx->d_vec, sizeof(double) * 24 * N) != cudaSuccess) return fail(SEDACS_ENOMEM, "alloc");
+  if (cudaMalloc(&ctx->d_rsp, sizeof(double) * 8 * N) != cudaSuccess) return fail(SEDACS_ENOMEM, "alloc");
   if (cudaMalloc(&ctx->d_scal, sizeof(double) * 16) != cudaSuccess) return fail(SEDACS_ENOMEM, "alloc");
   if (cudaMalloc(&ctx->d_species, sizeof(int) * N) != cudaSuccess) return fail(SEDACS_ENOMEM, "alloc");
   cudaMemcpy(ctx->d_species, species, sizeof(int) * N, cudaMemcpyHostToDevice);
@@ -1306,7 +1687,7 @@ void sedacs_destroy(sedacs_ctx* ctx) {
                   ctx->d_views_x1, ctx->d_hoff, ctx->d_soff, ctx->d_dcoff, ctx->d_wcoff, ctx->d_rowbase,
                   ctx->d_tr_off, ctx->d_n_pad, ctx->d_n_real, ctx->d_n_diag, ctx->d_glo, ctx->d_ghi, ctx->d_bounds,
                   ctx->d_slots, ctx->d_sp2, ctx->d_nactive, ctx->d_dcoff_d, ctx->d_dqpop, ctx->d_dhoff,
-                  ctx->d_steps};
+                  ctx->d_steps, ctx->d_rsp, ctx->d_dcoff_t};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto* v : ctx->d_views)
@@ -1338,8 +1719,20 @@ sedacs_status sedacs_set_params(sedacs_ctx* ctx, const sedacs_params* p) {
     ctx->err = "precision, core_size and ewald_tol are fixed at creation";
     return SEDACS_EINVAL;
   }
+  if (!(p->Te >= 0.0)) { ctx->err = "Te must be >= 0"; return SEDACS_EINVAL; }
   if (p->ns_iters != ctx->prm.ns_iters) ctx->z_valid = false;
   ctx->prm = *p;
+  return SEDACS_OK;
+}
+
+sedacs_status sedacs_density_info(sedacs_ctx* ctx, double* info, int32_t n_info) {
+  if (!ctx || !info || n_info < 0) return SEDACS_EINVAL;
+  if (!ctx->have_density) { ctx->err = "no density"; return SEDACS_EINVAL; }
+  const double v[5] = {ctx->fermi_count_err, ctx->fermi_dndmu, ctx->fermi_dmu, (double)ctx->fermi_passes,
+                       (double)ctx->fermi_n};
+  for (int k = 0; k < std::min(5, (int)n_info); ++k) info[k] = v[k];
+  for (int k = 5; k < n_info; ++k)
+    info[k] = (k - 5) < (int)ctx->fermi_hist.size() ? ctx->fermi_hist[k - 5] : 0.0;
   return SEDACS_OK;
 }
 
@@ -1476,7 +1869,7 @@ sedacs_status sedacs_subgraph_density(sedacs_ctx* ctx, const double* R, const do
   }
   STCHK(copy_in(ctx, ctx->d_n, n, ctx->N));
   double m = *mu;
-  STCHK(density_core(ctx, &m, std::isnan(*mu)));
+  STCHK(density_core(ctx, &m));
   *mu = m;
   STCHK(copy_out(ctx, q, ctx->d_q, sizeof(double) * ctx->N));
   if (e_band) *e_band = ctx->e_band;
@@ -1525,6 +1918,10 @@ sedacs_status sedacs_subgraph_matrix(sedacs_ctx* ctx, int32_t part, int32_t whic
   if (n) *n = nr;
   if (n_core_orb) *n_core_orb = nc;
   if (!out) return SEDACS_OK;
+  if ((which == 0 || which == 3) && ctx->ht_stale) {
+    ctx->err = "h and h~ were overwritten by a response call; run a density call first";
+    return SEDACS_EINVAL;
+  }
   int sl = kH;
   switch (which) {
     case 0: sl = kH; break;
@@ -1557,25 +1954,11 @@ sedacs_status sedacs_scc_step(sedacs_ctx* ctx, const double* R, double* n, int32
   double m = *mu, r = 0.0;
   int it = 0;
   cudaStream_t s = ctx->stream;
-  // mu is placed in the gap once and kept while the count stays in its window; as the charges
-  // move the levels, a kept mu can end up next to a band edge where occupations flicker and the
-  // iteration stalls.  When the residual has not fallen by 10 % over 8 iterations, mu is placed
-  // in the middle of the current gap again.
-  double r_best = std::numeric_limits<double>::infinity();
-  int stalled = 0;
   for (it = 1; it <= max_iter; ++it) {
     STCHK(cycle(ctx, &m, it > 1));
     maxdiff_kernel<<<1, 1024, 0, s>>>(ctx->d_q, ctx->d_n, ctx->N, ctx->d_scal + 4);
     r = host_scalar(ctx, ctx->d_scal + 4);
     if (r <= ctx->prm.scc_tol) break;
-    if (r < 0.9 * r_best) {
-      r_best = r;
-      stalled = 0;
-    } else if (++stalled >= 8) {
-      STCHK(solve_mu(ctx, &m));
-      stalled = 0;
-      r_best = std::numeric_limits<double>::infinity();
-    }
     if (ctx->prm.kernel >= 1 && r < 0.1) {
       // quasi-Newton step n <- n - K (q - n) with the rank-m Krylov kernel (K0 J)^-1 K0 or the
       // learned one (SI Sec. C)
@@ -1610,6 +1993,7 @@ sedacs_status sedacs_xlbomd_init(sedacs_ctx* ctx, const double* R, const double*
   STCHK(copy_in(ctx, ctx->d_n, n0, ctx->N));
   fill_hist_kernel<<<nblk(ctx->N, 128), 128, 0, ctx->stream>>>(ctx->d_hist, ctx->d_n, ctx->N);
   ctx->hist_head = 0;
+  ctx->mu_prev = std::numeric_limits<double>::quiet_NaN();
   double m = mu;
   ctx->fuse_forces = true;
   const sedacs_status st = cycle(ctx, &m);
@@ -1662,11 +2046,14 @@ sedacs_status sedacs_xlbomd_step(sedacs_ctx* ctx, double* R, double* V, int32_t 
     ctx->launches += 8;
     ctx->geom_valid = false;
     phase_end(ctx, 0, 7);
-    double m = ctx->mu;
+    // mu predicted by linear extrapolation over the last two steps, then solved (Eq. 2)
+    const double mu_now = ctx->mu;
+    double m = std::isfinite(ctx->mu_prev) ? 2.0 * mu_now - ctx->mu_prev : mu_now;
     ctx->fuse_forces = true;
     const sedacs_status st = cycle(ctx, &m);
     ctx->fuse_forces = false;
     STCHK(st);
+    ctx->mu_prev = mu_now;
     STCHK(forces_core(ctx));
     kick_kernel<<<nblk(3 * N, 256), 256, 0, s>>>(ctx->d_vel, ctx->d_F, ctx->d_mass, 0.5 * dt_fs * kAccHaAAmu, N);
     kin_kernel<<<1, 1024, 0, s>>>(ctx->d_vel, ctx->d_mass, N, ctx->d_scal + 5);
@@ -1874,7 +2261,7 @@ sedacs_status sedacs_kernel_stats(sedacs_ctx* ctx, int32_t on, double* sp2_ms, i
                                   double* sp2_flops) {
   if (!ctx) return SEDACS_EINVAL;
   if (on && ctx->kev.empty()) {
-    ctx->kev.resize(512);
+    ctx->kev.resize(4096);
     for (auto& e : ctx->kev) cudaEventCreate(&e);
   }
   ctx->kstats = on != 0;

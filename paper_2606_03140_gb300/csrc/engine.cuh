@@ -3,6 +3,7 @@
 #pragma once
 #include <string>
 #include <tuple>
+#include <limits>
 #include <vector>
 
 #include "../../include/sedacs.h"
@@ -30,6 +31,7 @@ enum SlotId : int {
   kS = 0, kH, kT, kY0, kY1, kZ0, kZ1, kP, kHt, kX, kT1, kDc, kT2, kWc,
   kR1, kR2,            // response: X dX, and dX (ping-pong)
   kdH, kdHt, kdT1, kdDc,
+  kdT2, kdDt,          // core rows of t = s (I - 2F) (second-order mu term): Z_c t, 2 Z_c t Z
   kNumSlots
 };
 
@@ -37,8 +39,9 @@ struct GemmOp {
   GemmMat* mats_d = nullptr;
   GemmWork* work_d = nullptr;
   int n_work = 0;
-  float alpha = 1.f, beta = 0.f, g1 = 0.f, g2 = 0.f;
+  double alpha = 1.0, beta = 0.0, g1 = 0.0, g2 = 0.0;
   int mode = kModeGeneric;
+  bool sym = false;          // symmetric output: upper tiles only (counted as n^3 flops)
 };
 
 enum OpId : int {
@@ -51,6 +54,16 @@ enum OpId : int {
   OP_RSP_A, OP_RSP_B, OP_DP0, OP_DP1, OP_DHT0, OP_DHT1, OP_DT1_0, OP_DT1_1, OP_DDC0, OP_DDC1,
   // Z = s^-1/2 by the degree-6 Taylor polynomial of (I + E)^-1/2 (Paterson-Stockmeyer)
   OP_TE2, OP_TE3, OP_TZ,
+  // finite-temperature Fermi operator (engine.cu, run_fermi): start U0 = tanh(z) = z q(z^2)
+  // (Z2 = z z, Z4 = Z2 Z2, Horner in Z4), doublings U <- 2 U r(U^2) (V = U U, V2 = V V, Horner
+  // in V2), the last doubling writing F = (I + U) / 2, and s = F - F^2
+  OP_F_Z2, OP_F_Z4, OP_F_ST1, OP_F_SH0, OP_F_SH1, OP_F_SH2, OP_F_SH3, OP_F_U0_0, OP_F_U0_1,
+  OP_F_V_0, OP_F_V_1, OP_F_V2, OP_F_IT1, OP_F_IH0, OP_F_IH1, OP_F_IH2, OP_F_IH3, OP_F_IH4, OP_F_IH5,
+  OP_F_UP_0, OP_F_UP_1, OP_F_FIN, OP_F_S,
+  // core rows of F into the response slots (dT1 = Z_c F), and W of s: T2 = dT1 h~, Ws = 2 T2 Z
+  OP_F_FT1_0, OP_F_FT1_1, OP_F_T2S, OP_F_WS0, OP_F_WS1,
+  // second-order mu term: t = s - 2 s F (kR1 copy 1), its core rows (kdT2, kdDt), T2 = kdT2 h~
+  OP_F_T, OP_F_TT1_0, OP_F_TT1_1, OP_F_DT0, OP_F_DT1, OP_F_T2T,
   OP_NUM
 };
 
@@ -102,6 +115,20 @@ struct sedacs_ctx {
   int nsplit_sp2 = 3, nsplit_ns = 3;
   int nsplit_rsp = 3;    // plane format of the first-order SP2 replay (X and dX): fp16 two-plane
                          // SP2 forms replay in three bf16 planes (dX can exceed the fp16 range)
+  int nsplit_fermi = 3;  // plane format of the finite-temperature Fermi recursion's products
+  // finite-temperature Fermi operator: degrees of its two polynomials (kTanh*, kInv*), the
+  // tanh doublings of the last pass, and the diagnostics of the last density call
+  int fermi_j = 3, fermi_m = 4;   // Horner lengths (start: Z4 steps; inverse: V2 steps)
+  int fermi_n = 0;                // doublings of the last pass
+  double fermi_count_err = 0.0;   // collected count minus N_e after the mu solve
+  double fermi_dndmu = 0.0;       // dN/dmu at the accepted pass (e / Ha)
+  double fermi_dmu = 0.0;         // mu step applied (to second order) after the accepted pass
+  double mu_prev = std::numeric_limits<double>::quiet_NaN();   // mu of the MD step before (predictor)
+  int fermi_passes = 0;           // Fermi-operator passes of the last density call
+  std::vector<double> fermi_hist; // per pass: mu, N_e - N(mu), dN/dmu
+  double sum_n3 = 0.0;            // sum over subgraphs of n_real^3 (flops of one symmetric product)
+  bool ht_stale = false;          // h, h~ of the arena hold a perturbed state (response passes)
+  double* d_rsp = nullptr;        // 8 N-vectors of the finite-difference response
   // device vectors
   int* d_err = nullptr;
   int* d_species = nullptr;
@@ -160,6 +187,7 @@ struct sedacs_ctx {
   sedacs::Sp2State* d_sp2 = nullptr;
   int* d_nactive = nullptr;
   long long* d_dcoff_d = nullptr;   // core-row offsets of the response density
+  long long* d_dcoff_t = nullptr;   // core-row offsets of the second-order mu term (kdDt)
   double* d_dqpop = nullptr;        // response populations scratch
   long long* d_dhoff = nullptr;     // per-subgraph offsets of the response Hamiltonian
   int* d_steps = nullptr;           // SP2 step counts of the last density call

@@ -12,18 +12,18 @@ from . import sedacs as S
 
 
 class NoGroundState(RuntimeError):
-    """The zero-temperature SCC did not reach the ground state."""
+    """The SCC did not reach the ground state."""
 
 
 def ground_state(workload: str, precision: int, seed_v: int = 20260703, quick: bool = False,
                  core_size: int = 32):
-    """SCC ground state, mu in the gap and Maxwell-Boltzmann velocities at 300 K.
+    """SCC ground state (mu from Eq. 2 at 300 K) and Maxwell-Boltzmann velocities at 300 K.
 
     Returns (system, model, ctx, R, V, n, info) with ctx ready for sedacs_xlbomd_init (kernel
     K0).  The ground state comes from the kernel-accelerated quasi-Newton SCC (SI Sec. C, rank-4
     Krylov) in the three-plane bf16 form (precision 4, 24-bit products); a context of the
-    requested form (FP64 plain, or the two-plane fp16 SP2 form 1) then receives its charges, mu
-    and density graph, so all forms start from the same state.
+    requested form (FP64 plain, or form 1) then receives its charges, mu and density graph, so
+    all forms start from the same state.
     quick=True starts from zero charges (same per-step work, no SCC)."""
     s = I.workload(workload)
     model = I.default_model()
@@ -42,14 +42,10 @@ def ground_state(workload: str, precision: int, seed_v: int = 20260703, quick: b
         mu, _, _, _ = S.sedacs_subgraph_density(ctx, R, n)
         S.sedacs_graph_build(ctx, R, use_prev_D=True)
     else:
-        mu, res, it, ok = S.sedacs_scc_step(ctx, R, n, max_iter=60)
-        # place mu in the middle of the gap of the final graph, then settle the charges again
-        mu, q, _, _ = S.sedacs_subgraph_density(ctx, R, n)
-        mu, res2, it2, ok2 = S.sedacs_scc_step(ctx, R, n, max_iter=30, mu=mu)
-        if not (res2 < 1e-3):
+        mu, res2, it, ok = S.sedacs_scc_step(ctx, R, n, max_iter=60)
+        if not ok:
             S.sedacs_destroy(ctx)
-            raise NoGroundState(f"{workload}: SCC ground state not reached (max residual {res2}); the "
-                                "zero-temperature SCC does not converge for this workload")
+            raise NoGroundState(f"{workload}: SCC ground state not reached (max residual {res2})")
     if precision != scc_precision:
         gd = S.sedacs_density_graph_get(ctx, s.n_atoms)
         S.sedacs_destroy(ctx)
@@ -61,4 +57,4 @@ def ground_state(workload: str, precision: int, seed_v: int = 20260703, quick: b
     prm.kernel = 0
     S.sedacs_set_params(ctx, prm)
     S.sedacs_xlbomd_init(ctx, R, V, n, mu)
-    return s, model, ctx, R, V, n, {"scc_iters": it + it2, "scc_resid": res2, "mu": mu}
+    return s, model, ctx, R, V, n, {"scc_iters": it, "scc_resid": res2, "mu": mu}

@@ -37,7 +37,8 @@ class sedacs_params(C.Structure):
                 ("kernel", C.c_int32), ("krylov_rank", C.c_int32), ("krylov_tol", C.c_double),
                 ("c_k0", C.c_double), ("scc_tol", C.c_double), ("scc_alpha", C.c_double),
                 ("sp2_tol", C.c_double), ("sp2_kmax", C.c_int32), ("ns_iters", C.c_int32),
-                ("ewald_tol", C.c_double), ("judge_every", C.c_int32), ("judge_tol", C.c_double)]
+                ("ewald_tol", C.c_double), ("judge_every", C.c_int32), ("judge_tol", C.c_double),
+                ("Te", C.c_double), ("mu_given", C.c_int32), ("fermi_lin", C.c_double)]
 
 
 def _load():
@@ -84,6 +85,7 @@ def _load():
         "sedacs_gnn_collect": (I32, [P, I32, I32]),
         "sedacs_gnn_train": (I32, [P, P, P, I32, I32, D, P, P]),
         "sedacs_kernel_judge": (I32, [P, P, P]),
+        "sedacs_density_info": (I32, [P, P, I32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -102,7 +104,7 @@ EXPORTED = (
     "sedacs_xlbomd_init", "sedacs_xlbomd_step", "sedacs_phase_times", "sedacs_reset_counters",
     "sedacs_kernel_stats", "sedacs_set_params", "sedacs_graph_build_noalloc", "sedacs_gnn_num_params",
     "sedacs_gnn_init", "sedacs_gnn_set_params", "sedacs_gnn_get_params", "sedacs_gnn_apply", "sedacs_gnn_param_grad",
-    "sedacs_gnn_collect", "sedacs_gnn_train", "sedacs_kernel_judge",
+    "sedacs_gnn_collect", "sedacs_gnn_train", "sedacs_kernel_judge", "sedacs_density_info",
 )
 
 
@@ -314,8 +316,18 @@ def sedacs_reset_counters(ctx):
     _check(ctx, _lib.sedacs_reset_counters(ctx))
 
 
+def sedacs_density_info(ctx) -> dict:
+    """Diagnostics of the last density call (Te > 0)."""
+    v = np.zeros(5 + 3 * 16)
+    _check(ctx, _lib.sedacs_density_info(ctx, _ptr(v), len(v)))
+    npass = int(v[3])
+    return {"count_err": float(v[0]), "dn_dmu": float(v[1]), "dmu_linear": float(v[2]),
+            "passes": npass, "doublings": int(v[4]),
+            "history": [tuple(float(x) for x in v[5 + 3 * k:8 + 3 * k]) for k in range(min(npass, 16))]}
+
+
 def sedacs_kernel_stats(ctx, on: bool = True):
-    """(SP2 kernel ms, launches, algorithmic multiply-add pairs) since the last reset."""
+    """(Fermi-operator product ms, launches, algorithmic flops: n^3 per symmetric product) since the last reset."""
     ms = C.c_double()
     nl = C.c_int64()
     fl = C.c_double()

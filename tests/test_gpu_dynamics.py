@@ -1,9 +1,11 @@
 """SCC and XL-BOMD through the C ABI against the oracle on the 96-atom water box.
 
-FP64 plain form: the self-consistent charges (kernel quasi-Newton, graph rebuilt every
-iteration) and a 10-step shadow-dynamics trajectory from the oracle's ground state must agree
-with the oracle to round-off.  FP32-class form: the SCC reaches its arithmetic noise floor and
-its charges agree with the oracle's within the 1e-5 e bound.
+Both sides solve Eq. 2 for mu at 300 K in every density call.  FP64 plain form: the
+self-consistent charges (kernel quasi-Newton, graph rebuilt every iteration) and a 10-step
+shadow-dynamics trajectory from the oracle's ground state must agree with the oracle to
+round-off.  FP32-class form (the benchmarked form 1): the SCC reaches its arithmetic noise floor
+and its charges agree with the oracle's within the 1e-5 e bound, and its 10-step trajectory
+keeps charges within 1e-5 e and energies within 1e-5 Ha per atom of the oracle's.
 """
 import numpy as np
 import pytest
@@ -50,13 +52,14 @@ def test_scc_matches_oracle(ground, precision, tol):
         S.sedacs_destroy(ctx)
 
 
-def test_xlbomd_trajectory_matches_oracle(ground):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_xlbomd_trajectory_matches_oracle(ground, precision):
     from paper_2606_03140_gb300 import sedacs as S
 
     s, m, gp, n0, res = ground
     V0 = I.maxwell_boltzmann(s.species, 300.0, 9, m)
     ref = odyn.xlbomd(s.R, V0, s.species, s.box, m, gp, 10, 0.25, n0=n0, gd=res.gd)
-    ctx, R = _ctx(S, s, m, 0, 0)
+    ctx, R = _ctx(S, s, m, precision, 0)
     try:
         # the oracle's ground state (charges and density graph) is the shared starting point
         S.sedacs_graph_build(ctx, R, gd=res.gd)
@@ -67,10 +70,12 @@ def test_xlbomd_trajectory_matches_oracle(ground):
         E = S.sedacs_xlbomd_step(ctx, R, V, 10, 0.25, n_out=nout)
     finally:
         S.sedacs_destroy(ctx)
-    # the GPU's FP64 SP2 stops at Tr(X - X^2) < 1e-9 n, the oracle diagonalises exactly:
-    # agreement at that level (1e-8 Ha per atom)
-    print(f"[parity] water96 XL-BOMD 10 steps, FP64: max|dE_tot| = {np.max(np.abs(E[:, 2] - ref['energies'][1:, 2])):.3e} Ha, "
-          f"max|dR| = {np.max(np.abs(R - ref['R'])):.3e} A, max|dn| = {np.max(np.abs(nout - ref['n'])):.3e} e")
-    assert np.max(np.abs(E[:, 2] - ref["energies"][1:, 2])) < 1e-6
-    assert np.max(np.abs(R - ref["R"])) < 1e-8
-    assert np.max(np.abs(nout - ref["n"])) < 1e-7
+    dE = np.max(np.abs(E[:, 2] - ref["energies"][1:, 2]))
+    dR = np.max(np.abs(R - ref["R"]))
+    dn = np.max(np.abs(nout - ref["n"]))
+    print(f"[parity] water96 XL-BOMD 10 steps, form {precision}: max|dE_tot| = {dE:.3e} Ha "
+          f"({dE / 96:.2e} Ha/atom), max|dR| = {dR:.3e} A, max|dn| = {dn:.3e} e")
+    if precision == 0:
+        assert dE < 1e-6 and dR < 1e-8 and dn < 1e-7
+    else:
+        assert dE / 96 < 1e-5 and dn < 1e-5 and dR < 1e-5

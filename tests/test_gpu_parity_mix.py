@@ -1,7 +1,8 @@
 """Parity on the 9,999-atom methanol/water mixture (1:1, 0.9 g/cm3) in the mixed form: graph,
 cores and halos bit for bit on the whole system, charges of sampled subgraphs (C/O sp and H s
 orbitals) within the 1e-5 e bound, at zero trial charges and one chemical potential in a clean
-window of the sampled spectra (the oracle solves the sampled subgraphs one by one)."""
+window of the sampled spectra, given to both sides (Fermi occupations at 300 K; the oracle solves
+the sampled subgraphs one by one)."""
 import numpy as np
 import pytest
 
@@ -32,7 +33,7 @@ def test_mixture_graph_and_sampled_charges():
     ref = odn.density(s.R, s.species, s.box, m, np.zeros(s.n_atoms), [cores[i] for i in PICK],
                       [hal[i] for i in PICK], mu=mu, V=np.zeros(s.n_atoms))
     R = np.ascontiguousarray(s.R)
-    ctx = S.sedacs_create(s.species, s.box, m, S.sedacs_default_params(core_size=32, precision=1))
+    ctx = S.sedacs_create(s.species, s.box, m, S.sedacs_default_params(core_size=32, precision=1, mu_given=1))
     try:
         nnz = S.sedacs_graph_build(ctx, R)
         rp, col = S.sedacs_graph_get(ctx, s.n_atoms, nnz)

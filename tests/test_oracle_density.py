@@ -186,3 +186,19 @@ def test_forces_equal_finite_difference_of_shadow_energy(w96, full96):
         Rm = s.R.copy(); Rm[A, c] -= h
         assert abs(F[A, c] + (U(Rp) - U(Rm)) / (2 * h)) < 1e-6
     assert np.max(np.abs(F.sum(axis=0))) < 1e-9      # no net force
+
+
+def test_subset_rows_equal_full_rows(w96, trunc96):
+    """The row-restricted forms of forces, Coulomb potential and gradient, and repulsion give the
+    full computation's rows for the chosen atoms."""
+    s, m, n = w96
+    r, _, _ = trunc96
+    pick = np.array([0, 5, 41, 77, 95])
+    F = dn.forces(r, n, s.R, s.species, s.box, m)
+    Fs = dn.forces(r, n, s.R, s.species, s.box, m, atoms=pick)
+    assert np.max(np.abs(Fs[pick] - F[pick])) < 1e-13
+    assert np.all(Fs[np.setdiff1d(np.arange(96), pick)] == 0.0)
+    from oracle import ewald
+    V = ewald.coulomb_potential(s.R, s.species, m.hubbard_u, s.box, n)
+    Vs = ewald.coulomb_potential(s.R, s.species, m.hubbard_u, s.box, n, rows=pick)
+    assert np.max(np.abs(Vs[pick] - V[pick])) < 1e-13
