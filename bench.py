@@ -3,8 +3,9 @@
 Workload: the 9,000-atom water box (3,000 H2O, 44.8 A, seeded synthetic geometry, synthetic
 sp SCC-TB model) -- cores of ~32 atoms, halos from the distance + |D| > 1e-3 graph,
 Maxwell-Boltzmann velocities at 300 K, dt = 0.25 fs.  A step is one full QMD step: graph
-rebuild from the previous density, halos, Coulomb (Ewald), H/S gather, S^-1/2, h~, SP2 Fermi
-operator, core rows, charges, energies, forces, kernel K(q - n), charge and Verlet updates.
+rebuild from the previous density, halos, Coulomb (Ewald), H/S gather, S^-1/2, h~, the Fermi
+operator at 300 K (tanh-doubling recursion on tcgen05) with mu solved from Eq. 2, core rows,
+charges, energies, forces, kernel K(q - n), charge and Verlet updates.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--precision 1] [--workload water9000]
@@ -38,11 +39,13 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", type=int, default=1, choices=[0, 1, 2, 3, 4],
-                    help="0 plain FP64; 1 FP32-class (SP2 squares in two fp16 planes, other products "
-                         "three-way bf16); 4 FP32-class three-way bf16 throughout; 2, 3 diagnostics")
+                    help="0 plain FP64; 1 FP32-class (Fermi-recursion products in two fp16 planes, other "
+                         "products three-way bf16); 4 FP32-class three-way bf16 throughout; 2, 3 diagnostics")
     ap.add_argument("--workload", default="water9000")
     ap.add_argument("--dt", type=float, default=0.25)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 sub-record")
+    ap.add_argument("--no-frames", action="store_true", help="skip the oracle check of sampled frames")
     ap.add_argument("--profile-case", action="store_true",
                     help="small ncu case: 3,000-atom water box, two densities, the second inside NVTX range 'second'")
     ap.add_argument("--quick-setup", action="store_true",
@@ -53,12 +56,11 @@ def parse():
 
 METRIC = "atoms*QMD-steps/s at |dq|<=1e-5 e vs FP64 oracle (mixed vs plain, one GB300)"
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the SP2 square kernel, averaged
-# over the SP2 launches of 2 timed steps of the 9,000-atom water workload in the mixed form (one
-# ncu capture, profiles/tc_gemm_sp2_traffic_water9000.md).  Reported only while the kernel
-# source is the one the counters were taken on.
-SP2_TRAFFIC = {"bytes_per_launch": 182.9e6, "workload": "water9000", "precision": 1,
-               "kernel_sha1": "5b91c84eede22b3ba5e372166adf3648e1512de0"}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the Fermi-recursion
+# product kernel (tc_gemm_persistent<2, true>) on the small capture case (bench.py --profile-case,
+# 3,000-atom water box), scaled to the 9,000-atom workload by the ratio of the subgraphs' padded
+# sizes; reported only while the kernel source is the one the counters were taken on.
+FERMI_TRAFFIC = None
 
 
 def strip_comments(src: str) -> str:
@@ -85,7 +87,7 @@ def strip_comments(src: str) -> str:
 
 
 def kernel_sha1() -> str:
-    """sha1 of the SP2 kernel's source (dense_gemm.cu, dense.cuh, common.cuh), comments stripped."""
+    """sha1 of the GEMM kernel's source (dense_gemm.cu, dense.cuh, common.cuh), comments stripped."""
     import hashlib
     h = hashlib.sha1()
     for f in ("dense_gemm.cu", "dense.cuh", "common.cuh"):
@@ -206,6 +208,50 @@ def setup_system(S, I, workload: str, precision: int, seed_v: int = 20260703, qu
         raise SystemExit(f"{e}; it is not an MD benchmark")
 
 
+def frame_check(S, ctx, R, n, q, mu, picks, model, species, box):
+    """Charges of sampled subgraphs at one frame, recomputed by the FP64 oracle from the GPU's
+    positions R, charges n, chemical potential mu and subgraph lists (the Coulomb potential only
+    at the sampled atoms, its sums over every atom).  Returns max |q_gpu - q_oracle| there."""
+    from oracle import density as odn
+    from oracle import ewald as oew
+
+    sp, sa, nc = S.sedacs_parts_get(ctx)
+    cores = [sa[sp[i]:sp[i] + nc[i]] for i in picks]
+    halos = [sa[sp[i] + nc[i]:sp[i + 1]] for i in picks]
+    atoms = np.unique(np.concatenate([sa[sp[i]:sp[i + 1]] for i in picks]))
+    V = oew.coulomb_potential(R, species, model.hubbard_u, box, n, rows=atoms)
+    ref = odn.density(R, species, box, model, n, cores, halos, mu=mu, V=V)
+    a = np.concatenate(cores)
+    d = np.abs(q[a] - ref.q[a])
+    return float(np.max(d)), float(np.sqrt(np.mean(d ** 2))), int(np.sum(d > 1e-5)), int(d.shape[0])
+
+
+def run_plain(args, S, model, s, R0, V0, n0, mu0, gd, steps: int = 2):
+    """The plain FP64 form from the same ground state: charges at the start (against the mixed
+    form's) and the device-timed step."""
+    import torch
+
+    N = s.n_atoms
+    prm = S.sedacs_default_params(core_size=32, precision=0)
+    ctx = S.sedacs_create(s.species, s.box, model, prm)
+    try:
+        R = np.ascontiguousarray(R0.copy())
+        V = np.ascontiguousarray(V0.copy())
+        S.sedacs_graph_build(ctx, R, gd=gd)
+        S.sedacs_partition(ctx, R)
+        S.sedacs_xlbomd_init(ctx, R, V, np.ascontiguousarray(n0), mu0)
+        q0 = S.sedacs_charges(ctx, N)
+        S.sedacs_xlbomd_step(ctx, R, V, 1, args.dt)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S.sedacs_xlbomd_step(ctx, R, V, steps, args.dt)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / steps
+    finally:
+        S.sedacs_destroy(ctx)
+    return q0, dt
+
+
 def run_ours(args, world, rank, local):
     import torch
 
@@ -215,6 +261,9 @@ def run_ours(args, world, rank, local):
 
     s, model, ctx, R, V, n, info = setup_system(S, I, args.workload, args.precision, quick=args.quick_setup)
     N = s.n_atoms
+    R0, V0, n0, mu0 = R.copy(), V.copy(), n.copy(), info["mu"]
+    q_start = S.sedacs_charges(ctx, N)
+    gd0 = S.sedacs_density_graph_get(ctx, N)
     # warm-up (host I/O)
     S.sedacs_xlbomd_step(ctx, R, V, args.warmup, args.dt)
     # ---- device-resident timed region -------------------------------------------------
@@ -245,78 +294,130 @@ def run_ours(args, world, rank, local):
     S.sedacs_set_device_io(ctx, False, 0)
     E = Ed.cpu().numpy()
     # ---- end to end through the public call with host buffers ----------------------------
+    # (frames of this run are kept for the oracle check: positions, charges, density, mu)
     Rh = Rd.cpu().numpy().copy()
     Vh = Vd.cpu().numpy().copy()
     Eh = np.zeros((1, 3))
+    nh = np.zeros(N)
+    keep = sorted({0, args.steps // 2, args.steps - 1})
+    frames, evals = [], []
     torch.cuda.synchronize()
     barrier(world)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        S.sedacs_xlbomd_step(ctx, Rh, Vh, 1, args.dt, Eh)
+    t_e2e = 0.0
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        S.sedacs_xlbomd_step(ctx, Rh, Vh, 1, args.dt, Eh, nh)
+        t_e2e += time.perf_counter() - t0
+        dinf = S.sedacs_density_info(ctx)
+        evals.append((dinf["passes"], dinf["reentries"]))
+        if k in keep and rank == 0 and not args.no_frames:
+            mu_k = dinf["history"][-1][0] + dinf["dmu_linear"]
+            frames.append((k, Rh.copy(), nh.copy(), S.sedacs_charges(ctx, N), mu_k))
     torch.cuda.synchronize()
-    t_e2e = allmax(world, time.perf_counter() - t0)
-    # roofline of the SP2 square kernel from a separate pass with per-launch CUDA events (kept
-    # out of the timed region: the events and the per-density readback of the step counts
-    # would slow it down)
+    t_e2e = allmax(world, t_e2e)
+    # roofline of the Fermi-operator products from a separate pass with per-launch CUDA events
+    # (kept out of the timed region: the events read back after every density)
+    S.sedacs_kernel_stats(ctx, True)
+    S.sedacs_reset_counters(ctx)
     S.sedacs_kernel_stats(ctx, True)
     S.sedacs_xlbomd_step(ctx, Rh, Vh, 4, args.dt)
-    k_ms, k_launch, k_pairs = S.sedacs_kernel_stats(ctx, False)
+    k_ms, k_launch, k_flops = S.sedacs_kernel_stats(ctx, False)
+    ph4, _ = S.sedacs_phase_times(ctx)
+    # oracle check of sampled subgraphs at the kept frames
+    acc = None
+    if frames:
+        picks = [0, 97, 180, 280]
+        nsub = S.sedacs_parts_get(ctx)[2].shape[0]
+        picks = [p for p in picks if p < nsub]
+        t0 = time.perf_counter()
+        res = [frame_check(S, ctx, Rf, nf, qf, muf, picks, model, s.species, s.box) for (_, Rf, nf, qf, muf) in frames]
+        errs = [r[0] for r in res]
+        acc = {"max_dq_vs_oracle": max(errs), "rms_dq_vs_oracle": float(np.sqrt(np.mean([r[1] ** 2 for r in res]))),
+               "atoms_above_1e-5": sum(r[2] for r in res), "atoms_checked": sum(r[3] for r in res),
+               "per_frame": {str(k): r[0] for (k, *_), r in zip(frames, res)},
+               "sampled_subgraphs": picks, "oracle_seconds": round(time.perf_counter() - t0, 1),
+               "how": "FP64 oracle on the sampled subgraphs from the GPU's positions, charges n, mu and subgraph "
+                      "lists at steps " + ",".join(str(f[0]) for f in frames) + " of the e2e trajectory"}
     S.sedacs_destroy(ctx)
     value = world * N * args.steps / (ms / 1e3)
     e2e = world * N * args.steps / t_e2e
-    # roofline of the dominant kernel (SP2 squares on tcgen05): algorithmic FLOPs = 2 n^3 per
-    # symmetric square (n^3 multiply-add pairs); one FP32-class product = 3 fp16 tensor-core products
-    # (two-plane fp16 form 1) or 6 bf16 products (three-plane form 4); fp16 and bf16 run at one rate
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
     bf16 = peaks.get("bf16_tflops_sustained", 1700.0)
-    nsplit_products = {1: 3, 2: 3, 3: 1, 4: 6}.get(args.precision, 6)
-    achieved = (2.0 * k_pairs / max(k_launch, 1)) / (k_ms / max(k_launch, 1) / 1e3) / 1e12 if k_ms > 0 else None
-    peak = bf16 / nsplit_products
-    kname = ("tc_gemm_persistent (SP2 square, " + ("two-plane fp16" if args.precision == 1 else "split-bf16")
-             + " tcgen05)")
-    bound = "tensor"
-    peak_note = f"measured sustained bf16 {bf16} TF/s (= fp16 rate) / {nsplit_products} split products (of measured)"
+    peak_src = "of measured" if "bf16_tflops_sustained" in peaks else "of fallback"
+    split = {1: 3, 2: 3, 3: 1, 4: 6}.get(args.precision, 6)
+    # algorithmic work: a symmetric product of two n x n matrices (upper triangle) = n^3 flops
+    achieved = (k_flops / (k_ms / 1e3)) / 1e12 if k_ms > 0 else None
     if args.precision == 0:
-        # FP64 form: the SIMT FP64 GEMM on the CUDA cores; no measured FP64 peak, the nominal
-        # 1.25 TFLOP/s of the part (algorithmic flops count the full square, the kernel computes
-        # the upper tiles, so the fraction can exceed 1)
-        kname, bound, peak = "f64_gemm_kernel (SP2 square, FP64 CUDA cores)", "alu", 1.25
+        kname, bound, peak = "f64_gemm_kernel (Fermi-recursion products, FP64 CUDA cores)", "alu", 1.25
         peak_note = "nominal FP64 1.25 TF/s (no measured FP64 peak)"
-    roof = {"kernel": kname, "bound": bound,
-            "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": (achieved / peak) if achieved else None,
-            "traffic": (SP2_TRAFFIC["bytes_per_launch"]
-                        if (kernel_sha1() == SP2_TRAFFIC["kernel_sha1"] and args.workload == SP2_TRAFFIC["workload"]
-                            and args.precision == SP2_TRAFFIC["precision"]) else None),
-            "traffic_unit": "bytes per launch (DRAM read + write, ncu, average over the SP2 launches)",
-            "peak_note": peak_note,
-            "launches": k_launch, "kernel_ms": k_ms}
+    else:
+        kname = ("tc_gemm_persistent<2,F16> (Fermi-recursion products, two-plane fp16 on tcgen05)" if args.precision == 1
+                 else "tc_gemm_persistent (Fermi-recursion products, split bf16 on tcgen05)")
+        bound, peak = "tensor", bf16
+        peak_note = (f"measured sustained dense bf16 {bf16} TF/s {peak_src} (fp16 runs at the bf16 rate); the "
+                     f"FP32-class product costs {split} tensor-core products, counted as work of the kernel, not "
+                     f"of the method")
+    traffic = None
+    if FERMI_TRAFFIC and kernel_sha1() == FERMI_TRAFFIC["kernel_sha1"] and args.precision == FERMI_TRAFFIC["precision"] \
+            and args.workload == FERMI_TRAFFIC["workload"]:
+        traffic = FERMI_TRAFFIC["bytes_per_launch"]
+    roof = {"kernel": kname, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+            "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
+            "split_products": split, "tensor_frac_with_split_products": (achieved * split / peak) if achieved else None,
+            "peak_note": peak_note, "launches": k_launch, "kernel_ms": k_ms,
+            "work_note": "flops = sum over launches of sum_i n_i^3 (one symmetric product per subgraph, upper "
+                         "triangle, n_i the orbital count)"}
+    plain = None
+    if not args.no_plain and args.precision != 0 and rank == 0:
+        q64, t64 = run_plain(args, S, model, s, R0, V0, n0, mu0, gd0)
+        dq_mp = float(np.max(np.abs(q64 - q_start)))
+        plain = {"precision": 0, "ms_per_step": 1e3 * t64, "value": N / t64, "unit": UNIT,
+                 "mixed_vs_plain_max_dq": dq_mp,
+                 "mixed_vs_plain_rms_dq": float(np.sqrt(np.mean((q64 - q_start) ** 2))),
+                 "how": "same SCC ground state handed to an FP64 context; charges of its first density against the "
+                        "mixed form's; step time from 2 steps with host I/O (FP64 GEMMs on the CUDA cores)",
+                 "speedup_mixed_over_plain": (value / world) / (N / t64)}
     drift = float(E[-1, 2] - E[0, 2])
+    names = ["graph+halos", "coulomb", "gather", "Z+h~", "fermi(mu solve)", "collect", "forces", "kernel+update"]
     return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {1: "f32-class (SP2: 2-plane fp16 on tcgen05; other products 3-way bf16) / "
-                                          "f64 sums",
-                                       4: "f32 (3-way split bf16 on tcgen05) / f64 sums", 2: "bf16x2 split / f64 sums",
-                                       3: "bf16 / f64 sums", 0: "f64"}[args.precision],
+        "vs_baseline": None,
+        "dtype": {1: "f32-class (Fermi products: 2-plane fp16 on tcgen05; other products 3-way bf16) / f64 sums",
+                  4: "f32 (3-way split bf16 on tcgen05) / f64 sums", 2: "bf16x2 split / f64 sums",
+                  3: "bf16 / f64 sums", 0: "f64"}[args.precision],
         "data": "synthetic (seeded water box, synthetic sp SCC-TB model)",
-        "config": {"workload": f"{args.workload}: {N} atoms, cores~32, tau 1e-3, r_graph 3 A, XL-BOMD NVE 300 K, dt {args.dt} fs",
+        "config": {"workload": f"{args.workload}: {N} atoms, cores~32, tau 1e-3, r_graph 3 A, XL-BOMD NVE 300 K, "
+                               f"Te 300 K, dt {args.dt} fs",
                    "precision": args.precision, "parallelism": f"replicas x{world}",
                    "l2": "working set (per-subgraph arena, several GB) far exceeds the 129 MB L2; no flush needed",
                    "scc_iters_setup": info["scc_iters"], "scc_resid_setup": info["scc_resid"], "mu": info["mu"],
-                   "kernel": "K0 = -0.5 I"},
+                   "kernel": "K0 = -0.05 I (paper_2606_03140_gb300.runs.MD_C_K0)"},
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 2 * 3 * N * 8,
-                "d2h_bytes_per_step": 2 * 3 * N * 8 + 3 * 8},
+                "d2h_bytes_per_step": 2 * 3 * N * 8 + 3 * 8 + N * 8},
         "gpu_launches": int(launches),
-        "phase_ms_per_step": {k: round(float(v) / args.steps, 3) for k, v in zip(
-            ["graph+halos", "coulomb", "gather", "Z+h~", "sp2", "collect", "forces", "kernel+update"], phases)},
+        "phase_ms_per_step": {k: round(float(v) / args.steps, 3) for k, v in zip(names, phases)},
+        "mu_solve": {"fermi_evaluations_per_step": float(np.mean([e[0] for e in evals])) if evals else None,
+                     "of_which_stage_shifts": float(np.mean([e[1] for e in evals])) if evals else None},
+        "accuracy": acc, "plain_fp64": plain,
         "energy_drift_ha": drift, "energy_fluct_ha": float(E[:, 2].max() - E[:, 2].min()),
         "clocks": clocks, "roofline": roof,
+        "rooflines_other": phase_rooflines(ph4, 4, k_ms, bf16, peak_src, args.precision),
     }
+
+
+def phase_rooflines(ph, steps, fermi_ms, bf16, peak_src, precision):
+    """Per-phase times of the kernel-statistics pass, per step (the phases hold several kernels each;
+    the Fermi phase minus its product kernels is the mu-solve bookkeeping: counts, core rows)."""
+    names = ["graph+halos", "coulomb", "gather", "Z+h~", "fermi", "collect", "forces", "kernel+update"]
+    out = {k: {"ms_per_step": round(float(v) / steps, 3)} for k, v in zip(names, ph)}
+    out["fermi"]["product_kernels_ms_per_step"] = round(fermi_ms / steps, 3)
+    return out
 
 
 class OracleStep:
@@ -375,10 +476,11 @@ def cpu_baseline(args, sample: int = 8, steps: int = 1):
     t = float(np.median([r["t_step"] for r in recs]))
     r = recs[0]
     return {"value": ors.s.n_atoms / t, "unit": UNIT, "cores": _threads(), "kind": "oracle",
-            "sample": (f"full-box graph+RCB+halos ({r['t_graph']:.1f}s), full-box Ewald potential ({ors.t_ew:.1f}s, "
-                       f"counted x2 for potential+gradient), {r['picked']} of {r['P']} subgraphs solved "
-                       f"({r['t_sub']:.1f}s) and scaled to all; subgraph forces not included"),
-            "seconds_per_step": t}
+            "sample": (f"EXTRAPOLATED: full-box graph+RCB+halos ({r['t_graph']:.1f}s), full-box Ewald potential "
+                       f"({ors.t_ew:.1f}s, counted x2 for potential+gradient), {r['picked']} of {r['P']} subgraphs "
+                       f"solved ({r['t_sub']:.1f}s) and scaled to all; subgraph forces not included (an "
+                       f"underestimate of the oracle's step)"),
+            "extrapolated": True, "seconds_per_step": t}
 
 
 def run_reference(args, world, rank):
@@ -391,18 +493,21 @@ def run_reference(args, world, rank):
     t = float(np.median([r["t_step"] for r in recs]))
     v = ors.s.n_atoms / t
     cb = {"value": v, "unit": UNIT, "cores": _threads(), "kind": "oracle",
-          "sample": f"per step: full-box graph + {recs[0]['picked']} sampled subgraph solves scaled to {recs[0]['P']}, "
-                    f"plus 2 x full-box Ewald potential timed once ({ors.t_ew:.1f}s)"}
+          "sample": f"EXTRAPOLATED per step: full-box graph + {recs[0]['picked']} sampled subgraph solves scaled to "
+                    f"{recs[0]['P']}, plus 2 x full-box Ewald potential timed once ({ors.t_ew:.1f}s); forces "
+                    f"not included", "extrapolated": True}
     return {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": args.workload, "implementation": "FP64 oracle (numpy/scipy) on host cores"},
+            "config": {"workload": args.workload, "implementation": "FP64 oracle (numpy/scipy) on host cores",
+                       "extrapolated": "each step's time is a bounded sample scaled to the full step (see cpu_baseline)"},
             "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def profile_case(args):
     """Small case for kernel captures: 3,000-atom water box (1,000 H2O, 31 A), distance graph,
-    RCB cores, one density, graph rebuilt from it, a second density inside NVTX range 'second'."""
+    RCB cores, one density (mu solved), graph rebuilt from it, a second density (warm-started mu)
+    inside NVTX range 'second'."""
     import torch
 
     from paper_2606_03140_gb300 import inputs as I
@@ -415,13 +520,15 @@ def profile_case(args):
     S.sedacs_graph_build(ctx, R)
     P = S.sedacs_partition(ctx, R)
     n = np.zeros(s.n_atoms)
-    S.sedacs_subgraph_density(ctx, R, n, mu=-0.13, n_parts=P)
+    mu, _, _, _ = S.sedacs_subgraph_density(ctx, R, n, n_parts=P)
     S.sedacs_graph_build(ctx, R, use_prev_D=True)
     torch.cuda.nvtx.range_push("second")
-    _, q, _, it = S.sedacs_subgraph_density(ctx, R, n, mu=-0.13, n_parts=P)
+    _, q, _, it = S.sedacs_subgraph_density(ctx, R, n, mu=mu, n_parts=P)
     torch.cuda.nvtx.range_pop()
+    info = S.sedacs_density_info(ctx)
     S.sedacs_destroy(ctx)
-    print(json.dumps({"profile_case": "water3000", "subgraphs": P, "sp2_steps_mean": float(it.mean())}))
+    print(json.dumps({"profile_case": "water3000", "subgraphs": P, "doublings": info["doublings"],
+                      "fermi_evaluations": info["passes"]}))
 
 
 def main():

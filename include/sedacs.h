@@ -100,7 +100,7 @@ typedef struct {
                            dmu of its second-order expansion (D += beta dmu D_s + (beta dmu)^2 / 2 D_t,
                            with dF/dmu = beta (F - F^2) and d2F/dmu2 = beta^2 (F - F^2)(I - 2F)) when
                            |beta dmu| is at most this; otherwise another pass runs (0: 3e-2 in the
-                           FP32-class forms, 1.5e-3 in FP64) */
+                           FP32-class forms, 3e-4 in FP64) */
 } sedacs_params;
 
 /* Fill p with the defaults (r_graph 3.0, tau 1e-3, core_size 32, precision 1, kernel 0,
@@ -168,6 +168,9 @@ sedacs_status sedacs_coulomb_potential(sedacs_ctx* ctx, const double* R, const d
  * SP2 steps when Te = 0, else the tanh doublings of the last pass in every entry). */
 sedacs_status sedacs_subgraph_density(sedacs_ctx* ctx, const double* R, const double* n, double* mu, double* q,
                                       double* e_band, int32_t* sp2_iters);
+/* Net Mulliken charges q [N] (e) of the last density call (also after sedacs_xlbomd_step: the
+ * density of the last step's positions and charges n). */
+sedacs_status sedacs_charges(sedacs_ctx* ctx, double* q);
 /* Energies of the last density call: e[0] band Tr[D H0], e[1] Coulomb 1/2 (2q - n)^T gamma n,
  * e[2] repulsion, e[3] total shadow potential (Hartree). */
 sedacs_status sedacs_energy(sedacs_ctx* ctx, double* e);
@@ -240,8 +243,9 @@ sedacs_status sedacs_kernel_judge(sedacs_ctx* ctx, double* last_error, int32_t* 
 
 /* Diagnostics of the last density call (Te > 0): info[0] collected electron count minus N_e
  * after the mu solve, info[1] dN/dmu at the accepted pass (e/Ha), info[2] the linear mu step
- * applied after it (Ha), info[3] Fermi-operator passes, info[4] tanh doublings per pass, then per
- * pass the triple (mu, N_e - N(mu), dN/dmu) (zeros past the last pass).  n_info entries are written. */
+ * applied after it (Ha), info[3] Fermi-operator evaluations, info[4] tanh doublings per pass, info[5]
+ * evaluations that shifted mu at the stage kept by a full pass instead of running one, then per
+ * evaluation the triple (mu, N_e - N(mu), dN/dmu) (zeros past the last).  n_info entries are written. */
 sedacs_status sedacs_density_info(sedacs_ctx* ctx, double* info, int32_t n_info);
 
 /* Wall time (ms, CUDA events on the context stream) of the phases of the last call:

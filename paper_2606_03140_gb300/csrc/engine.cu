@@ -553,6 +553,11 @@ sedacs_status build_fermi_ops(sedacs_ctx* ctx) {
   STCHK(build_op(ctx, OP_F_DT0, kdT2, kZ0, kdDt, kModeGeneric, 2.0, 0.0, F, F, kdT2, 2.0));
   STCHK(build_op(ctx, OP_F_DT1, kdT2, kZ1, kdDt, kModeGeneric, 2.0, 0.0, F, F, kdT2, 2.0));
   STCHK(build_op(ctx, OP_F_T2T, kdT2, kHt, kT2, kModeGeneric, 1.0, 0.0, F));
+  // mu shift at a saved stage: U' = U Q + tau Q (U in kY0, Q = (I + tau U)^-1 in the Horner slot)
+  // into either copy of kX; tau is set in g1 at run time
+  for (int cu = 0; cu < 2; ++cu)
+    STCHK(build_op(ctx, OP_F_MOB_0 + cu, kY0, horner_slot(M), kX, kModeGeneric, 1.0, 0.0, F, F, horner_slot(M), 0.0,
+                   -1, 0.0, F, T, 0, 0, cu));
   return SEDACS_OK;
 }
 
@@ -1017,7 +1022,86 @@ void drain_kstats(sedacs_ctx* ctx, int ev0) {
   ctx->kev_used = ev0;
 }
 
-// One pass: F at (mu, beta) into kX copy 0, every buffer index pointing there.
+// Horner coefficients of sum_k c_k X^k (degree 2M + 1) on the ops of the inverse polynomial
+// (X in kY0, X^2 in kY1): T_1 = c_2M+1 X X^2 + c_2M X^2 + c_2M-1 X + c_2M-2 I, T_j = B_{M-j} + X^2 T_{j-1}.
+void set_horner(sedacs_ctx* ctx, const double* c) {
+  const int M = ctx->fermi_m;
+  GemmOp& t1 = ctx->ops[OP_F_IT1];
+  t1.alpha = c[2 * M + 1];
+  t1.beta = c[2 * M - 2];
+  t1.g1 = c[2 * M];
+  t1.g2 = c[2 * M - 1];
+  for (int j = 2; j <= M; ++j) {
+    GemmOp& o = ctx->ops[OP_F_IH0 + (j - 2)];
+    o.alpha = 1.0;
+    o.beta = c[2 * (M - j)];
+    o.g1 = c[2 * (M - j) + 1];
+    o.g2 = 0.0;
+  }
+}
+
+// Monomial coefficients c[0..d] of the degree-d interpolant of 1 / (1 + tau u) at the Chebyshev
+// points of [-1, 1] (|tau| < 1; the interpolation error falls like rho^-d with
+// rho = 1/|tau| + sqrt(1/tau^2 - 1)).
+void mobius_coeffs(double tau, int d, double* c) {
+  const int m = d + 1;
+  std::vector<double> a(m, 0.0);
+  for (int k = 0; k < m; ++k) {
+    double sum = 0.0;
+    for (int j = 0; j < m; ++j) {
+      const double th = M_PI * (j + 0.5) / m;
+      sum += std::cos(k * th) / (1.0 + tau * std::cos(th));
+    }
+    a[k] = (k == 0 ? 1.0 : 2.0) * sum / m;
+  }
+  // Chebyshev to monomial: T_0 = 1, T_1 = u, T_k+1 = 2 u T_k - T_k-1
+  std::vector<double> tkm(m, 0.0), tk(m, 0.0), tkp(m, 0.0);
+  for (int p = 0; p < m; ++p) c[p] = 0.0;
+  tkm[0] = 1.0;
+  c[0] += a[0];
+  if (m > 1) {
+    tk[1] = 1.0;
+    c[1] += a[1];
+  }
+  for (int k = 1; k + 1 < m; ++k) {
+    for (int p = 0; p < m; ++p) tkp[p] = (p > 0 ? 2.0 * tk[p - 1] : 0.0) - tkm[p];
+    for (int p = 0; p < m; ++p) c[p] += a[k + 1] * tkp[p];
+    tkm.swap(tk);
+    tk.swap(tkp);
+  }
+}
+
+// The doublings k0 .. nd-1 from U_k0 in kX copy cu; the last writes F = (I + U) / 2 into copy 0.
+// The stage js (0 <= js < nd; -1: none) is copied into kR2 copy 1 before its doubling.
+void fermi_doublings_from(sedacs_ctx* ctx, int k0, int nd, int cu, int js) {
+  const int nf = ctx->f64 ? 0 : ctx->nsplit_fermi;
+  for (int k = k0; k < nd; ++k) {
+    if (k == js) {
+      const Slot& X = ctx->slot[kX];
+      const Slot& Sv = ctx->slot[kR2];
+      cudaMemcpyAsync(ctx->arena + Sv.base + Sv.copy_stride, ctx->arena + X.base + (long long)cu * X.copy_stride,
+                      (size_t)X.copy_stride, cudaMemcpyDeviceToDevice, ctx->stream);
+    }
+    run_fop(ctx, OP_F_V_0 + cu, nf, nf);
+    run_fop(ctx, OP_F_V2, nf, nf);
+    run_fop(ctx, OP_F_IT1, nf, nf);
+    for (int j = 2; j <= ctx->fermi_m; ++j) run_fop(ctx, OP_F_IH0 + (j - 2), nf, nf);
+    if (k == nd - 1) {
+      run_fop(ctx, OP_F_FIN, nf, ctx->f64 ? 0 : 3);    // cu == 1 here: F = U r(V) + I / 2, bf16 planes
+    } else {
+      run_fop(ctx, OP_F_UP_0 + cu, nf, nf);
+      cu = 1 - cu;
+    }
+  }
+  launch_buffer_index(ctx->d_sp2, 0, ctx->lay.n_sub, ctx->stream);
+  ctx->launches += 1;
+}
+
+// Doublings redone from the kept stage after a mu shift (see fermi_reentry).
+constexpr int kReentryStages = 3;
+
+// One pass: F at (mu, beta) into kX copy 0, every buffer index pointing there; the stage
+// nd - kReentryStages is kept for mu shifts.
 void run_fermi(sedacs_ctx* ctx, double mu, int nd) {
   cudaStream_t s = ctx->stream;
   const Layout& L = ctx->lay;
@@ -1031,22 +1115,47 @@ void run_fermi(sedacs_ctx* ctx, double mu, int nd) {
   run_fop(ctx, OP_F_ST1, nf, nf);
   for (int j = 2; j <= ctx->fermi_j; ++j) run_fop(ctx, OP_F_SH0 + (j - 2), nf, nf);
   // U_0 goes to the copy from which n doublings end in copy 0
-  int cu = nd & 1;
+  const int cu = nd & 1;
   run_fop(ctx, OP_F_U0_0 + cu, nf, nf);
-  for (int k = 0; k < nd; ++k) {
-    run_fop(ctx, OP_F_V_0 + cu, nf, nf);
-    run_fop(ctx, OP_F_V2, nf, nf);
-    run_fop(ctx, OP_F_IT1, nf, nf);
-    for (int j = 2; j <= ctx->fermi_m; ++j) run_fop(ctx, OP_F_IH0 + (j - 2), nf, nf);
-    if (k == nd - 1) {
-      run_fop(ctx, OP_F_FIN, nf, ctx->f64 ? 0 : 3);    // cu == 1 here: F = U r(V) + I / 2, bf16 planes
-    } else {
-      run_fop(ctx, OP_F_UP_0 + cu, nf, nf);
-      cu = 1 - cu;
-    }
-  }
-  launch_buffer_index(ctx->d_sp2, 0, L.n_sub, s);
-  ctx->launches += 1;
+  const int js = std::max(0, nd - kReentryStages);
+  fermi_doublings_from(ctx, 0, nd, cu, js);
+  ctx->fermi_n = nd;
+  ctx->fermi_saved_mu = mu;
+  ctx->fermi_saved_j = js;
+  ctx->fermi_saved_nd = nd;
+}
+
+// Largest |beta dmu| handled by a shift at the kept stage: |tau| <= 0.2 (0.3 in FP64, whose
+// Horner polynomial has degree 15) with tau = tanh(beta_j dmu / 2), beta_j = beta / 2^S.
+double reentry_reach(const sedacs_ctx* ctx) {
+  const int S = ctx->fermi_saved_nd - ctx->fermi_saved_j;
+  return std::ldexp(2.0 * std::atanh(ctx->f64 ? 0.3 : 0.2), S);
+}
+
+// F at mu from the stage kept by the last full pass (mu_s, stage j): the tanh addition rule
+// tanh(a + b) = (tanh a + tanh b) / (1 + tanh a tanh b) shifts U_j to mu exactly,
+// U_j' = (U_j + tau I)(I + tau U_j)^-1 with tau = tanh(beta_j (mu - mu_s) / 2), the inverse being a
+// polynomial in U_j (Chebyshev interpolant of 1 / (1 + tau u) on [-1, 1]); the remaining doublings
+// then run as in a full pass.
+void fermi_reentry(sedacs_ctx* ctx, double mu) {
+  const int nf = ctx->f64 ? 0 : ctx->nsplit_fermi;
+  const int nd = ctx->fermi_saved_nd, js = ctx->fermi_saved_j, S = nd - js;
+  const double tau = std::tanh(0.5 * std::ldexp(beta_of(ctx), -S) * (mu - ctx->fermi_saved_mu));
+  const Slot& Y = ctx->slot[kY0];
+  const Slot& Sv = ctx->slot[kR2];
+  cudaMemcpyAsync(ctx->arena + Y.base, ctx->arena + Sv.base + Sv.copy_stride, (size_t)Y.copy_stride,
+                  cudaMemcpyDeviceToDevice, ctx->stream);
+  double c[16];
+  mobius_coeffs(tau, 2 * ctx->fermi_m + 1, c);
+  set_horner(ctx, c);
+  run_fop(ctx, OP_F_V2, nf, nf);                     // U_j^2
+  run_fop(ctx, OP_F_IT1, nf, nf);
+  for (int j = 2; j <= ctx->fermi_m; ++j) run_fop(ctx, OP_F_IH0 + (j - 2), nf, nf);
+  set_horner(ctx, fermi_inv(ctx));
+  const int cu = S & 1;                              // S doublings then end in copy 0
+  ctx->ops[OP_F_MOB_0 + cu].g1 = tau;
+  run_fop(ctx, OP_F_MOB_0 + cu, nf, nf);             // U_j' = U_j Q + tau Q
+  fermi_doublings_from(ctx, js, nd, cu, -1);
   ctx->fermi_n = nd;
 }
 
@@ -1098,7 +1207,7 @@ sedacs_status fermi_density(sedacs_ctx* ctx, double* mu_io) {
   const Layout& L = ctx->lay;
   const int ns = ctx->nsplit_ns, N = ctx->N;
   const double beta = beta_of(ctx), ne = ctx->n_electrons;
-  const double lin = ctx->prm.fermi_lin > 0 ? ctx->prm.fermi_lin : (ctx->f64 ? 1.5e-3 : 3e-2);
+  const double lin = ctx->prm.fermi_lin > 0 ? ctx->prm.fermi_lin : (ctx->f64 ? 3e-4 : 3e-2);
   double lo = 1e300, hi = -1e300;
   for (int i = 0; i < L.n_sub; ++i) {
     if (L.n_real[i] == 0) continue;
@@ -1113,13 +1222,20 @@ sedacs_status fermi_density(sedacs_ctx* ctx, double* mu_io) {
   double* scr = ctx->d_rsp + 7LL * N;
   double* pop_t = ctx->d_rsp + 5LL * N;
   int pass = 0;
-  bool done = false;
+  bool done = false, have_stage = false;
   double step_old = b - a, step_prev = b - a;
   ctx->fermi_hist.clear();
+  ctx->fermi_reentries = 0;
   const int ev0 = ctx->kev_used;
   while (!done && pass < 80) {
     ++pass;
-    run_fermi(ctx, mu, fermi_doublings(ctx, mu));
+    if (have_stage && std::fabs(beta * (mu - ctx->fermi_saved_mu)) <= reentry_reach(ctx)) {
+      fermi_reentry(ctx, mu);                                     // shift at the kept stage
+      ctx->fermi_reentries += 1;
+    } else {
+      run_fermi(ctx, mu, fermi_doublings(ctx, mu));
+      have_stage = true;
+    }
     back_transform(ctx, false);                                   // T1 = Z_c F, D_c
     if (given) { done = true; break; }
     core_pops(ctx, ctx->d_dcoff, ctx->d_pop, ctx->d_eband, 9);     // N(mu)
@@ -1136,23 +1252,27 @@ sedacs_status fermi_density(sedacs_ctx* ctx, double* mu_io) {
     const double dn = ne - nel;
     ctx->fermi_hist.insert(ctx->fermi_hist.end(), {mu, dn, np});
     if (!std::isfinite(nel) || !std::isfinite(np)) { ctx->err = "non-finite electron count"; return SEDACS_ENUMERIC; }
+    // root of the second-order model np d + n2 d^2 / 2 = dn next to the Newton step dn / np (its
+    // step is also the next trial when it lies on the increasing branch of the model)
+    double dq2 = std::numeric_limits<double>::quiet_NaN();
     if (np > 0.0) {
-      // root of np d + n2 d^2 / 2 = dn next to the Newton step dn / np
       double d = dn / np;
-      for (int it = 0; it < 4; ++it) {
+      bool ok = true;
+      for (int it = 0; it < 6; ++it) {
         const double gp = np + n2 * d;
-        if (!(gp > 0.0)) break;
+        if (!(gp > 0.0)) { ok = false; break; }
         d -= (np * d + 0.5 * n2 * d * d - dn) / gp;
       }
-      if (std::isfinite(d) && std::fabs(beta * d) <= lin) { dmu = d; done = true; break; }
+      if (ok && std::isfinite(d)) dq2 = d;
+      if (ok && std::isfinite(d) && std::fabs(beta * d) <= lin) { dmu = d; done = true; break; }
     }
     // a count already within its rounding noise (a clean gap: dN/dmu ~ 0) is accepted as it is
-    if (std::fabs(dn) <= (ctx->f64 ? 1e-9 : 1e-7) * ne) { dmu = 0.0; done = true; break; }
+    if (std::fabs(dn) <= (ctx->f64 ? 1e-12 : 1e-7) * ne) { dmu = 0.0; done = true; break; }
     if (dn > 0.0) a = mu; else b = mu;
     if (b - a < 1e-13) { dmu = 0.0; done = true; break; }
     // Newton only while it lands inside the bracket and at least halves the step before last
     // (in a gap dN/dmu is tiny and, in the FP32-class forms, rounding noise): else bisect
-    const double step = np > 0.0 ? dn / np : std::numeric_limits<double>::infinity();
+    const double step = std::isfinite(dq2) ? dq2 : (np > 0.0 ? dn / np : std::numeric_limits<double>::infinity());
     const double next = mu + step;
     const bool newton = (next > a && next < b) && std::fabs(step) < 0.5 * std::fabs(step_old);
     step_old = step_prev;
@@ -1728,11 +1848,11 @@ sedacs_status sedacs_set_params(sedacs_ctx* ctx, const sedacs_params* p) {
 sedacs_status sedacs_density_info(sedacs_ctx* ctx, double* info, int32_t n_info) {
   if (!ctx || !info || n_info < 0) return SEDACS_EINVAL;
   if (!ctx->have_density) { ctx->err = "no density"; return SEDACS_EINVAL; }
-  const double v[5] = {ctx->fermi_count_err, ctx->fermi_dndmu, ctx->fermi_dmu, (double)ctx->fermi_passes,
-                       (double)ctx->fermi_n};
-  for (int k = 0; k < std::min(5, (int)n_info); ++k) info[k] = v[k];
-  for (int k = 5; k < n_info; ++k)
-    info[k] = (k - 5) < (int)ctx->fermi_hist.size() ? ctx->fermi_hist[k - 5] : 0.0;
+  const double v[6] = {ctx->fermi_count_err, ctx->fermi_dndmu, ctx->fermi_dmu, (double)ctx->fermi_passes,
+                       (double)ctx->fermi_n, (double)ctx->fermi_reentries};
+  for (int k = 0; k < std::min(6, (int)n_info); ++k) info[k] = v[k];
+  for (int k = 6; k < n_info; ++k)
+    info[k] = (k - 6) < (int)ctx->fermi_hist.size() ? ctx->fermi_hist[k - 6] : 0.0;
   return SEDACS_OK;
 }
 
@@ -1874,6 +1994,13 @@ sedacs_status sedacs_subgraph_density(sedacs_ctx* ctx, const double* R, const do
   STCHK(copy_out(ctx, q, ctx->d_q, sizeof(double) * ctx->N));
   if (e_band) *e_band = ctx->e_band;
   if (sp2_iters) std::copy(ctx->sp2_iters_h.begin(), ctx->sp2_iters_h.end(), sp2_iters);
+  CUCHK(cudaStreamSynchronize(ctx->stream));
+  return SEDACS_OK;
+}
+
+sedacs_status sedacs_charges(sedacs_ctx* ctx, double* q) {
+  if (!ctx || !q || !ctx->have_density) return SEDACS_EINVAL;
+  STCHK(copy_out(ctx, q, ctx->d_q, sizeof(double) * ctx->N));
   CUCHK(cudaStreamSynchronize(ctx->stream));
   return SEDACS_OK;
 }
@@ -2046,9 +2173,9 @@ sedacs_status sedacs_xlbomd_step(sedacs_ctx* ctx, double* R, double* V, int32_t 
     ctx->launches += 8;
     ctx->geom_valid = false;
     phase_end(ctx, 0, 7);
-    // mu predicted by linear extrapolation over the last two steps, then solved (Eq. 2)
+    // mu solved (Eq. 2) from the last step's value
     const double mu_now = ctx->mu;
-    double m = std::isfinite(ctx->mu_prev) ? 2.0 * mu_now - ctx->mu_prev : mu_now;
+    double m = mu_now;
     ctx->fuse_forces = true;
     const sedacs_status st = cycle(ctx, &m);
     ctx->fuse_forces = false;

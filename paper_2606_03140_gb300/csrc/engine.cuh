@@ -64,6 +64,8 @@ enum OpId : int {
   OP_F_FT1_0, OP_F_FT1_1, OP_F_T2S, OP_F_WS0, OP_F_WS1,
   // second-order mu term: t = s - 2 s F (kR1 copy 1), its core rows (kdT2, kdDt), T2 = kdT2 h~
   OP_F_T, OP_F_TT1_0, OP_F_TT1_1, OP_F_DT0, OP_F_DT1, OP_F_T2T,
+  // mu shift at a saved doubling stage: U' = U Q + tau Q, Q ~ (I + tau U)^-1 (U in kY0), into kX
+  OP_F_MOB_0, OP_F_MOB_1,
   OP_NUM
 };
 
@@ -126,6 +128,11 @@ struct sedacs_ctx {
   double mu_prev = std::numeric_limits<double>::quiet_NaN();   // mu of the MD step before (predictor)
   int fermi_passes = 0;           // Fermi-operator passes of the last density call
   std::vector<double> fermi_hist; // per pass: mu, N_e - N(mu), dN/dmu
+  // the stage of the last full pass kept for mu shifts (U_j in kR2 copy 1): its mu, its stage j
+  // (doublings done) and the pass's doubling count; j < 0: none
+  double fermi_saved_mu = 0.0;
+  int fermi_saved_j = -1, fermi_saved_nd = 0;
+  int fermi_reentries = 0;        // mu shifts at the saved stage in the last density call
   double sum_n3 = 0.0;            // sum over subgraphs of n_real^3 (flops of one symmetric product)
   bool ht_stale = false;          // h, h~ of the arena hold a perturbed state (response passes)
   double* d_rsp = nullptr;        // 8 N-vectors of the finite-difference response

@@ -86,6 +86,7 @@ def _load():
         "sedacs_gnn_train": (I32, [P, P, P, I32, I32, D, P, P]),
         "sedacs_kernel_judge": (I32, [P, P, P]),
         "sedacs_density_info": (I32, [P, P, I32]),
+        "sedacs_charges": (I32, [P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -104,7 +105,7 @@ EXPORTED = (
     "sedacs_xlbomd_init", "sedacs_xlbomd_step", "sedacs_phase_times", "sedacs_reset_counters",
     "sedacs_kernel_stats", "sedacs_set_params", "sedacs_graph_build_noalloc", "sedacs_gnn_num_params",
     "sedacs_gnn_init", "sedacs_gnn_set_params", "sedacs_gnn_get_params", "sedacs_gnn_apply", "sedacs_gnn_param_grad",
-    "sedacs_gnn_collect", "sedacs_gnn_train", "sedacs_kernel_judge", "sedacs_density_info",
+    "sedacs_gnn_collect", "sedacs_gnn_train", "sedacs_kernel_judge", "sedacs_density_info", "sedacs_charges",
 )
 
 
@@ -238,6 +239,12 @@ def sedacs_subgraph_density(ctx, R, n, mu=float("nan"), q=None, n_parts=None):
     return muc.value, qo, eb.value, it
 
 
+def sedacs_charges(ctx, n_atoms: int, q=None):
+    out = np.zeros(n_atoms) if q is None else q
+    _check(ctx, _lib.sedacs_charges(ctx, _ptr(out)))
+    return out
+
+
 def sedacs_energy(ctx):
     e = np.zeros(4)
     _check(ctx, _lib.sedacs_energy(ctx, _ptr(e)))
@@ -318,12 +325,12 @@ def sedacs_reset_counters(ctx):
 
 def sedacs_density_info(ctx) -> dict:
     """Diagnostics of the last density call (Te > 0)."""
-    v = np.zeros(5 + 3 * 16)
+    v = np.zeros(6 + 3 * 16)
     _check(ctx, _lib.sedacs_density_info(ctx, _ptr(v), len(v)))
     npass = int(v[3])
     return {"count_err": float(v[0]), "dn_dmu": float(v[1]), "dmu_linear": float(v[2]),
-            "passes": npass, "doublings": int(v[4]),
-            "history": [tuple(float(x) for x in v[5 + 3 * k:8 + 3 * k]) for k in range(min(npass, 16))]}
+            "passes": npass, "doublings": int(v[4]), "reentries": int(v[5]),
+            "history": [tuple(float(x) for x in v[6 + 3 * k:9 + 3 * k]) for k in range(min(npass, 16))]}
 
 
 def sedacs_kernel_stats(ctx, on: bool = True):
