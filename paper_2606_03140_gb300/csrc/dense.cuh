@@ -37,6 +37,9 @@ struct GemmMat {
                                  // from A's planes (the value the MMAs see), no master
   int c_planes;                  // generic mode: C1 is three blocked bf16 planes at c_off
   long long c_plane;             // bytes between the planes of C1
+  long long outp2_off;           // generic mode, second output (planes only; -1: none): with it the
+                                 // first output takes alpha * AB^T alone and the second
+                                 // alpha2 * AB^T + beta * I + g1 * C1 + g2 * C2
 };
 
 struct GemmWork {
@@ -73,6 +76,10 @@ struct GemmParams {
                       // the fp16-operand kernel writes two fp16 planes unless 3 is asked for)
   double alpha, beta; // epilogue coefficients (FP64 in the FP64 path, rounded to FP32 on the tensor path)
   double g1, g2;
+  double alpha2;      // second output (outp2_off) only
+  int ops_upper;      // generic mode, fp16 two-plane path: A and B are symmetric and may be stored as
+                      // their upper 128x128 tiles only (blocks left of the diagonal read as transposes)
+  int store_upper;    // symmetric result written as its upper tiles only (no mirrored tile)
 };
 
 // Host launchers (dense.cu)

@@ -90,7 +90,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_persistent(const GemmPa
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 3);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool stepping = (p.mode == kModeSp2 || p.mode == kModeRsp);
-  const bool upper_only = F16 && p.mode == kModeSp2;
+  // operands stored as upper tiles: the SP2 step, and generic products of symmetric operands
+  const bool upper_only = F16 && (p.mode == kModeSp2 || p.ops_upper);
   constexpr uint32_t kTmemCols = NSPLIT > 1 ? 512 : 128;
 
   if (threadIdx.x == 0) {
@@ -372,7 +373,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_persistent(const GemmPa
       const bool planes = m.outp_off >= 0 && p.nsplit_out > 0;
       const int fmt = (F16 && p.nsplit_out != 3) ? kPlanesF16x2 : p.nsplit_out;
       const float e_alpha = (float)p.alpha, e_beta = (float)p.beta, e_g1 = (float)p.g1, e_g2 = (float)p.g2;
-      const bool mirror = m.sym_out && !diag_tile && !upper_only;
+      const bool mirror = m.sym_out && !diag_tile && !(F16 && p.mode == kModeSp2) && !p.store_upper;
+      const bool dual = !stepping && m.outp2_off >= 0;
+      const float e_alpha2 = (float)p.alpha2;
       float tr_x = 0.f, tr_x2 = 0.f;
 #pragma unroll
       for (int cc = 0; cc < 2; ++cc) {
@@ -409,11 +412,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_persistent(const GemmPa
             for (int e = 0; e < 8; ++e) sec[e] = 0.f;
           }
           const bool rok = grow < m.m_real;
+          float out2[8];
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
             const bool ok_ij = rok && (gcol + e) < m.n_real;
             float r;
-            if (stepping) {
+            if (dual) {
+              const float r2 = e_alpha2 * acc[e] + (grow == gcol + e ? e_beta : 0.f) + e_g1 * pre[i][e] + e_g2 * sec[e];
+              out2[e] = ok_ij ? r2 : 0.f;
+              r = e_alpha * acc[e];
+            } else if (stepping) {
               const float sum = acc[e] + sec[e];
               r = branch_sq ? sum : 2.f * pre[i][e] - sum;
               if (p.mode == kModeSp2 && diag_tile && ok_ij && (qd * 32 + rl) == (ctile + csub + e)) {
@@ -432,6 +440,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_persistent(const GemmPa
             dst[1] = make_float4(out[4], out[5], out[6], out[7]);
           }
           if (planes) store_planes8(p.arena, m.outp_off + out_shift, m.outp_plane, fmt, m.n_pad, grow, gcol, out);
+          if (dual) store_planes8(p.arena, m.outp2_off, m.outp_plane, fmt, m.n_pad, grow, gcol, out2);
           if (mirror) {
             *reinterpret_cast<float4*>(tb + tb_idx(rl, csub)) = make_float4(out[0], out[1], out[2], out[3]);
             *reinterpret_cast<float4*>(tb + tb_idx(rl, csub + 4)) = make_float4(out[4], out[5], out[6], out[7]);

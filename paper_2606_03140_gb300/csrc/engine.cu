@@ -397,7 +397,7 @@ sedacs_status flush_staged(sedacs_ctx* ctx) {
 sedacs_status build_op(sedacs_ctx* ctx, int id, int a, int b, int out, int mode, double alpha, double beta,
                        bool b_from_sp2, bool a_from_sp2 = false, int c1 = -1, double g1 = 0.0, int c2 = -1,
                        double g2 = 0.0, bool c_from_sp2 = false, bool sym = false, int ca = 0, int cb = 0,
-                       int cout = 0, int cc1 = 0) {
+                       int cout = 0, int cc1 = 0, int out2 = -1, int cout2 = 0) {
   const Layout& L = ctx->lay;
   std::vector<GemmMat> mats(L.n_sub);
   std::vector<GemmWork> work;
@@ -411,6 +411,7 @@ sedacs_status build_op(sedacs_ctx* ctx, int id, int a, int b, int out, int mode,
     m.out_off = mptr(ctx, out, i, cout);
     m.outp_off = ctx->f64 ? -1 : pptr_(ctx, out, i, cout);
     m.outp_plane = ctx->slot[out].plane_stride;
+    m.outp2_off = (out2 >= 0 && !ctx->f64) ? pptr_(ctx, out2, i, cout2) : -1;
     m.x_off = (mode == kModeRsp) ? mptr(ctx, kR2, i) : mptr(ctx, kX, i);
     m.c_off = (mode == kModeRsp) ? mptr(ctx, kR1, i) : (c1 >= 0 ? mptr(ctx, c1, i, cc1) : -1);
     m.c2_off = (c2 >= 0) ? mptr(ctx, c2, i) : -1;
@@ -457,6 +458,9 @@ sedacs_status build_op(sedacs_ctx* ctx, int id, int a, int b, int out, int mode,
   op.g2 = g2;
   op.mode = mode;
   op.sym = sym && !rows_out;
+  op.alpha2 = 0.0;
+  op.ops_upper = 0;
+  op.store_upper = 0;
   return SEDACS_OK;
 }
 
@@ -475,6 +479,9 @@ void run_op(sedacs_ctx* ctx, int id, int nsplit_in, int nsplit_out) {
   p.beta = op.beta;
   p.g1 = op.g1;
   p.g2 = op.g2;
+  p.alpha2 = op.alpha2;
+  p.ops_upper = op.ops_upper;
+  p.store_upper = op.store_upper;
   if (ctx->f64) launch_gemm_f64(p, op.n_work, ctx->stream);
   else launch_gemm_tc(p, op.n_work, nsplit_in, ctx->stream);
   ctx->launches += op.n_work > 0 ? 1 : 0;
@@ -486,6 +493,51 @@ sedacs_status upload_vec(sedacs_ctx* ctx, T** dst, const std::vector<T>& v) {
   if (!v.empty()) CUCHK(cudaMemcpyAsync(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, ctx->stream));
   CUCHK(cudaStreamSynchronize(ctx->stream));   // v may be a temporary
   return SEDACS_OK;
+}
+
+// Coefficients of the polynomial sum_k c_k X^k of the inverse stage (X in kY0, X^2 in kY1).
+// V^2-stride scheme (degree 2M + 1): T_1 = c_2M+1 X X^2 + c_2M X^2 + c_2M-1 X + c_2M-2 I,
+// T_j = B_{M-j} + X^2 T_{j-1}, B_j = c_2j + c_2j+1 X.  V^3-stride scheme (degree 9): the product
+// X X^2 gives X^3 and T_1 = c_9 X^3 + c_8 X^2 + c_7 X + c_6 I, then T_2 = X^3 T_1 + c_5 X^2 + c_4 X +
+// c_3 I and r = X^3 T_2 + c_2 X^2 + c_1 X + c_0 I.
+void set_horner(sedacs_ctx* ctx, const double* c) {
+  if (ctx->fermi_v3) {
+    GemmOp& i3 = ctx->ops[OP_F_I3];
+    i3.alpha = 1.0; i3.alpha2 = c[9]; i3.beta = c[6]; i3.g1 = c[7]; i3.g2 = c[8];
+    GemmOp& i4 = ctx->ops[OP_F_I4];
+    i4.alpha = 1.0; i4.beta = c[3]; i4.g1 = c[4]; i4.g2 = c[5];
+    GemmOp& i5 = ctx->ops[OP_F_I5];
+    i5.alpha = 1.0; i5.beta = c[0]; i5.g1 = c[1]; i5.g2 = c[2];
+    return;
+  }
+  const int M = ctx->fermi_m;
+  GemmOp& t1 = ctx->ops[OP_F_IT1];
+  t1.alpha = c[2 * M + 1];
+  t1.beta = c[2 * M - 2];
+  t1.g1 = c[2 * M];
+  t1.g2 = c[2 * M - 1];
+  for (int j = 2; j <= M; ++j) {
+    GemmOp& o = ctx->ops[OP_F_IH0 + (j - 2)];
+    o.alpha = 1.0;
+    o.beta = c[2 * (M - j)];
+    o.g1 = c[2 * (M - j) + 1];
+    o.g2 = 0.0;
+  }
+}
+
+void run_fop(sedacs_ctx* ctx, int id, int nin, int nout);
+
+// The inverse stage: V^2 = V V, then r(V) in the slot horner_slot(M) (kR1 copy 0 in the tensor forms).
+void run_inverse(sedacs_ctx* ctx, int nf) {
+  run_fop(ctx, OP_F_V2, nf, nf);
+  if (ctx->fermi_v3) {
+    run_fop(ctx, OP_F_I3, nf, nf);
+    run_fop(ctx, OP_F_I4, nf, nf);
+    run_fop(ctx, OP_F_I5, nf, nf);
+    return;
+  }
+  run_fop(ctx, OP_F_IT1, nf, nf);
+  for (int j = 2; j <= ctx->fermi_m; ++j) run_fop(ctx, OP_F_IH0 + (j - 2), nf, nf);
 }
 
 // ---- finite-temperature Fermi operator: GEMM tables ---------------------------------------------
@@ -558,6 +610,29 @@ sedacs_status build_fermi_ops(sedacs_ctx* ctx) {
   for (int cu = 0; cu < 2; ++cu)
     STCHK(build_op(ctx, OP_F_MOB_0 + cu, kY0, horner_slot(M), kX, kModeGeneric, 1.0, 0.0, F, F, horner_slot(M), 0.0,
                    -1, 0.0, F, T, 0, 0, cu));
+  // fp16 two-plane form: the degree-9 inverse in powers of V^3 (V in kY0, V^2 in kY1, V^3 in kT, T_1
+  // in kR1 copy 0, T_2 in kR1 copy 1, r in kR1 copy 0 = horner_slot(4)); coefficients set by
+  // set_horner.  Its two-output product stores upper tiles only, which that form's operands allow.
+  ctx->fermi_v3 = !ctx->f64 && ctx->nsplit_fermi == kPlanesF16x2;
+  if (ctx->fermi_v3) {
+    STCHK(build_op(ctx, OP_F_I3, kY0, kY1, kT, kModeGeneric, 1.0, 0.0, F, F, kY0, 0.0, kY1, 0.0, F, T, 0, 0, 0, 0,
+                   kR1, 0));
+    STCHK(build_op(ctx, OP_F_I4, kT, kR1, kR1, kModeGeneric, 1.0, 0.0, F, F, kY0, 0.0, kY1, 0.0, F, T, 0, 0, 1));
+    STCHK(build_op(ctx, OP_F_I5, kT, kR1, kR1, kModeGeneric, 1.0, 0.0, F, F, kY0, 0.0, kY1, 0.0, F, T, 0, 1, 0));
+  }
+  // fp16 two-plane form: the recursion's symmetric intermediates are stored as their upper tiles
+  // (operands read across the diagonal as transposes); F itself is written in full
+  if (ctx->nsplit_fermi == kPlanesF16x2 && !ctx->f64) {
+    const int ids[] = {OP_F_Z2, OP_F_Z4, OP_F_ST1, OP_F_SH0, OP_F_SH1, OP_F_SH2, OP_F_SH3, OP_F_U0_0, OP_F_U0_1,
+                       OP_F_V_0, OP_F_V_1, OP_F_V2, OP_F_IT1, OP_F_IH0, OP_F_IH1, OP_F_IH2, OP_F_IH3, OP_F_IH4,
+                       OP_F_IH5, OP_F_UP_0, OP_F_UP_1, OP_F_MOB_0, OP_F_MOB_1, OP_F_I3, OP_F_I4, OP_F_I5};
+    for (int id : ids) {
+      ctx->ops[id].ops_upper = 1;
+      ctx->ops[id].store_upper = 1;
+    }
+    ctx->ops[OP_F_FIN].ops_upper = 1;
+  }
+  set_horner(ctx, fermi_inv(ctx));
   return SEDACS_OK;
 }
 
@@ -1022,24 +1097,6 @@ void drain_kstats(sedacs_ctx* ctx, int ev0) {
   ctx->kev_used = ev0;
 }
 
-// Horner coefficients of sum_k c_k X^k (degree 2M + 1) on the ops of the inverse polynomial
-// (X in kY0, X^2 in kY1): T_1 = c_2M+1 X X^2 + c_2M X^2 + c_2M-1 X + c_2M-2 I, T_j = B_{M-j} + X^2 T_{j-1}.
-void set_horner(sedacs_ctx* ctx, const double* c) {
-  const int M = ctx->fermi_m;
-  GemmOp& t1 = ctx->ops[OP_F_IT1];
-  t1.alpha = c[2 * M + 1];
-  t1.beta = c[2 * M - 2];
-  t1.g1 = c[2 * M];
-  t1.g2 = c[2 * M - 1];
-  for (int j = 2; j <= M; ++j) {
-    GemmOp& o = ctx->ops[OP_F_IH0 + (j - 2)];
-    o.alpha = 1.0;
-    o.beta = c[2 * (M - j)];
-    o.g1 = c[2 * (M - j) + 1];
-    o.g2 = 0.0;
-  }
-}
-
 // Monomial coefficients c[0..d] of the degree-d interpolant of 1 / (1 + tau u) at the Chebyshev
 // points of [-1, 1] (|tau| < 1; the interpolation error falls like rho^-d with
 // rho = 1/|tau| + sqrt(1/tau^2 - 1)).
@@ -1083,9 +1140,7 @@ void fermi_doublings_from(sedacs_ctx* ctx, int k0, int nd, int cu, int js) {
                       (size_t)X.copy_stride, cudaMemcpyDeviceToDevice, ctx->stream);
     }
     run_fop(ctx, OP_F_V_0 + cu, nf, nf);
-    run_fop(ctx, OP_F_V2, nf, nf);
-    run_fop(ctx, OP_F_IT1, nf, nf);
-    for (int j = 2; j <= ctx->fermi_m; ++j) run_fop(ctx, OP_F_IH0 + (j - 2), nf, nf);
+    run_inverse(ctx, nf);
     if (k == nd - 1) {
       run_fop(ctx, OP_F_FIN, nf, ctx->f64 ? 0 : 3);    // cu == 1 here: F = U r(V) + I / 2, bf16 planes
     } else {
@@ -1146,11 +1201,9 @@ void fermi_reentry(sedacs_ctx* ctx, double mu) {
   cudaMemcpyAsync(ctx->arena + Y.base, ctx->arena + Sv.base + Sv.copy_stride, (size_t)Y.copy_stride,
                   cudaMemcpyDeviceToDevice, ctx->stream);
   double c[16];
-  mobius_coeffs(tau, 2 * ctx->fermi_m + 1, c);
+  mobius_coeffs(tau, ctx->fermi_v3 ? 9 : 2 * ctx->fermi_m + 1, c);
   set_horner(ctx, c);
-  run_fop(ctx, OP_F_V2, nf, nf);                     // U_j^2
-  run_fop(ctx, OP_F_IT1, nf, nf);
-  for (int j = 2; j <= ctx->fermi_m; ++j) run_fop(ctx, OP_F_IH0 + (j - 2), nf, nf);
+  run_inverse(ctx, nf);                              // Q = (I + tau U_j)^-1
   set_horner(ctx, fermi_inv(ctx));
   const int cu = S & 1;                              // S doublings then end in copy 0
   ctx->ops[OP_F_MOB_0 + cu].g1 = tau;
@@ -2173,9 +2226,9 @@ sedacs_status sedacs_xlbomd_step(sedacs_ctx* ctx, double* R, double* V, int32_t 
     ctx->launches += 8;
     ctx->geom_valid = false;
     phase_end(ctx, 0, 7);
-    // mu solved (Eq. 2) from the last step's value
+    // mu solved (Eq. 2) from its linear extrapolation over the last two steps
     const double mu_now = ctx->mu;
-    double m = mu_now;
+    double m = std::isfinite(ctx->mu_prev) ? 2.0 * mu_now - ctx->mu_prev : mu_now;
     ctx->fuse_forces = true;
     const sedacs_status st = cycle(ctx, &m);
     ctx->fuse_forces = false;

@@ -39,9 +39,11 @@ struct GemmOp {
   GemmMat* mats_d = nullptr;
   GemmWork* work_d = nullptr;
   int n_work = 0;
-  double alpha = 1.0, beta = 0.0, g1 = 0.0, g2 = 0.0;
+  double alpha = 1.0, beta = 0.0, g1 = 0.0, g2 = 0.0, alpha2 = 0.0;
   int mode = kModeGeneric;
   bool sym = false;          // symmetric output: upper tiles only (counted as n^3 flops)
+  int ops_upper = 0;         // operands stored as upper tiles (fp16 two-plane path)
+  int store_upper = 0;       // result stored as upper tiles (no mirror)
 };
 
 enum OpId : int {
@@ -66,6 +68,9 @@ enum OpId : int {
   OP_F_T, OP_F_TT1_0, OP_F_TT1_1, OP_F_DT0, OP_F_DT1, OP_F_T2T,
   // mu shift at a saved doubling stage: U' = U Q + tau Q, Q ~ (I + tau U)^-1 (U in kY0), into kX
   OP_F_MOB_0, OP_F_MOB_1,
+  // degree-9 inverse in powers of V^3 (fp16 two-plane form): [V^3 | T_1] from one product V V^2 (two
+  // outputs), T_2 = V^3 T_1 + B_1, r = V^3 T_2 + B_0
+  OP_F_I3, OP_F_I4, OP_F_I5,
   OP_NUM
 };
 
@@ -121,6 +126,7 @@ struct sedacs_ctx {
   // finite-temperature Fermi operator: degrees of its two polynomials (kTanh*, kInv*), the
   // tanh doublings of the last pass, and the diagnostics of the last density call
   int fermi_j = 3, fermi_m = 4;   // Horner lengths (start: Z4 steps; inverse: V2 steps)
+  bool fermi_v3 = false;          // inverse by the V^3-stride scheme with the two-output product
   int fermi_n = 0;                // doublings of the last pass
   double fermi_count_err = 0.0;   // collected count minus N_e after the mu solve
   double fermi_dndmu = 0.0;       // dN/dmu at the accepted pass (e / Ha)
