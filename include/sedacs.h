@@ -263,19 +263,21 @@ sedacs_status sedacs_kernel_stats(sedacs_ctx* ctx, int32_t on, double* sp2_ms, i
                                   double* sp2_flops);
 
 /* ---- Allocation-free distance graph.  The paper has no counterpart to this entry point;
- * it exists for callers that cannot allocate device memory at the time of the call (code
- * running under CUDA stream capture, programs whose device memory belongs to another
- * allocator, loops that cannot take cudaMalloc's implicit synchronisation).  It writes the
+ * it exists for callers that cannot allocate device memory at the time of the call (programs
+ * whose device memory belongs to another allocator, loops that cannot take cudaMalloc's
+ * implicit synchronisation).  It writes the
  * distance part of the graph of sedacs_graph_build (edge iff minimum-image distance
  * < r_graph, columns ascending, bit-identical) into caller-owned DEVICE arrays: R [N][3]
  * (Angstrom), row_ptr [N+1], col [col_capacity]; *nnz (host) receives the edge count.
  * No context, no cudaMalloc / cudaFree: the scratch is a fixed array inside the library
  * (N <= 16384 atoms; larger N -> SEDACS_EINVAL), present on every GPU that loaded the
- * library until exit.  The first call on a device looks up that array's address, so make
- * it before any stream capture.  Every call shares the one array: calls that can overlap
+ * library until exit; the first call on a device looks up that array's address.  The call
+ * copies the edge count to the host and synchronises `stream`, so it cannot be recorded
+ * into a CUDA graph.  Every call shares the one array: calls that can overlap
  * on the GPU (other streams, other host threads) race and must be serialised by the
  * caller.  col too small -> SEDACS_ECAPACITY with *nnz = the size needed (col untouched).
- * Runs on `stream` (cudaStream_t) and returns after it has finished. */
+ * A CUDA error already pending when the call starts -> SEDACS_ECUDA, left pending for the
+ * caller.  Runs on `stream` (cudaStream_t) and returns after it has finished. */
 sedacs_status sedacs_graph_build_noalloc(const double* R, int32_t n_atoms, const double box[3], double r_graph,
                                          int64_t* row_ptr, int32_t* col, int64_t col_capacity, int64_t* nnz,
                                          void* stream);

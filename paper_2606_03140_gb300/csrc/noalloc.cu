@@ -1,10 +1,9 @@
 // Allocation-free build of the distance graph.
 //
-// Some callers cannot allocate device memory when they call into this library: code that
-// runs while a CUDA stream is being captured into a graph (cudaMalloc is not allowed
-// there), programs whose device memory is owned by another allocator or memory pool that
-// must not be bypassed, and real-time loops that cannot afford the implicit device
-// synchronisation of cudaMalloc / cudaFree.  sedacs_graph_build_noalloc serves them: it
+// Some callers cannot allocate device memory when they call into this library: programs
+// whose device memory is owned by another allocator or memory pool that must not be
+// bypassed, and loops that cannot afford the implicit device synchronisation of
+// cudaMalloc / cudaFree.  sedacs_graph_build_noalloc serves them: it
 // writes the same CSR as the distance part of sedacs_graph_build into arrays the caller
 // owns and allocates nothing.  Its scratch (one neighbour count per atom and a status word)
 // is a file-scope __device__ array, present on every GPU that loads the library until the
@@ -20,8 +19,8 @@ namespace {
 constexpr int kNoAllocMaxAtoms = 16384;
 constexpr int kNoAllocMaxDevices = 64;
 
-// counts[0 .. kNoAllocMaxAtoms), then status words.
-static __device__ __align__(256) int g_noalloc_scratch[kNoAllocMaxAtoms + 64];
+// counts[0 .. kNoAllocMaxAtoms), then one status word.
+static __device__ __align__(256) int g_noalloc_scratch[kNoAllocMaxAtoms + 1];
 
 int* g_scratch_addr[kNoAllocMaxDevices] = {};
 std::mutex g_scratch_mutex;
@@ -40,10 +39,6 @@ __device__ __forceinline__ double na_r2(const double* R, int i, int j, const Box
   return __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
 }
 
-__global__ void na_clear(int* scr, int n) {
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n + 64; t += gridDim.x * blockDim.x) scr[t] = 0;
-}
-
 __global__ void na_count(const double* R, int N, Box3 b, double rg2, int* cnt) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
@@ -53,7 +48,9 @@ __global__ void na_count(const double* R, int N, Box3 b, double rg2, int* cnt) {
   cnt[i] = c;
 }
 
-// Exclusive scan into the caller's row_ptr (single CTA); status[0] = 1 when col is too small.
+// Exclusive scan into the caller's row_ptr (single CTA).  It always writes status[0] (1 when col
+// is too small, else 0), so the status word needs no clearing between calls; na_count writes
+// every count it reads.
 __global__ void na_scan(const int* cnt, int N, long long* row_ptr, int* status, long long cap) {
   __shared__ long long part[1024];
   const int per = (N + blockDim.x - 1) / blockDim.x;
@@ -117,14 +114,16 @@ extern "C" sedacs_status sedacs_graph_build_noalloc(const double* R, int32_t n_a
   for (int a = 0; a < 3; ++a) b.L[a] = box[a];
   const double rg2 = r_graph * r_graph;
   const int TB = 128, nb = (n_atoms + TB - 1) / TB;
-  na_clear<<<(n_atoms + 64 + 255) / 256, 256, 0, s>>>(scr, n_atoms);
+  // an error left pending by the caller is not this call's: it stays for the caller to read
+  if (cudaPeekAtLastError() != cudaSuccess) return SEDACS_ECUDA;
   na_count<<<nb, TB, 0, s>>>(R, n_atoms, b, rg2, counts);
   na_scan<<<1, 1024, 0, s>>>(counts, n_atoms, reinterpret_cast<long long*>(row_ptr), status, col_capacity);
   na_fill<<<nb, TB, 0, s>>>(R, n_atoms, b, rg2, reinterpret_cast<const long long*>(row_ptr), col, status);
+  if (cudaGetLastError() != cudaSuccess) return SEDACS_ECUDA;    // launch errors of the three kernels
   long long total = 0;
   if (cudaMemcpyAsync(&total, row_ptr + n_atoms, sizeof(long long), cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return SEDACS_ECUDA;
-  if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return SEDACS_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return SEDACS_ECUDA;
   *nnz = total;
   return total > col_capacity ? SEDACS_ECAPACITY : SEDACS_OK;
 }

@@ -1,10 +1,11 @@
 """The allocation-free distance-graph entry point against the regular graph builder.
 
 sedacs_graph_build_noalloc is for callers that cannot allocate device memory when they call
-in (stream capture, foreign allocators, loops that cannot take cudaMalloc's synchronisation);
-its scratch is a fixed array inside the library.  Two calls in a row must both reproduce,
-bit for bit, the CSR that sedacs_graph_build writes for the same positions (integer output:
-bit-exact is the tolerance), so the shared scratch is cleared correctly between calls.
+in (foreign allocators, loops that cannot take cudaMalloc's synchronisation); its scratch is a
+fixed array inside the library.  Two calls in a row must both reproduce, bit for bit, the CSR
+that sedacs_graph_build writes for the same positions (integer output: bit-exact is the
+tolerance), so the shared scratch is reused correctly between calls; a warm call must leave
+both the caching allocator's count and the driver's free device memory unchanged.
 """
 import numpy as np
 import pytest
@@ -43,6 +44,14 @@ def test_noalloc_graph_matches_regular_builder_twice(which):
         assert st == 0 and nnz == len(col_ref)
         assert np.array_equal(row_ptr.cpu().numpy(), rp_ref)
         assert np.array_equal(col[:nnz].cpu().numpy(), col_ref)
+    # the call allocates nothing: a warm third call moves neither figure
+    torch.cuda.synchronize()
+    alloc0, free0 = torch.cuda.memory_allocated(), torch.cuda.mem_get_info()[0]
+    st, nnz = S.sedacs_graph_build_noalloc(R, s.box, 3.0, row_ptr, col, stream)
+    torch.cuda.synchronize()
+    alloc1, free1 = torch.cuda.memory_allocated(), torch.cuda.mem_get_info()[0]
+    assert st == 0 and nnz == len(col_ref)
+    assert alloc1 == alloc0 and free1 == free0, (alloc0, alloc1, free0, free1)
 
 
 def test_noalloc_rejects_small_output_and_oversized_input():
