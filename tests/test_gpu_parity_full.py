@@ -10,11 +10,20 @@ collected electron count, the band and Coulomb energies of the whole system, and
 the atoms of four sampled cores (the oracle evaluates the rows of those atoms only).
 
 With these seeded trial charges mu lies inside a band (dN/dmu ~ 1,900 e/Ha, 76 levels within
-2 kT).  The FP32-class form then meets 1e-5 e in RMS over all atoms but not on the few atoms that
-hold a level within ~kT of mu with a large core weight: FP32 accumulation in the recursion's
-products (which span the whole ~1 Ha spectrum) leaves ~1e-7 Ha of level noise, which moves such
-an occupation by beta f (1 - f) x 1e-7 ~ 3e-5.  Those atoms are held to 2e-4 e; the plain FP64
-form is held to 1e-9 e on every atom.
+2 kT).  Two effects of FP32-class arithmetic are tested apart:
+
+* at the oracle's mu (mu passed as given), every atom's charge: FP32 accumulation in the
+  recursion's products (which span the whole ~1 Ha spectrum) leaves ~1e-7 Ha of level noise, which
+  moves an occupation near mu by beta f (1 - f) x 1e-7 ~ 3e-5; held to 1e-4 e per atom and 5e-6 e
+  RMS.  The collected count then carries a systematic offset of ~1e-7 e per atom (measured
+  1.0e-3 to 1.7e-3 e over the 9,000 atoms for two seeds; hydrogen -6e-7 e on average), held to
+  4e-3 e.
+* mu solved by each side (Eq. 2): the count offset becomes a mu offset of offset / (dN/dmu), at
+  most 4e-3 / 1,900 ~ 2.1e-6 Ha, which moves the atoms holding a level within kT of mu by up to
+  beta / 4 x 2.1e-6 ~ 5.5e-4 e; so mu is held to 2.5e-6 Ha, those atoms to 6e-4 e and the RMS
+  over all atoms to 1e-5 e.
+
+The plain FP64 form is held to 1e-9 e on every atom.
 """
 import numpy as np
 import pytest
@@ -59,6 +68,11 @@ def full():
         info = S.sedacs_density_info(ctx)
         F = S.sedacs_forces(ctx, N)
         e = S.sedacs_energy(ctx)
+        # the same context at the oracle's mu, taken as given
+        prm = S.sedacs_default_params(core_size=32, precision=1, mu_given=1)
+        S.sedacs_set_params(ctx, prm)
+        _, q_at, _, _ = S.sedacs_subgraph_density(ctx, R, n, mu=float(ref.mu))
+        info_at = S.sedacs_density_info(ctx)
     finally:
         S.sedacs_destroy(ctx)
     # the plain FP64 form on the same graph
@@ -73,7 +87,7 @@ def full():
         S.sedacs_destroy(ctx)
     return dict(s=s, m=m, n=n, V=V, g0=g0, g1=g1, rp0=rp0, col0=col0, rp1=rp1, col1=col1, cores=cores,
                 hal1=hal1, sp=sp, sa=sa, nc=nc, mu=mu, q=q, eb=eb, info=info, F=F, e=e, ref=ref, atoms=atoms,
-                Fref=Fref, mu64=mu64, q64=q64, eb64=eb64, F64=F64)
+                Fref=Fref, mu64=mu64, q64=q64, eb64=eb64, F64=F64, q_at=q_at, info_at=info_at)
 
 
 def test_graph_cores_halos_bit_exact_full_size(full):
@@ -87,6 +101,18 @@ def test_graph_cores_halos_bit_exact_full_size(full):
         assert np.array_equal(sa[sp[i] + nc[i]:sp[i + 1]], hal[i])
 
 
+def test_charges_at_oracle_mu_full_size(full):
+    ref = full["ref"]
+    dq = full["q_at"] - ref.q
+    off = full["info_at"]["count_err"]
+    print(f"[parity] water9000 form 1 at the oracle's mu: max|dq| {np.max(np.abs(dq)):.3e} e, RMS "
+          f"{np.sqrt(np.mean(dq ** 2)):.2e} e, count offset {off:+.3e} e ({off / len(dq):+.1e} e per atom)")
+    assert np.max(np.abs(dq)) < 1e-4
+    assert np.sqrt(np.mean(dq ** 2)) < 5e-6
+    assert abs(off) < 4e-3
+    assert abs(float(np.sum(dq)) - off) < 1e-6
+
+
 def test_mu_count_charges_energies_full_size(full):
     ref, info = full["ref"], full["info"]
     N = full["s"].n_atoms
@@ -97,9 +123,9 @@ def test_mu_count_charges_energies_full_size(full):
           f"{ref.in_gap_weight:.2f}; max|dq| over all {N} atoms = {dq:.3e} e, RMS "
           f"{np.sqrt(np.mean((full['q'] - ref.q) ** 2)):.2e} e, atoms above 1e-5 e: "
           f"{int(np.sum(np.abs(full['q'] - ref.q) > 1e-5))}")
-    assert dq < 2e-4, dq
+    assert dq < 6e-4, dq
     assert np.sqrt(np.mean((full["q"] - ref.q) ** 2)) < 1e-5
-    assert abs(full["mu"] - ref.mu) < 1e-5
+    assert abs(full["mu"] - ref.mu) < 2.5e-6
     assert abs(info["count_err"]) < 1e-3
     assert abs(full["q"].sum()) < 1e-3
     deb = abs(full["eb"] - ref.e_band) / N
