@@ -23,7 +23,9 @@ With these seeded trial charges mu lies inside a band (dN/dmu ~ 1,900 e/Ha, 76 l
   beta / 4 x 2.1e-6 ~ 5.5e-4 e; so mu is held to 2.5e-6 Ha, those atoms to 6e-4 e and the RMS
   over all atoms to 1e-5 e.
 
-The plain FP64 form is held to 1e-9 e on every atom.
+The plain FP64 form is held to 5e-9 e on every atom: its recursion's inverse polynomial (degree 15,
+fit error 8.2e-13) errs by that much at each doubling, and a level at mu carries the error of the
+first doubling amplified by 2^n (n = 11 here), ~1.7e-9 in its occupation.
 """
 import numpy as np
 import pytest
@@ -150,4 +152,4 @@ def test_plain_fp64_form_full_size(full):
     dF = np.max(np.abs(full["F64"][a] - full["Fref"][a]))
     print(f"[parity] water9000 FP64 form: |dmu| {abs(full['mu64'] - ref.mu):.2e} Ha, max|dq| {dq:.2e} e, "
           f"|dE_band|/atom {abs(full['eb64'] - ref.e_band) / len(ref.q):.2e} Ha, max|dF| (sampled) {dF:.2e} Ha/A")
-    assert dq < 1e-9 and dF < 1e-8 and abs(full["mu64"] - ref.mu) < 1e-9
+    assert dq < 5e-9 and dF < 1e-8 and abs(full["mu64"] - ref.mu) < 1e-9
