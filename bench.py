@@ -208,14 +208,15 @@ def setup_system(S, I, workload: str, precision: int, seed_v: int = 20260703, qu
         raise SystemExit(f"{e}; it is not an MD benchmark")
 
 
-def frame_check(S, ctx, R, n, q, mu, picks, model, species, box):
+def frame_check(parts, R, n, q, mu, picks, model, species, box):
     """Charges of sampled subgraphs at one frame, recomputed by the FP64 oracle from the GPU's
-    positions R, charges n, chemical potential mu and subgraph lists (the Coulomb potential only
-    at the sampled atoms, its sums over every atom).  Returns max |q_gpu - q_oracle| there."""
+    positions R, charges n, chemical potential mu and subgraph lists of that frame (parts, as
+    sedacs_parts_get returned them right after the frame's step; the Coulomb potential only at
+    the sampled atoms, its sums over every atom).  Returns max |q_gpu - q_oracle| there."""
     from oracle import density as odn
     from oracle import ewald as oew
 
-    sp, sa, nc = S.sedacs_parts_get(ctx)
+    sp, sa, nc = parts
     cores = [sa[sp[i]:sp[i] + nc[i]] for i in picks]
     halos = [sa[sp[i] + nc[i]:sp[i + 1]] for i in picks]
     atoms = np.unique(np.concatenate([sa[sp[i]:sp[i + 1]] for i in picks]))
@@ -312,7 +313,7 @@ def run_ours(args, world, rank, local):
         evals.append((dinf["passes"], dinf["reentries"]))
         if k in keep and rank == 0 and not args.no_frames:
             mu_k = dinf["history"][-1][0] + dinf["dmu_linear"]
-            frames.append((k, Rh.copy(), nh.copy(), S.sedacs_charges(ctx, N), mu_k))
+            frames.append((k, Rh.copy(), nh.copy(), S.sedacs_charges(ctx, N), mu_k, S.sedacs_parts_get(ctx)))
     torch.cuda.synchronize()
     t_e2e = allmax(world, t_e2e)
     # roofline of the Fermi-operator products from a separate pass with per-launch CUDA events
@@ -330,7 +331,7 @@ def run_ours(args, world, rank, local):
         nsub = S.sedacs_parts_get(ctx)[2].shape[0]
         picks = [p for p in picks if p < nsub]
         t0 = time.perf_counter()
-        res = [frame_check(S, ctx, Rf, nf, qf, muf, picks, model, s.species, s.box) for (_, Rf, nf, qf, muf) in frames]
+        res = [frame_check(pf, Rf, nf, qf, muf, picks, model, s.species, s.box) for (_, Rf, nf, qf, muf, pf) in frames]
         errs = [r[0] for r in res]
         acc = {"max_dq_vs_oracle": max(errs), "rms_dq_vs_oracle": float(np.sqrt(np.mean([r[1] ** 2 for r in res]))),
                "atoms_above_1e-5": sum(r[2] for r in res), "atoms_checked": sum(r[3] for r in res),
