@@ -80,6 +80,7 @@ struct GemmParams {
   int ops_upper;      // generic mode, fp16 two-plane path: A and B are symmetric and may be stored as
                       // their upper 128x128 tiles only (blocks left of the diagonal read as transposes)
   int store_upper;    // symmetric result written as its upper tiles only (no mirrored tile)
+  int no_master;      // planes only: the FP32 master of the result is not written (no reader needs it)
 };
 
 // Host launchers (dense.cu)

@@ -369,7 +369,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_gemm_persistent(const GemmPa
       }
       ++ti;
 
-      float* outm = (m.out_off >= 0) ? reinterpret_cast<float*>(p.arena + m.out_off + out_shift) : nullptr;
+      float* outm = (m.out_off >= 0 && !p.no_master) ? reinterpret_cast<float*>(p.arena + m.out_off + out_shift)
+                                                     : nullptr;
       const bool planes = m.outp_off >= 0 && p.nsplit_out > 0;
       const int fmt = (F16 && p.nsplit_out != 3) ? kPlanesF16x2 : p.nsplit_out;
       const float e_alpha = (float)p.alpha, e_beta = (float)p.beta, e_g1 = (float)p.g1, e_g2 = (float)p.g2;

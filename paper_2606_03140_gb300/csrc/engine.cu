@@ -482,6 +482,8 @@ void run_op(sedacs_ctx* ctx, int id, int nsplit_in, int nsplit_out) {
   p.alpha2 = op.alpha2;
   p.ops_upper = op.ops_upper;
   p.store_upper = op.store_upper;
+  // planes-only results exist in the fp16 two-plane path, whose outputs are read as planes
+  p.no_master = (!ctx->f64 && nsplit_in == kPlanesF16x2 && nsplit_out == kPlanesF16x2) ? op.no_master : 0;
   if (ctx->f64) launch_gemm_f64(p, op.n_work, ctx->stream);
   else launch_gemm_tc(p, op.n_work, nsplit_in, ctx->stream);
   ctx->launches += op.n_work > 0 ? 1 : 0;
@@ -631,6 +633,13 @@ sedacs_status build_fermi_ops(sedacs_ctx* ctx) {
       ctx->ops[id].store_upper = 1;
     }
     ctx->ops[OP_F_FIN].ops_upper = 1;
+    // results read only as MMA operands keep no FP32 master: the tanh Horner sums and U_0, V^3 and
+    // T_2 of the inverse, and every U but the kept stage.  Masters stay where an epilogue adds the
+    // result: Z2, Z4, V, V^2 (kY0, kY1), the inverse's last sum r (the mu shift adds Q = r as
+    // tau Q) and the kept stage U_j (copied to kY0, whose master the shift's inverse adds).
+    const int pl[] = {OP_F_ST1, OP_F_SH0, OP_F_SH1, OP_F_SH2, OP_F_SH3, OP_F_U0_0, OP_F_U0_1, OP_F_I3, OP_F_I4,
+                      OP_F_UP_0, OP_F_UP_1, OP_F_MOB_0, OP_F_MOB_1};
+    for (int id : pl) ctx->ops[id].no_master = 1;
   }
   set_horner(ctx, fermi_inv(ctx));
   return SEDACS_OK;
@@ -1144,7 +1153,12 @@ void fermi_doublings_from(sedacs_ctx* ctx, int k0, int nd, int cu, int js) {
     if (k == nd - 1) {
       run_fop(ctx, OP_F_FIN, nf, ctx->f64 ? 0 : 3);    // cu == 1 here: F = U r(V) + I / 2, bf16 planes
     } else {
+      // the U that becomes the kept stage carries its FP32 master: the mu shift's inverse adds it
+      GemmOp& up = ctx->ops[OP_F_UP_0 + cu];
+      const int nm = up.no_master;
+      if (k + 1 == js) up.no_master = 0;
       run_fop(ctx, OP_F_UP_0 + cu, nf, nf);
+      up.no_master = nm;
       cu = 1 - cu;
     }
   }
@@ -1171,8 +1185,12 @@ void run_fermi(sedacs_ctx* ctx, double mu, int nd) {
   for (int j = 2; j <= ctx->fermi_j; ++j) run_fop(ctx, OP_F_SH0 + (j - 2), nf, nf);
   // U_0 goes to the copy from which n doublings end in copy 0
   const int cu = nd & 1;
-  run_fop(ctx, OP_F_U0_0 + cu, nf, nf);
   const int js = std::max(0, nd - kReentryStages);
+  GemmOp& u0 = ctx->ops[OP_F_U0_0 + cu];
+  const int nm = u0.no_master;
+  if (js == 0) u0.no_master = 0;                   // U_0 is the kept stage (see fermi_doublings_from)
+  run_fop(ctx, OP_F_U0_0 + cu, nf, nf);
+  u0.no_master = nm;
   fermi_doublings_from(ctx, 0, nd, cu, js);
   ctx->fermi_n = nd;
   ctx->fermi_saved_mu = mu;

@@ -44,6 +44,7 @@ struct GemmOp {
   bool sym = false;          // symmetric output: upper tiles only (counted as n^3 flops)
   int ops_upper = 0;         // operands stored as upper tiles (fp16 two-plane path)
   int store_upper = 0;       // result stored as upper tiles (no mirror)
+  int no_master = 0;         // fp16 two-plane path: result kept as planes only (no FP32 master)
 };
 
 enum OpId : int {
