@@ -97,10 +97,11 @@ typedef struct {
                            mu-branch SP2 recursion at a chemical potential the caller gives. */
   int32_t mu_given;     /* Te > 0: 1 = use the mu passed to the density calls as given (no Eq. 2 solve) */
   double fermi_lin;     /* Te > 0: after a Fermi pass at mu0 the count is brought to N_e by the mu step
-                           dmu of its second-order expansion (D += beta dmu D_s + (beta dmu)^2 / 2 D_t,
-                           with dF/dmu = beta (F - F^2) and d2F/dmu2 = beta^2 (F - F^2)(I - 2F)) when
-                           |beta dmu| is at most this; otherwise another pass runs (0: 3e-2 in the
-                           FP32-class forms, 3e-4 in FP64) */
+                           dmu of its fourth-order expansion (D += sum_k (beta dmu)^k / k! D_k, with
+                           d^kF/dmu^k = beta^k X_k: X_1 = s = F - F^2, X_2 = t = s (I - 2F),
+                           X_3 = t (I - 2F) - 2 s^2, X_4 = X_3 (I - 2F) - 6 s t) when |beta dmu| is at
+                           most this; otherwise another pass runs (0: 0.2 in the FP32-class forms,
+                           1e-2 in FP64; remainder <= (beta dmu)^5 / 120 x 0.25 per occupation) */
 } sedacs_params;
 
 /* Fill p with the defaults (r_graph 3.0, tau 1e-3, core_size 32, precision 1, kernel 0,

@@ -591,8 +591,14 @@ sedacs_status build_fermi_ops(sedacs_ctx* ctx) {
                    cu, 0, 1 - cu));
   STCHK(build_op(ctx, OP_F_FIN, kX, horner_slot(M), kX, kModeGeneric, 1.0, 0.5, F, F, -1, 0.0, -1, 0.0, F, T, 1, 0,
                  0));
-  // s = F - F^2 (F in copy 0, where the SP2 state's buffer index points after a pass)
-  STCHK(build_op(ctx, OP_F_S, kX, kX, kR2, kModeGeneric, -1.0, 0.0, T, T, kX, 1.0, -1, 0.0, T, T));
+  // s = F - F^2 without the cancellation of F - F F on the saturated levels: with V = U^2 and
+  // r = (I + V)^-1 of the last doubling, I - U'^2 = ((I - V) r)^2, so s = (I - U'^2) / 4 = G^2 / 4
+  // with G = r - V r (small where F is 0 or 1)
+  // (G goes to the Horner slot that does not hold r: kT for M even, kR1 copy 0 for M odd)
+  const int gslot = horner_slot(M) == kT ? kR1 : kT;
+  STCHK(build_op(ctx, OP_F_G, kY0, horner_slot(M), gslot, kModeGeneric, -1.0, 0.0, F, F, horner_slot(M), 1.0, -1,
+                 0.0, F, T));
+  STCHK(build_op(ctx, OP_F_S, gslot, gslot, kR2, kModeGeneric, 0.25, 0.0, F, F, -1, 0.0, -1, 0.0, F, T));
   // core rows of F into the response slots: dT1 = Z_c F = F_c + E_z,c F
   STCHK(build_op(ctx, OP_F_FT1_0, kZ0, kX, kdT1, kModeGeneric, 1.0, 0.0, T, F, kX, 1.0, -1, 0.0, T));
   STCHK(build_op(ctx, OP_F_FT1_1, kZ1, kX, kdT1, kModeGeneric, 1.0, 0.0, T, F, kX, 1.0, -1, 0.0, T));
@@ -607,6 +613,22 @@ sedacs_status build_fermi_ops(sedacs_ctx* ctx) {
   STCHK(build_op(ctx, OP_F_DT0, kdT2, kZ0, kdDt, kModeGeneric, 2.0, 0.0, F, F, kdT2, 2.0));
   STCHK(build_op(ctx, OP_F_DT1, kdT2, kZ1, kdDt, kModeGeneric, 2.0, 0.0, F, F, kdT2, 2.0));
   STCHK(build_op(ctx, OP_F_T2T, kdT2, kHt, kT2, kModeGeneric, 1.0, 0.0, F));
+  // third order: P = t F into kT, u = -2 s s + t - 2 P into kY0 (both free after the pass); rows
+  STCHK(build_op(ctx, OP_F_TF, kR1, kX, kT, kModeGeneric, 1.0, 0.0, T, F, -1, 0.0, -1, 0.0, F, T, 1, 0, 0));
+  STCHK(build_op(ctx, OP_F_U, kR2, kR2, kY0, kModeGeneric, -2.0, 0.0, T, T, kR1, 1.0, kT, -2.0, F, T, 0, 0, 0, 1));
+  STCHK(build_op(ctx, OP_F_UT1_0, kZ0, kY0, kdT3, kModeGeneric, 1.0, 0.0, F, F, kY0, 1.0, -1, 0.0, F, F));
+  STCHK(build_op(ctx, OP_F_UT1_1, kZ1, kY0, kdT3, kModeGeneric, 1.0, 0.0, F, F, kY0, 1.0, -1, 0.0, F, F));
+  STCHK(build_op(ctx, OP_F_DU0, kdT3, kZ0, kdDu, kModeGeneric, 2.0, 0.0, F, F, kdT3, 2.0));
+  STCHK(build_op(ctx, OP_F_DU1, kdT3, kZ1, kdDu, kModeGeneric, 2.0, 0.0, F, F, kdT3, 2.0));
+  STCHK(build_op(ctx, OP_F_T2U, kdT3, kHt, kT2, kModeGeneric, 1.0, 0.0, F));
+  // fourth order: Q = u F into kT, w = -6 s t + u - 2 Q into kY1; rows
+  STCHK(build_op(ctx, OP_F_UF, kY0, kX, kT, kModeGeneric, 1.0, 0.0, T, F, -1, 0.0, -1, 0.0, F, T));
+  STCHK(build_op(ctx, OP_F_W, kR2, kR1, kY1, kModeGeneric, -6.0, 0.0, F, T, kY0, 1.0, kT, -2.0, F, T, 0, 1, 0));
+  STCHK(build_op(ctx, OP_F_WT1_0, kZ0, kY1, kdT4, kModeGeneric, 1.0, 0.0, F, F, kY1, 1.0, -1, 0.0, F, F));
+  STCHK(build_op(ctx, OP_F_WT1_1, kZ1, kY1, kdT4, kModeGeneric, 1.0, 0.0, F, F, kY1, 1.0, -1, 0.0, F, F));
+  STCHK(build_op(ctx, OP_F_DW0, kdT4, kZ0, kdDw, kModeGeneric, 2.0, 0.0, F, F, kdT4, 2.0));
+  STCHK(build_op(ctx, OP_F_DW1, kdT4, kZ1, kdDw, kModeGeneric, 2.0, 0.0, F, F, kdT4, 2.0));
+  STCHK(build_op(ctx, OP_F_T2W, kdT4, kHt, kT2, kModeGeneric, 1.0, 0.0, F));
   // mu shift at a saved stage: U' = U Q + tau Q (U in kY0, Q = (I + tau U)^-1 in the Horner slot)
   // into either copy of kX; tau is set in g1 at run time
   for (int cu = 0; cu < 2; ++cu)
@@ -633,6 +655,8 @@ sedacs_status build_fermi_ops(sedacs_ctx* ctx) {
       ctx->ops[id].store_upper = 1;
     }
     ctx->ops[OP_F_FIN].ops_upper = 1;
+    ctx->ops[OP_F_G].ops_upper = ctx->ops[OP_F_G].store_upper = ctx->ops[OP_F_G].no_master = 1;
+    ctx->ops[OP_F_S].ops_upper = 1;                // s itself is written in full, as bf16 planes
     // results read only as MMA operands keep no FP32 master: the tanh Horner sums and U_0, V^3 and
     // T_2 of the inverse, and every U but the kept stage.  Masters stay where an epilogue adds the
     // result: Z2, Z4, V, V^2 (kY0, kY1), the inverse's last sum r (the mu shift adds Q = r as
@@ -701,8 +725,9 @@ sedacs_status rebuild_layout(sedacs_ctx* ctx) {
   long long off = 0;
   for (int k = 0; k < kNumSlots; ++k) {
     Slot& S = ctx->slot[k];
-    S.rows = (k == kT1 || k == kDc || k == kT2 || k == kWc || k == kdT1 || k == kdDc || k == kdT2 || k == kdDt);
-    S.planes = planes && !(k == kDc || k == kWc || k == kdDc || k == kdDt);
+    S.rows = (k == kT1 || k == kDc || k == kT2 || k == kWc || k == kdT1 || k == kdDc || k == kdT2 || k == kdDt ||
+              k == kdT3 || k == kdDu || k == kdT4 || k == kdDw);
+    S.planes = planes && !(k == kDc || k == kWc || k == kdDc || k == kdDt || k == kdDu || k == kdDw);
     S.copies = (k == kX || k == kR1 || k == kR2) ? 2 : 1;
     const long long el = S.rows ? L.rw_total : L.sq_total;
     S.master_bytes = (el * esz + 1023) / 1024 * 1024;
@@ -721,7 +746,8 @@ sedacs_status rebuild_layout(sedacs_ctx* ctx) {
   // views and per-subgraph offset arrays
   for (int k = 0; k < kNumSlots; ++k) STCHK(stage_views(ctx, k, 0, &ctx->d_views[k]));
   STCHK(stage_views(ctx, kX, 1, &ctx->d_views_x1));
-  std::vector<long long> hoff(P), soff(P), dco(P), wco(P), rbase(P), troff(P), ddco(P), dhoff(P), dtco(P);
+  std::vector<long long> hoff(P), soff(P), dco(P), wco(P), rbase(P), troff(P), ddco(P), dhoff(P), dtco(P), duco(P),
+      dwco(P);
   std::vector<int> npad(P), nreal(P), ndiag(P);
   long long rb = 0;
   for (int i = 0; i < P; ++i) {
@@ -731,6 +757,8 @@ sedacs_status rebuild_layout(sedacs_ctx* ctx) {
     wco[i] = mptr(ctx, kWc, i);
     ddco[i] = mptr(ctx, kdDc, i);
     dtco[i] = mptr(ctx, kdDt, i);
+    duco[i] = mptr(ctx, kdDu, i);
+    dwco[i] = mptr(ctx, kdDw, i);
     dhoff[i] = mptr(ctx, kdH, i);
     rbase[i] = rb;
     rb += L.n_pad[i];
@@ -745,6 +773,8 @@ sedacs_status rebuild_layout(sedacs_ctx* ctx) {
   STCHK(stage_vec(ctx, &ctx->d_wcoff, wco));
   STCHK(stage_vec(ctx, &ctx->d_dcoff_d, ddco));
   STCHK(stage_vec(ctx, &ctx->d_dcoff_t, dtco));
+  STCHK(stage_vec(ctx, &ctx->d_dcoff_u, duco));
+  STCHK(stage_vec(ctx, &ctx->d_dcoff_w, dwco));
   STCHK(stage_vec(ctx, &ctx->d_dhoff, dhoff));
   STCHK(stage_vec(ctx, &ctx->d_rowbase, rbase));
   STCHK(stage_vec(ctx, &ctx->d_tr_off, troff));
@@ -1242,10 +1272,13 @@ void core_pops(sedacs_ctx* ctx, const long long* dc_off, double* pop, double* eb
   ctx->launches += 2;
 }
 
-// s = F - F^2 and the core rows D_s = 2 Z_c s Z (kdT1 -> kdDc); d/dmu of F is beta s.
+// s = F - F^2 (as G^2 / 4 from the last doubling's V and r, still in kY0 and the Horner slot) and
+// the core rows D_s = 2 Z_c s Z (kdT1 -> kdDc); d/dmu of F is beta s.
 void fermi_s_rows(sedacs_ctx* ctx) {
   const int ns = ctx->nsplit_ns;
-  run_fop(ctx, OP_F_S, ctx->f64 ? 0 : 3, ctx->f64 ? 0 : 3);
+  const int nf = ctx->f64 ? 0 : ctx->nsplit_fermi;
+  run_fop(ctx, OP_F_G, nf, nf);
+  run_fop(ctx, OP_F_S, nf, ctx->f64 ? 0 : 3);
   run_op(ctx, ctx->zc == 0 ? OP_DT1_0 : OP_DT1_1, 3, ns);
   run_op(ctx, ctx->zc == 0 ? OP_DDC0 : OP_DDC1, ns, 0);
 }
@@ -1259,6 +1292,22 @@ void fermi_t_rows(sedacs_ctx* ctx) {
 }
 
 
+// The third- and fourth-order terms, u = t (I - 2F) - 2 s^2 and w = u (I - 2F) - 6 s t
+// (d^3 F / dmu^3 = beta^3 u, d^4 F / dmu^4 = beta^4 w), and their core rows D_u, D_w.  They enter
+// scaled by (beta dmu)^k / k! <= 1.4e-3, so their products read two of the three bf16 planes.
+void fermi_uw_rows(sedacs_ctx* ctx) {
+  const int ns = ctx->nsplit_ns;
+  const int nl = ctx->f64 ? 0 : 2, no = ctx->f64 ? 0 : 3;
+  run_fop(ctx, OP_F_TF, nl, no);
+  run_fop(ctx, OP_F_U, nl, no);
+  run_op(ctx, ctx->zc == 0 ? OP_F_UT1_0 : OP_F_UT1_1, nl, ns);
+  run_op(ctx, ctx->zc == 0 ? OP_F_DU0 : OP_F_DU1, ns, 0);
+  run_fop(ctx, OP_F_UF, nl, no);
+  run_fop(ctx, OP_F_W, nl, no);
+  run_op(ctx, ctx->zc == 0 ? OP_F_WT1_0 : OP_F_WT1_1, nl, ns);
+  run_op(ctx, ctx->zc == 0 ? OP_F_DW0 : OP_F_DW1, ns, 0);
+}
+
 void rows_axpy(sedacs_ctx* ctx, int sy, int sx, double a) {
   const long long n = ctx->lay.rw_total;
   rows_axpy_kernel<<<nblk(n, 256), 256, 0, ctx->stream>>>(ctx->arena + ctx->slot[sy].base,
@@ -1269,16 +1318,18 @@ void rows_axpy(sedacs_ctx* ctx, int sy, int sx, double a) {
 // Eq. 2: mu with the collected count N(mu) = sum_i Tr_core[D_i S_i] = N_e, by safeguarded Newton
 // steps on full passes inside a bracket that starts at the spectral bounds, bisecting when a step
 // leaves it.  The mu derivatives of the Fermi function are exact matrix functions of F:
-// dF/dmu = beta s, s = F - F^2, and d^2F/dmu^2 = beta^2 t, t = s (I - 2F).  A pass at mu0 whose
-// count, expanded to second order, reaches N_e within |beta dmu| <= fermi_lin is accepted with
-// D_c += beta dmu D_s + (beta dmu)^2 / 2 D_t and the same for W_c (third-order remainder).  Leaves
-// D_c, W_c of the final density in kDc, kWc; mu_io in: guess (NaN: none), out: mu.
+// d^kF/dmu^k = beta^k X_k with X_1 = s = F - F^2, X_2 = t = s (I - 2F), X_3 = u = t (I - 2F) - 2 s^2,
+// X_4 = w = u (I - 2F) - 6 s t.  A pass at mu0 whose count, expanded to fourth order, reaches N_e
+// within |beta dmu| <= fermi_lin (0.2 in the FP32-class forms, 1e-2 in FP64) is accepted with
+// D_c += sum_k (beta dmu)^k / k! D_k and the same for W_c; the fifth-order remainder is at most
+// (beta dmu)^5 / 120 x 0.25 per occupation (6.7e-7 at 0.2, 2e-13 at 1e-2).  Leaves D_c, W_c of the
+// final density in kDc, kWc; mu_io in: guess (NaN: none), out: mu.
 sedacs_status fermi_density(sedacs_ctx* ctx, double* mu_io) {
   cudaStream_t s = ctx->stream;
   const Layout& L = ctx->lay;
   const int ns = ctx->nsplit_ns, N = ctx->N;
   const double beta = beta_of(ctx), ne = ctx->n_electrons;
-  const double lin = ctx->prm.fermi_lin > 0 ? ctx->prm.fermi_lin : (ctx->f64 ? 3e-4 : 3e-2);
+  const double lin = ctx->prm.fermi_lin > 0 ? ctx->prm.fermi_lin : (ctx->f64 ? 1e-2 : 0.2);
   double lo = 1e300, hi = -1e300;
   for (int i = 0; i < L.n_sub; ++i) {
     if (L.n_real[i] == 0) continue;
@@ -1292,6 +1343,7 @@ sedacs_status fermi_density(sedacs_ctx* ctx, double* mu_io) {
   double* pop_s = ctx->d_rsp + 6LL * N;      // kept for the response calls (their dN/dmu weights)
   double* scr = ctx->d_rsp + 7LL * N;
   double* pop_t = ctx->d_rsp + 5LL * N;
+  double* pop_uw = ctx->d_rsp + 8LL * N;
   int pass = 0;
   bool done = false, have_stage = false;
   double step_old = b - a, step_prev = b - a;
@@ -1314,25 +1366,31 @@ sedacs_status fermi_density(sedacs_ctx* ctx, double* mu_io) {
     core_pops(ctx, ctx->d_dcoff_d, pop_s, scr, 10);                // sum of D_s populations
     fermi_t_rows(ctx);
     core_pops(ctx, ctx->d_dcoff_t, pop_t, scr, 14);                // sum of D_t populations
+    fermi_uw_rows(ctx);
+    core_pops(ctx, ctx->d_dcoff_u, pop_uw, scr, 11);               // sums of D_u and D_w populations
+    core_pops(ctx, ctx->d_dcoff_w, pop_uw, scr, 12);
     double sc[6];
     CUCHK(cudaMemcpyAsync(sc, ctx->d_scal + 9, sizeof(sc), cudaMemcpyDeviceToHost, s));
     CUCHK(cudaStreamSynchronize(s));
     const double nel = sc[0];
     np = beta * sc[1];
-    const double n2 = beta * beta * sc[5];
+    const double n2 = beta * beta * sc[5], n3 = beta * beta * beta * sc[2], n4 = beta * beta * beta * beta * sc[3];
     const double dn = ne - nel;
     ctx->fermi_hist.insert(ctx->fermi_hist.end(), {mu, dn, np});
-    if (!std::isfinite(nel) || !std::isfinite(np)) { ctx->err = "non-finite electron count"; return SEDACS_ENUMERIC; }
-    // root of the second-order model np d + n2 d^2 / 2 = dn next to the Newton step dn / np (its
-    // step is also the next trial when it lies on the increasing branch of the model)
+    if (!std::isfinite(nel) || !std::isfinite(np) || !std::isfinite(n3) || !std::isfinite(n4)) {
+      ctx->err = "non-finite electron count";
+      return SEDACS_ENUMERIC;
+    }
+    // root of the fourth-order model np d + n2 d^2 / 2 + n3 d^3 / 6 + n4 d^4 / 24 = dn next to the
+    // Newton step dn / np (its step is also the next trial when it lies on the increasing branch)
     double dq2 = std::numeric_limits<double>::quiet_NaN();
     if (np > 0.0) {
       double d = dn / np;
       bool ok = true;
-      for (int it = 0; it < 6; ++it) {
-        const double gp = np + n2 * d;
+      for (int it = 0; it < 8; ++it) {
+        const double gp = np + d * (n2 + d * (0.5 * n3 + d * n4 / 6.0));
         if (!(gp > 0.0)) { ok = false; break; }
-        d -= (np * d + 0.5 * n2 * d * d - dn) / gp;
+        d -= (d * (np + d * (0.5 * n2 + d * (n3 / 6.0 + d * n4 / 24.0))) - dn) / gp;
       }
       if (ok && std::isfinite(d)) dq2 = d;
       if (ok && std::isfinite(d) && std::fabs(beta * d) <= lin) { dmu = d; done = true; break; }
@@ -1360,15 +1418,19 @@ sedacs_status fermi_density(sedacs_ctx* ctx, double* mu_io) {
   run_op(ctx, OP_T2, ns, ns);                                      // W_c = 2 Z_c F h~ Z
   run_op(ctx, ctx->zc == 0 ? OP_WC0 : OP_WC1, ns, 0);
   if (dmu != 0.0) {
-    const double c1 = beta * dmu, c2 = 0.5 * c1 * c1;
+    const double c1 = beta * dmu, c2 = 0.5 * c1 * c1, c3 = c2 * c1 / 3.0, c4 = c3 * c1 / 4.0;
     rows_axpy(ctx, kDc, kdDc, c1);
     rows_axpy(ctx, kDc, kdDt, c2);
-    run_op(ctx, OP_F_T2S, ns, ns);                                 // W_s = 2 Z_c s h~ Z -> kT1
-    run_op(ctx, ctx->zc == 0 ? OP_F_WS0 : OP_F_WS1, ns, 0);
-    rows_axpy(ctx, kWc, kT1, c1);
-    run_op(ctx, OP_F_T2T, ns, ns);                                 // W_t = 2 Z_c t h~ Z -> kT1
-    run_op(ctx, ctx->zc == 0 ? OP_F_WS0 : OP_F_WS1, ns, 0);
-    rows_axpy(ctx, kWc, kT1, c2);
+    rows_axpy(ctx, kDc, kdDu, c3);
+    rows_axpy(ctx, kDc, kdDw, c4);
+    // W_k = 2 Z_c X_k h~ Z (X_k = s, t, u, w) -> kT1, added with c_k
+    const int t2[4] = {OP_F_T2S, OP_F_T2T, OP_F_T2U, OP_F_T2W};
+    const double ck[4] = {c1, c2, c3, c4};
+    for (int k = 0; k < 4; ++k) {
+      run_op(ctx, t2[k], ns, ns);
+      run_op(ctx, ctx->zc == 0 ? OP_F_WS0 : OP_F_WS1, ns, 0);
+      rows_axpy(ctx, kWc, kT1, ck[k]);
+    }
   }
   ctx->fermi_dndmu = np;
   ctx->fermi_dmu = dmu;
@@ -1847,7 +1909,7 @@ sedacs_status sedacs_create(int32_t n_atoms, const int32_t* species, const doubl
   if (cudaMalloc(&ctx->d_vel, sizeof(double) * 3 * N) != cudaSuccess) return fail(SEDACS_ENOMEM, "alloc");
   if (cudaMalloc(&ctx->d_hist, sizeof(double) * 6 * N) != cudaSuccess) return fail(SEDACS_ENOMEM, "alloc");
   if (cudaMalloc(&ctx->d_vec, sizeof(double) * 24 * N) != cudaSuccess) return fail(SEDACS_ENOMEM, "alloc");
-  if (cudaMalloc(&ctx->d_rsp, sizeof(double) * 8 * N) != cudaSuccess) return fail(SEDACS_ENOMEM, "alloc");
+  if (cudaMalloc(&ctx->d_rsp, sizeof(double) * 9 * N) != cudaSuccess) return fail(SEDACS_ENOMEM, "alloc");
   if (cudaMalloc(&ctx->d_scal, sizeof(double) * 16) != cudaSuccess) return fail(SEDACS_ENOMEM, "alloc");
   if (cudaMalloc(&ctx->d_species, sizeof(int) * N) != cudaSuccess) return fail(SEDACS_ENOMEM, "alloc");
   cudaMemcpy(ctx->d_species, species, sizeof(int) * N, cudaMemcpyHostToDevice);
@@ -1878,7 +1940,7 @@ void sedacs_destroy(sedacs_ctx* ctx) {
                   ctx->d_views_x1, ctx->d_hoff, ctx->d_soff, ctx->d_dcoff, ctx->d_wcoff, ctx->d_rowbase,
                   ctx->d_tr_off, ctx->d_n_pad, ctx->d_n_real, ctx->d_n_diag, ctx->d_glo, ctx->d_ghi, ctx->d_bounds,
                   ctx->d_slots, ctx->d_sp2, ctx->d_nactive, ctx->d_dcoff_d, ctx->d_dqpop, ctx->d_dhoff,
-                  ctx->d_steps, ctx->d_rsp, ctx->d_dcoff_t};
+                  ctx->d_steps, ctx->d_rsp, ctx->d_dcoff_t, ctx->d_dcoff_u, ctx->d_dcoff_w};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto* v : ctx->d_views)

@@ -32,6 +32,8 @@ enum SlotId : int {
   kR1, kR2,            // response: X dX, and dX (ping-pong)
   kdH, kdHt, kdT1, kdDc,
   kdT2, kdDt,          // core rows of t = s (I - 2F) (second-order mu term): Z_c t, 2 Z_c t Z
+  kdT3, kdDu,          // core rows of the third-order term u: Z_c u, 2 Z_c u Z
+  kdT4, kdDw,          // core rows of the fourth-order term w: Z_c w, 2 Z_c w Z
   kNumSlots
 };
 
@@ -72,6 +74,12 @@ enum OpId : int {
   // degree-9 inverse in powers of V^3 (fp16 two-plane form): [V^3 | T_1] from one product V V^2 (two
   // outputs), T_2 = V^3 T_1 + B_1, r = V^3 T_2 + B_0
   OP_F_I3, OP_F_I4, OP_F_I5,
+  // third- and fourth-order mu terms: P = t F (kT), u = t - 2 P - 2 s s (kY0), its core rows
+  // (kdT3, kdDu), T2 = kdT3 h~; Q = u F (kT), w = u - 2 Q - 6 s t (kY1), rows (kdT4, kdDw), T2
+  OP_F_TF, OP_F_U, OP_F_UT1_0, OP_F_UT1_1, OP_F_DU0, OP_F_DU1, OP_F_T2U,
+  OP_F_UF, OP_F_W, OP_F_WT1_0, OP_F_WT1_1, OP_F_DW0, OP_F_DW1, OP_F_T2W,
+  // G = (I - V) r(V) from the last doubling (kT); s = F - F^2 = G^2 / 4 (OP_F_S)
+  OP_F_G,
   OP_NUM
 };
 
@@ -202,6 +210,8 @@ struct sedacs_ctx {
   int* d_nactive = nullptr;
   long long* d_dcoff_d = nullptr;   // core-row offsets of the response density
   long long* d_dcoff_t = nullptr;   // core-row offsets of the second-order mu term (kdDt)
+  long long* d_dcoff_u = nullptr;   // ... of the third-order term (kdDu)
+  long long* d_dcoff_w = nullptr;   // ... of the fourth-order term (kdDw)
   double* d_dqpop = nullptr;        // response populations scratch
   long long* d_dhoff = nullptr;     // per-subgraph offsets of the response Hamiltonian
   int* d_steps = nullptr;           // SP2 step counts of the last density call
