@@ -57,10 +57,12 @@ def parse():
 METRIC = "atoms*QMD-steps/s at |dq|<=1e-5 e vs FP64 oracle (mixed vs plain, one GB300)"
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the Fermi-recursion
-# product kernel (tc_gemm_persistent<2, true>) on the small capture case (bench.py --profile-case,
-# 3,000-atom water box), scaled to the 9,000-atom workload by the ratio of the subgraphs' padded
-# sizes; reported only while the kernel source is the one the counters were taken on.
-FERMI_TRAFFIC = None
+# product kernel (tc_gemm_persistent<2, true>) on the benchmarked 9,000-atom workload: the mean over
+# its 136 launches in the NVTX range 'timed' of `bench.py --no-plain --no-frames --no-cpu-baseline
+# --steps 2 --warmup 1` (one ncu pass, so the full workload could be captured); reported only while
+# the kernel source is the one the counters were taken on (profiles/launches_water9000.md).
+FERMI_TRAFFIC = {"kernel_sha1": "f1e27abead4ca70ebedad479f3f8cb922699ee59", "precision": 1,
+                 "workload": "water9000", "bytes_per_launch": 998.1e6}
 
 
 def strip_comments(src: str) -> str:
@@ -323,6 +325,7 @@ def run_ours(args, world, rank, local):
     S.sedacs_kernel_stats(ctx, True)
     S.sedacs_xlbomd_step(ctx, Rh, Vh, 4, args.dt)
     k_ms, k_launch, k_flops = S.sedacs_kernel_stats(ctx, False)
+    f16_ms, f16_launch, f16_flops, f16_bytes = S.sedacs_kernel_stats_fp16(ctx)
     ph4, _ = S.sedacs_phase_times(ctx)
     # oracle check of sampled subgraphs at the kept frames
     acc = None
@@ -350,29 +353,60 @@ def run_ours(args, world, rank, local):
     bf16 = peaks.get("bf16_tflops_sustained", 1700.0)
     peak_src = "of measured" if "bf16_tflops_sustained" in peaks else "of fallback"
     split = {1: 3, 2: 3, 3: 1, 4: 6}.get(args.precision, 6)
-    # algorithmic work: a symmetric product of two n x n matrices (upper triangle) = n^3 flops
-    achieved = (k_flops / (k_ms / 1e3)) / 1e12 if k_ms > 0 else None
-    if args.precision == 0:
-        kname, bound, peak = "f64_gemm_kernel (Fermi-recursion products, FP64 CUDA cores)", "alu", 1.25
-        peak_note = "nominal FP64 1.25 TF/s (no measured FP64 peak)"
-    else:
-        kname = ("tc_gemm_persistent<2,F16> (Fermi-recursion products, two-plane fp16 on tcgen05)" if args.precision == 1
-                 else "tc_gemm_persistent (Fermi-recursion products, split bf16 on tcgen05)")
-        bound, peak = "tensor", bf16
-        peak_note = (f"measured sustained dense bf16 {bf16} TF/s {peak_src} (fp16 runs at the bf16 rate); the "
-                     f"FP32-class product costs {split} tensor-core products, counted as work of the kernel, not "
-                     f"of the method")
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    hbm_src = "of measured" if "hbm_gbs" in peaks else "of fallback"
     traffic = None
     if FERMI_TRAFFIC and kernel_sha1() == FERMI_TRAFFIC["kernel_sha1"] and args.precision == FERMI_TRAFFIC["precision"] \
             and args.workload == FERMI_TRAFFIC["workload"]:
         traffic = FERMI_TRAFFIC["bytes_per_launch"]
-    roof = {"kernel": kname, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-            "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
-            "split_products": split, "tensor_frac_with_split_products": (achieved * split / peak) if achieved else None,
-            "peak_note": peak_note, "launches": k_launch, "kernel_ms": k_ms,
-            "work_note": "flops = sum over launches of sum_i n_i^3 (one symmetric product per subgraph, upper "
-                         "triangle, n_i the orbital count)"}
+    if args.precision == 1 and f16_ms > 0:
+        # the dominant kernel: the products in two fp16 planes.  Roofline: its algorithmic bytes
+        # (operands once, FP32 addends, output planes and master, over the upper triangles) against
+        # the measured HBM copy bandwidth, and its algorithmic flops (n^3 per symmetric product) x 3
+        # tensor-core products against the measured bf16 rate; the larger fraction is the bound
+        bw = f16_bytes / (f16_ms / 1e3) / 1e9
+        tf = f16_flops / (f16_ms / 1e3) / 1e12
+        f_bw, f_tf = bw / hbm, tf * split / bf16
+        kname = "tc_gemm_persistent<2,F16> (Fermi-recursion products, two-plane fp16 on tcgen05)"
+        if f_bw >= f_tf:
+            bound, achieved, peak, unit = "hbm", bw, hbm, "GB/s"
+        else:
+            bound, achieved, peak, unit = "tensor", tf, bf16, "TFLOP/s"
+        roof = {"kernel": kname, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak, "traffic": traffic,
+                "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
+                "algorithmic_bytes_per_launch": f16_bytes / f16_launch,
+                "hbm": {"achieved_gbs": bw, "peak_gbs": hbm, "frac": f_bw, "peak_note": f"STREAM copy {hbm_src}"},
+                "tensor": {"achieved_tflops": tf, "peak_tflops": bf16, "frac": tf / bf16,
+                           "frac_with_split_products": f_tf, "split_products": split,
+                           "peak_note": f"dense bf16 sustained {peak_src} (fp16 runs at the bf16 rate); the FP32-class "
+                                        f"product costs {split} tensor-core products"},
+                "launches": f16_launch, "kernel_ms": f16_ms,
+                "work_note": "bytes: per launch, over the upper triangle of every subgraph (n (n+1)/2 elements), operands "
+                             "read once (4 B an element in two fp16 planes; once when A = B), each FP32 addend (4 B), "
+                             "output planes (4 B, 6 B in three bf16 planes), FP32 master (4 B) unless planes-only, second "
+                             "output (4 B); flops: n^3 per symmetric product",
+                "all_fermi_products": {"launches": k_launch, "kernel_ms": k_ms,
+                                       "tflops_algorithmic": (k_flops / (k_ms / 1e3)) / 1e12 if k_ms > 0 else None}}
+    else:
+        # algorithmic work: a symmetric product of two n x n matrices (upper triangle) = n^3 flops
+        achieved = (k_flops / (k_ms / 1e3)) / 1e12 if k_ms > 0 else None
+        if args.precision == 0:
+            kname, bound, peak = "f64_gemm_kernel (Fermi-recursion products, FP64 CUDA cores)", "alu", 1.25
+            peak_note = "nominal FP64 1.25 TF/s (no measured FP64 peak)"
+        else:
+            kname = "tc_gemm_persistent (Fermi-recursion products, split bf16 on tcgen05)"
+            bound, peak = "tensor", bf16
+            peak_note = (f"measured sustained dense bf16 {bf16} TF/s {peak_src}; the FP32-class product costs {split} "
+                         f"tensor-core products, counted as work of the kernel, not of the method")
+        roof = {"kernel": kname, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
+                "split_products": split,
+                "tensor_frac_with_split_products": (achieved * split / peak) if achieved else None,
+                "peak_note": peak_note, "launches": k_launch, "kernel_ms": k_ms,
+                "work_note": "flops = sum over launches of sum_i n_i^3 (one symmetric product per subgraph, upper "
+                             "triangle, n_i the orbital count)"}
     plain = None
     if not args.no_plain and args.precision != 0 and rank == 0:
         q64, t64 = run_plain(args, S, model, s, R0, V0, n0, mu0, gd0)

@@ -262,6 +262,14 @@ sedacs_status sedacs_reset_counters(sedacs_ctx* ctx);
  * as n^3 (n the orbital count of the subgraph), since the last reset. */
 sedacs_status sedacs_kernel_stats(sedacs_ctx* ctx, int32_t on, double* sp2_ms, int64_t* sp2_launches,
                                   double* sp2_flops);
+/* The part of those statistics from the products in two fp16 planes (the recursion of the
+ * FP32-class form 1), with their algorithmic DRAM bytes: over the upper triangle of every
+ * n x n subgraph (n (n + 1) / 2 elements), the operands read once (4 bytes an element; one read
+ * when both operands are the same matrix), each FP32 addend (4), the output planes (4, or 6 in
+ * three bf16 planes), the FP32 master (4) unless the product keeps planes only, and a second
+ * output (4).  Outputs are host scalars; counters as for sedacs_kernel_stats. */
+sedacs_status sedacs_kernel_stats_fp16(sedacs_ctx* ctx, double* ms, int64_t* launches, double* flops,
+                                       double* bytes);
 
 /* ---- Allocation-free distance graph.  The paper has no counterpart to this entry point;
  * it exists for callers that cannot allocate device memory at the time of the call (programs

@@ -452,6 +452,9 @@ sedacs_status build_op(sedacs_ctx* ctx, int id, int a, int b, int out, int mode,
   stage_bytes(ctx, op.mats_d, mats.data(), sizeof(GemmMat) * L.n_sub);
   stage_bytes(ctx, op.work_d, work.data(), sizeof(GemmWork) * work.size());
   op.n_work = (int)work.size();
+  op.same_ab = (a == b && ca == cb && a_from_sp2 == b_from_sp2) ? 1 : 0;
+  op.n_addends = (c1 >= 0 ? 1 : 0) + (c2 >= 0 ? 1 : 0);
+  op.dual = out2 >= 0 ? 1 : 0;
   op.alpha = alpha;
   op.beta = beta;
   op.g1 = g1;
@@ -718,7 +721,11 @@ sedacs_status rebuild_layout(sedacs_ctx* ctx) {
     L.max_mpad = std::max(L.max_mpad, L.m_pad[i]);
   }
   ctx->sum_n3 = 0.0;
-  for (int i = 0; i < P; ++i) ctx->sum_n3 += (double)L.n_real[i] * L.n_real[i] * L.n_real[i];
+  ctx->sum_tri = 0.0;
+  for (int i = 0; i < P; ++i) {
+    ctx->sum_n3 += (double)L.n_real[i] * L.n_real[i] * L.n_real[i];
+    ctx->sum_tri += 0.5 * (double)L.n_real[i] * (L.n_real[i] + 1);
+  }
   // arena slots
   const int esz = ctx->f64 ? 8 : 4;
   const bool planes = !ctx->f64;
@@ -1112,14 +1119,32 @@ int fermi_doublings(const sedacs_ctx* ctx, double mu) {
 // One launch of a Fermi-recursion product, with per-launch CUDA events when kernel statistics are
 // on; a symmetric product counts n^3 flops per subgraph (upper triangle), a core-row product is
 // not counted.
+// The fp16 two-plane launches are also tallied apart, with their algorithmic DRAM bytes: over the
+// upper triangle of every n x n subgraph (n (n + 1) / 2 elements), the operands once (4 bytes an
+// element in two fp16 planes; one read when A and B are the same matrix), each FP32 addend (4),
+// the output planes (4, or 6 in three bf16 planes), its FP32 master (4) unless the op keeps
+// planes only, and a second output's planes (4).
 void run_fop(sedacs_ctx* ctx, int id, int nin, int nout) {
   const bool rec = ctx->kstats && ctx->kev_used + 2 <= (int)ctx->kev.size();
   if (rec) cudaEventRecord(ctx->kev[ctx->kev_used], ctx->stream);
   run_op(ctx, id, nin, nout);
   if (rec) {
     cudaEventRecord(ctx->kev[ctx->kev_used + 1], ctx->stream);
+    const GemmOp& op = ctx->ops[id];
+    double bytes = -1.0;
+    if (!ctx->f64 && nin == kPlanesF16x2 && op.sym) {
+      const int master = (nout == kPlanesF16x2 && op.no_master) ? 0 : 4;
+      const double per = 4.0 * (op.same_ab ? 1 : 2) + 4.0 * op.n_addends + (nout == 3 ? 6.0 : 4.0) + master +
+                         4.0 * op.dual;
+      bytes = per * ctx->sum_tri;
+    }
+    if ((int)ctx->kev_bytes.size() < (int)ctx->kev.size()) ctx->kev_bytes.resize(ctx->kev.size(), -1.0);
+    ctx->kev_bytes[ctx->kev_used] = bytes;
     ctx->kev_used += 2;
-    if (ctx->ops[id].sym) ctx->k_flops += ctx->sum_n3;
+    if (op.sym) {
+      ctx->k_flops += ctx->sum_n3;
+      if (bytes >= 0.0) ctx->k16_flops += ctx->sum_n3;
+    }
   }
 }
 
@@ -1132,6 +1157,12 @@ void drain_kstats(sedacs_ctx* ctx, int ev0) {
     cudaEventElapsedTime(&ms, ctx->kev[e], ctx->kev[e + 1]);
     ctx->k_ms += ms;
     ctx->k_launches += 1;
+    if (e < (int)ctx->kev_bytes.size() && ctx->kev_bytes[e] >= 0.0) {
+      ctx->k16_ms += ms;
+      ctx->k16_launches += 1;
+      ctx->k16_bytes += ctx->kev_bytes[e];
+      ctx->kev_bytes[e] = -1.0;
+    }
   }
   ctx->kev_used = ev0;
 }
@@ -2531,11 +2562,23 @@ sedacs_status sedacs_kernel_stats(sedacs_ctx* ctx, int32_t on, double* sp2_ms, i
   return SEDACS_OK;
 }
 
+sedacs_status sedacs_kernel_stats_fp16(sedacs_ctx* ctx, double* ms, int64_t* launches, double* flops,
+                                       double* bytes) {
+  if (!ctx) return SEDACS_EINVAL;
+  if (ms) *ms = ctx->k16_ms;
+  if (launches) *launches = ctx->k16_launches;
+  if (flops) *flops = ctx->k16_flops;
+  if (bytes) *bytes = ctx->k16_bytes;
+  return SEDACS_OK;
+}
+
 sedacs_status sedacs_reset_counters(sedacs_ctx* ctx) {
   if (!ctx) return SEDACS_EINVAL;
   ctx->k_ms = 0.0;
   ctx->k_flops = 0.0;
   ctx->k_launches = 0;
+  ctx->k16_ms = ctx->k16_flops = ctx->k16_bytes = 0.0;
+  ctx->k16_launches = 0;
   for (double& x : ctx->t_phase) x = 0.0;
   ctx->launches = 0;
   return SEDACS_OK;

@@ -47,6 +47,9 @@ struct GemmOp {
   int ops_upper = 0;         // operands stored as upper tiles (fp16 two-plane path)
   int store_upper = 0;       // result stored as upper tiles (no mirror)
   int no_master = 0;         // fp16 two-plane path: result kept as planes only (no FP32 master)
+  int same_ab = 0;           // A and B are one matrix (read once)
+  int n_addends = 0;         // C1 / C2 added in the epilogue (FP32 masters)
+  int dual = 0;              // second output (planes)
 };
 
 enum OpId : int {
@@ -256,6 +259,11 @@ struct sedacs_ctx {
   int kev_used = 0;
   double k_ms = 0.0, k_flops = 0.0;
   long long k_launches = 0;
+  // the same for the fp16 two-plane products alone, with their algorithmic bytes
+  std::vector<double> kev_bytes;   // per recorded launch: bytes (fp16 launches), -1 otherwise
+  double k16_ms = 0.0, k16_flops = 0.0, k16_bytes = 0.0;
+  long long k16_launches = 0;
+  double sum_tri = 0.0;            // sum over subgraphs of n (n + 1) / 2
   // timing
   cudaEvent_t ev[10] = {};
   double t_phase[8] = {0, 0, 0, 0, 0, 0, 0, 0};

@@ -74,6 +74,7 @@ def _load():
         "sedacs_phase_times": (I32, [P, P, P]),
         "sedacs_reset_counters": (I32, [P]),
         "sedacs_kernel_stats": (I32, [P, I32, P, P, P]),
+        "sedacs_kernel_stats_fp16": (I32, [P, P, P, P, P]),
         "sedacs_set_params": (I32, [P, P]),
         "sedacs_graph_build_noalloc": (I32, [P, I32, P, D, P, P, I64, P, P]),
         "sedacs_gnn_num_params": (I32, []),
@@ -106,6 +107,7 @@ EXPORTED = (
     "sedacs_kernel_stats", "sedacs_set_params", "sedacs_graph_build_noalloc", "sedacs_gnn_num_params",
     "sedacs_gnn_init", "sedacs_gnn_set_params", "sedacs_gnn_get_params", "sedacs_gnn_apply", "sedacs_gnn_param_grad",
     "sedacs_gnn_collect", "sedacs_gnn_train", "sedacs_kernel_judge", "sedacs_density_info", "sedacs_charges",
+    "sedacs_kernel_stats_fp16",
 )
 
 
@@ -340,6 +342,16 @@ def sedacs_kernel_stats(ctx, on: bool = True):
     fl = C.c_double()
     _check(ctx, _lib.sedacs_kernel_stats(ctx, 1 if on else 0, C.byref(ms), C.byref(nl), C.byref(fl)))
     return ms.value, nl.value, fl.value
+
+
+def sedacs_kernel_stats_fp16(ctx):
+    """(ms, launches, flops, algorithmic bytes) of the two-plane fp16 products since the last reset."""
+    ms = C.c_double()
+    nl = C.c_int64()
+    fl = C.c_double()
+    by = C.c_double()
+    _check(ctx, _lib.sedacs_kernel_stats_fp16(ctx, C.byref(ms), C.byref(nl), C.byref(fl), C.byref(by)))
+    return ms.value, nl.value, fl.value, by.value
 
 
 def sedacs_graph_build_noalloc(R_dev, box, r_graph: float, row_ptr_dev, col_dev, stream: int = 0) -> tuple[int, int]:
