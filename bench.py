@@ -60,7 +60,7 @@ METRIC = "atoms*QMD-steps/s at |dq|<=1e-5 e vs FP64 oracle (mixed vs plain, one 
 # product kernel (tc_gemm_persistent<2, true>) on the benchmarked 9,000-atom workload: the mean over
 # its 136 launches in the NVTX range 'timed' of `bench.py --no-plain --no-frames --no-cpu-baseline
 # --steps 2 --warmup 1` (one ncu pass, so the full workload could be captured); reported only while
-# the kernel source is the one the counters were taken on (profiles/launches_water9000.md).
+# the kernel source is the one the counters were taken on.
 FERMI_TRAFFIC = {"kernel_sha1": "f1e27abead4ca70ebedad479f3f8cb922699ee59", "precision": 1,
                  "workload": "water9000", "bytes_per_launch": 998.1e6}
 
