@@ -19,6 +19,14 @@ Test infrastructure only (see ``oracle/__init__``).
   METIS community detection here; RCB is the deterministic stand-in.
 * Halo (Fig. 1c): the graph neighbours of the core atoms that are not core atoms.
   Subgraph order: core atoms ascending, then halo atoms ascending.
+* Weighted two-hop adaptation (Sec. "Dynamic Graph Adaption", Eqs. "neigh_mat" and
+  "Graph_Adaptation"): G^N_IK = exp(-alpha R_IK^2) on the neighbour list, G^N_II = 1;
+  P = G^N G^D with G^D in the row form the collection produces (each atom's row from
+  the subgraph it is core of); edge (I, J), I != J, when P_IJ > tau or P_JI > tau
+  (each subgraph's product thresholded, then collected and symmetrised).  The
+  neighbour list holds the pairs with exp(-alpha R^2) >= tau / 2 (R^2 < ln(2/tau) /
+  alpha): a two-hop path through a longer pair weighs less than tau, since G^D <= 2.
+  P_IJ is summed over K in ascending order, each term w * v rounded and then added.
 
 Pinned by tests against brute force on tiny inputs (edge sets, partition sizes,
 halo sets recomputed by explicit loops) and by the bit-exact CSR invariants.
@@ -129,3 +137,62 @@ def halos(row_ptr: np.ndarray, col: np.ndarray, cores: list[np.ndarray]) -> list
 def subgraphs(cores, halo_lists):
     """Atom lists of every core+halo subgraph (core ascending, then halo ascending)."""
     return [np.concatenate([c, h]).astype(np.int64) for c, h in zip(cores, halo_lists)]
+
+
+def two_hop_rn2(alpha: float, tau: float) -> float:
+    """Squared neighbour-list radius of the weighted two-hop rule: exp(-alpha R^2) >= tau / 2."""
+    return float(np.log(2.0 / tau) / alpha)
+
+
+def two_hop_products(R: np.ndarray, box: np.ndarray, gd, alpha: float, tau: float):
+    """Rows of P = G^N G^D: a list over atoms I of dicts {J: P_IJ} (every J reached)."""
+    R = np.asarray(R, dtype=np.float64)
+    box = np.asarray(box, dtype=np.float64)
+    N = R.shape[0]
+    rn2 = two_hop_rn2(alpha, tau)
+    ptr, col, val = gd
+    allj = np.arange(N)
+    rows = []
+    for i in range(N):
+        r2 = min_image_r2(R, box, i, allj)
+        ks = [int(k) for k in np.nonzero(r2 < rn2)[0]]          # ascending, i itself included
+        acc = {}
+        for k in ks:
+            w = 1.0 if k == i else float(np.exp(-alpha * r2[k]))
+            for p in range(int(ptr[k]), int(ptr[k + 1])):
+                j = int(col[p])
+                acc[j] = acc.get(j, 0.0) + w * float(val[p])
+        rows.append(acc)
+    return rows
+
+
+def build_graph_two_hop(R: np.ndarray, box: np.ndarray, gd, alpha: float, tau: float, keep=None):
+    """Symmetric CSR of G_tau = (G^N G^D + G^D G^N)|_tau, read as P = G^N G^D thresholded and
+    symmetrised: edge (I, J), I != J, when P_IJ > tau or P_JI > tau; keep as in build_graph.
+    Returns (row_ptr, col, ambiguous): ambiguous lists the pairs whose deciding products lie
+    within 1e-12 tau of tau (where another rounding of exp may decide the other way)."""
+    N = np.asarray(R).shape[0]
+    rows = two_hop_products(R, box, gd, alpha, tau)
+    adj = [set() for _ in range(N)]
+    amb = set()
+    for i in range(N):
+        for j, v in rows[i].items():
+            if j == i:
+                continue
+            if abs(v - tau) <= 1e-12 * tau:
+                amb.add((min(i, j), max(i, j)))
+            if v > tau:
+                adj[i].add(j)
+                adj[j].add(i)
+    if keep is not None:
+        kp, kc = keep
+        for i in range(N):
+            for p in range(int(kp[i]), int(kp[i + 1])):
+                adj[i].add(int(kc[p]))
+    row_ptr = np.zeros(N + 1, dtype=np.int64)
+    cols = []
+    for i in range(N):
+        c = sorted(adj[i])
+        cols.extend(c)
+        row_ptr[i + 1] = row_ptr[i] + len(c)
+    return row_ptr, np.asarray(cols, dtype=np.int32), sorted(amb)

@@ -129,3 +129,78 @@ def test_graph_keep_is_union_of_kept_and_rule_edges():
     # symmetric
     edges = {(i, int(j)) for i in range(N) for j in cu[rpu[i]:rpu[i + 1]]}
     assert all((j, i) in edges for i, j in edges)
+
+
+# ---- weighted two-hop graph adaptation (Sec. "Dynamic Graph Adaption", Eq. "Graph_Adaptation") ----
+
+def _gd_of_first_density(s, core_size, seed=3):
+    from oracle import density as odn
+    from paper_2606_03140_gb300 import inputs as I
+
+    m = I.default_model()
+    n = I.random_charges(s.n_atoms, seed, 0.05)
+    rp, col = graph.build_graph(s.R, s.box, 3.0)
+    cores = graph.rcb_partition(s.R, s.box, core_size)
+    r0 = odn.density(s.R, s.species, s.box, m, n, cores, graph.halos(rp, col, cores))
+    return m, n, cores, r0
+
+
+def test_two_hop_products_and_graph_against_dense_matrices():
+    """P = G^N G^D and the thresholded, symmetrised graph against dense matrices built by
+    brute force: G^N from every pair's minimum-image distance, G^D from the CSR."""
+    from paper_2606_03140_gb300 import inputs as I
+
+    s = I.workload("water96")
+    _, _, _, r0 = _gd_of_first_density(s, 12)
+    alpha, tau = 0.7, 1e-3
+    N = s.n_atoms
+    rn2 = graph.two_hop_rn2(alpha, tau)
+    GN = np.zeros((N, N))
+    for i in range(N):
+        r2 = graph.min_image_r2(s.R, s.box, i, np.arange(N))
+        keep = r2 < rn2
+        GN[i, keep] = np.exp(-alpha * r2[keep])
+        GN[i, i] = 1.0
+    ptr, col, val = r0.gd
+    GD = np.zeros((N, N))
+    for i in range(N):
+        np.add.at(GD[i], col[ptr[i]:ptr[i + 1]], val[ptr[i]:ptr[i + 1]])
+    P = GN @ GD
+    rows = graph.two_hop_products(s.R, s.box, r0.gd, alpha, tau)
+    for i in range(N):
+        for j, v in rows[i].items():
+            assert abs(v - P[i, j]) <= 1e-13 * max(1.0, abs(P[i, j]))
+        assert np.count_nonzero(P[i]) == len(rows[i])
+    E = (P > tau) | (P > tau).T
+    np.fill_diagonal(E, False)
+    rp, cl, amb = graph.build_graph_two_hop(s.R, s.box, r0.gd, alpha, tau)
+    assert amb == []
+    for i in range(N):
+        assert list(cl[rp[i]:rp[i + 1]]) == list(np.nonzero(E[i])[0])
+    # every |D| edge above tau is kept (G^N_II = 1), and the rule reaches two hops beyond it
+    rp1, cl1 = graph.build_graph(s.R, s.box, 0.0, r0.gd, tau)
+    for i in range(N):
+        assert set(cl1[rp1[i]:rp1[i + 1]]) <= set(cl[rp[i]:rp[i + 1]])
+    assert len(cl) > len(cl1)
+
+
+def test_two_hop_threshold_controls_accuracy():
+    """Sec. "Accuracy Control via Graph Thresholding": with the two-hop graph the band energy and
+    the charges approach the single-partition reference as tau falls (monotone, power law)."""
+    from oracle import density as odn
+    from paper_2606_03140_gb300 import inputs as I
+
+    s = I.small_water_box(60, 13.0, seed=41)
+    m, n, cores, r0 = _gd_of_first_density(s, 12, seed=5)
+    full_c, full_h = odn.full_partition(s.n_atoms)
+    ref = odn.density(s.R, s.species, s.box, m, n, full_c, full_h)
+    errs = []
+    taus = (3e-2, 1e-2, 3e-3, 1e-3)
+    for tau in taus:
+        rp, cl, _ = graph.build_graph_two_hop(s.R, s.box, r0.gd, 0.7, tau)
+        res = odn.density(s.R, s.species, s.box, m, n, cores, graph.halos(rp, cl, cores))
+        errs.append((abs(res.e_band - ref.e_band) / s.n_atoms, float(np.max(np.abs(res.q - ref.q)))))
+    e = np.array(errs)
+    assert np.all(np.diff(e[:, 0]) < 0) and np.all(np.diff(e[:, 1]) < 0), e
+    slope = np.polyfit(np.log(taus), np.log(e[:, 1]), 1)[0]
+    assert slope > 0.3, (slope, e)
