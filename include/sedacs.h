@@ -102,12 +102,21 @@ typedef struct {
                            X_3 = t (I - 2F) - 2 s^2, X_4 = X_3 (I - 2F) - 6 s t) when |beta dmu| is at
                            most this; otherwise another pass runs (0: 0.2 in the FP32-class forms,
                            1e-2 in FP64; remainder <= (beta dmu)^5 / 120 x 0.25 per occupation) */
+  int32_t graph_rule;   /* graph from the previous density graph G^D: 0 = edge when the minimum-image
+                           distance is below r_graph or G^D exceeds tau in either direction; 1 = the
+                           weighted two-hop rule (Sec. "Dynamic Graph Adaption", Eq.
+                           "Graph_Adaptation"): P = G^N G^D with G^N_IK = exp(-graph_alpha R_IK^2)
+                           on the pairs with R^2 < ln(2 / tau) / graph_alpha (Angstrom) and
+                           G^N_II = 1, edge when P_IJ or P_JI exceeds tau (r_graph unused).  Without
+                           a density graph (first build) both use the distance rule.  A G^D row
+                           holding more than ~1,500 distinct two-hop columns -> SEDACS_ECAPACITY. */
+  double graph_alpha;   /* G^N decay, Angstrom^-2 (paper: 0.7) */
 } sedacs_params;
 
 /* Fill p with the defaults (r_graph 3.0, tau 1e-3, core_size 32, precision 1, kernel 0,
  * krylov_rank 4, krylov_tol 1e-2, c_k0 0.5, scc_tol 1e-8, scc_alpha 0.2, sp2_tol 0,
  * sp2_kmax 60, ns_iters 0, ewald_tol 0, judge_every 20, judge_tol 0.1, Te 300, mu_given 0,
- * fermi_lin 0). */
+ * fermi_lin 0, graph_rule 0, graph_alpha 0.7). */
 void sedacs_default_params(sedacs_params* p);
 
 /* Create a context for N atoms of the given species in an orthorhombic periodic box

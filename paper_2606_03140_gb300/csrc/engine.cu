@@ -1572,7 +1572,8 @@ sedacs_status graph_core(sedacs_ctx* ctx, const long long* gptr, const int* gcol
                                                                                    : cudaErrorMemoryAllocation);
   long long nnz = 0;
   CUCHK(ctx->gb.build(ctx->d_R, ctx->N, ctx->box, ctx->prm.r_graph, gptr, gcol, gval, ctx->prm.tau, ctx->d_row_ptr,
-                      &ctx->d_col, &ctx->col_cap, &nnz, ctx->d_err, s, true, keep_prev && ctx->have_graph));
+                      &ctx->d_col, &ctx->col_cap, &nnz, ctx->d_err, s, true, keep_prev && ctx->have_graph,
+                      ctx->prm.graph_rule, ctx->prm.graph_alpha));
   ctx->launches += 9;
   ctx->nnz = nnz;
   ctx->have_graph = true;
@@ -1876,7 +1877,9 @@ void sedacs_default_params(sedacs_params* p) {
   p->ewald_tol = 0.0;
   p->Te = 300.0;
   p->mu_given = 0;
-  p->fermi_lin = 0.0;   // automatic: 5e-3 in the FP32-class forms, 1e-4 in FP64
+  p->fermi_lin = 0.0;   // automatic: 0.2 in the FP32-class forms, 1e-2 in FP64
+  p->graph_rule = 0;
+  p->graph_alpha = 0.7;
 }
 
 sedacs_status sedacs_create(int32_t n_atoms, const int32_t* species, const double box[3], const sedacs_model* model,

@@ -18,6 +18,8 @@
 // core, ascending, from a per-core bitmap.
 #include "graph.cuh"
 
+#include <cmath>
+
 namespace sedacs {
 
 namespace {
@@ -272,6 +274,88 @@ __global__ void compact_kernel(const long long* cptr, const int* cand, const lon
   for (int t = threadIdx.x; t < n; t += blockDim.x) col[d + t] = cand[s + t];
 }
 
+// Weighted two-hop rule (Sec. "Dynamic Graph Adaption", Eq. "Graph_Adaptation"), one block per
+// atom I: P_IJ = sum over K in {I} and I's neighbour row (ascending K) of G^N_IK G^D_KJ, with
+// G^N_II = 1 and G^N_IK = exp(-alpha R_IK^2), accumulated per J in a shared-memory hash table.
+// Each G^D row lists a J once, so within one K only one thread updates J's slot, and the slots
+// take their terms in ascending K (separately rounded FP64 products and sums): the values do not
+// depend on scheduling.  COUNT: the number of J != I with P_IJ > tau; FILL: those (J, P_IJ).
+constexpr int kTwoHopSlots = 2048;
+
+template <bool FILL>
+__global__ void twohop_kernel(const double* R, int N, CellGrid g, const long long* nptr, const int* ncol,
+                              const long long* gptr, const int* gcol, const double* gval, double alpha, double tau,
+                              int* pcnt, const long long* pptr, int* pcol, double* pval, int* err) {
+  __shared__ int key[kTwoHopSlots];
+  __shared__ double acc[kTwoHopSlots];
+  __shared__ int s_n, s_fail, s_pos;
+  const int i = blockIdx.x;
+  for (int t = threadIdx.x; t < kTwoHopSlots; t += blockDim.x) {
+    key[t] = -1;
+    acc[t] = 0.0;
+  }
+  const long long b = nptr[i];
+  const int deg = (int)(nptr[i + 1] - b);
+  if (threadIdx.x == 0) {
+    s_n = 0;
+    s_fail = 0;
+    int pos = 0;                                   // I's place among its sorted neighbours
+    while (pos < deg && ncol[b + pos] < i) ++pos;
+    s_pos = pos;
+  }
+  __syncthreads();
+  const int pos_i = s_pos;
+  for (int m = 0; m <= deg; ++m) {
+    int k;
+    double w;
+    if (m == pos_i) {
+      k = i;
+      w = 1.0;
+    } else {
+      k = ncol[b + (m < pos_i ? m : m - 1)];
+      w = exp(__dmul_rn(-alpha, min_image_r2(R, i, k, g.box)));
+    }
+    for (long long p = gptr[k] + threadIdx.x; p < gptr[k + 1]; p += blockDim.x) {
+      const int j = gcol[p];
+      if (j < 0 || j >= N) continue;
+      const double term = __dmul_rn(w, gval[p]);
+      unsigned h = ((unsigned)j * 2654435761u) >> (32 - 11);
+      int probes = 0;
+      for (;;) {
+        const int old = atomicCAS(&key[h], -1, j);
+        if (old == -1 || old == j) {
+          acc[h] = __dadd_rn(acc[h], term);
+          break;
+        }
+        h = (h + 1) & (kTwoHopSlots - 1);
+        if (++probes >= kTwoHopSlots) {
+          s_fail = 1;
+          break;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (s_fail) {
+    if (threadIdx.x == 0) {
+      atomicOr(err, kErrCapacity);
+      if (!FILL) pcnt[i] = 0;
+    }
+    return;
+  }
+  for (int t = threadIdx.x; t < kTwoHopSlots; t += blockDim.x) {
+    const int j = key[t];
+    if (j < 0 || j == i || !(acc[t] > tau)) continue;
+    const int slot = atomicAdd(&s_n, 1);
+    if (FILL && slot < (int)(pptr[i + 1] - pptr[i])) {   // the count pass sized the row
+      pcol[pptr[i] + slot] = j;
+      pval[pptr[i] + slot] = acc[t];
+    }
+  }
+  __syncthreads();
+  if (!FILL && threadIdx.x == 0) pcnt[i] = s_n;
+}
+
 // Exclusive scan of int counts into int64 offsets (single CTA, N up to a few 1e5).
 __global__ void scan_kernel(const int* cnt, int N, long long* out) {
   __shared__ long long part[1024];
@@ -447,13 +531,17 @@ GraphBuilder::~GraphBuilder() { release(); }
 
 void GraphBuilder::release() {
   for (void* p : {(void*)cell_of, (void*)cell_count, (void*)cell_start, (void*)cell_fill, (void*)cell_atoms,
-                  (void*)cnt, (void*)fillc, (void*)ucnt, (void*)cptr, (void*)cand})
+                  (void*)cnt, (void*)fillc, (void*)ucnt, (void*)cptr, (void*)cand, (void*)n_cnt, (void*)n_ptr,
+                  (void*)n_col, (void*)p_cnt, (void*)p_ptr, (void*)p_col, (void*)p_val})
     if (p) cudaFree(p);
   cell_of = cell_count = cell_start = cell_fill = cell_atoms = cnt = fillc = ucnt = nullptr;
   cptr = nullptr;
   cand = nullptr;
+  n_cnt = p_cnt = n_col = p_col = nullptr;
+  n_ptr = p_ptr = nullptr;
+  p_val = nullptr;
   cap_n = cap_cells = 0;
-  cap_cand = 0;
+  cap_cand = cap_ncol = cap_p = 0;
 }
 
 static CellGrid make_grid(const double box[3], double rc, int exact = 1) {
@@ -473,9 +561,11 @@ static CellGrid make_grid(const double box[3], double rc, int exact = 1) {
 cudaError_t GraphBuilder::build(const double* dR, int N, const double box[3], double r_graph, const long long* gptr,
                                 const int* gcol, const double* gval, double tau, long long* row_ptr, int** col_out,
                                 long long* col_cap, long long* nnz_host, int* derr, cudaStream_t s, bool exact,
-                                bool keep_prev) {
+                                bool keep_prev, int rule, double alpha) {
   cudaError_t e;
-  CellGrid g = make_grid(box, r_graph, exact ? 1 : 0);
+  const bool two_hop = rule == 1 && gptr != nullptr;
+  const double rn2 = two_hop ? std::log(2.0 / tau) / alpha : 0.0;   // G^N neighbour list: R^2 < rn2
+  CellGrid g = make_grid(box, two_hop ? std::sqrt(rn2) : r_graph, exact ? 1 : 0);
   const int ncell = g.nc[0] * g.nc[1] * g.nc[2];
   if (N > cap_n) {
     for (int** p : {&cell_of, &cnt, &fillc, &ucnt}) { if (*p) cudaFree(*p); *p = nullptr; }
@@ -487,6 +577,12 @@ cudaError_t GraphBuilder::build(const double* dR, int N, const double box[3], do
     if ((e = cudaMalloc(&cptr, sizeof(long long) * (N + 1)))) return e;
     if (cell_atoms) cudaFree(cell_atoms);
     if ((e = cudaMalloc(&cell_atoms, sizeof(int) * N))) return e;
+    for (int** p : {&n_cnt, &p_cnt}) { if (*p) cudaFree(*p); *p = nullptr; }
+    for (long long** p : {&n_ptr, &p_ptr}) { if (*p) cudaFree(*p); *p = nullptr; }
+    if ((e = cudaMalloc(&n_cnt, sizeof(int) * N))) return e;
+    if ((e = cudaMalloc(&p_cnt, sizeof(int) * N))) return e;
+    if ((e = cudaMalloc(&n_ptr, sizeof(long long) * (N + 1)))) return e;
+    if ((e = cudaMalloc(&p_ptr, sizeof(long long) * (N + 1)))) return e;
     cap_n = N;
   }
   if (ncell > cap_cells) {
@@ -506,8 +602,44 @@ cudaError_t GraphBuilder::build(const double* dR, int N, const double box[3], do
     cell_fill_kernel<<<nb, TB, 0, s>>>(cell_of, N, cell_start, cell_fill, cell_atoms);
   }
   const int nbw = (N + 3) / 4;   // warp per atom, four per block
-  count_dist_kernel<<<nbw, 128, 0, s>>>(dR, N, g, cell_of, cell_start, cell_count, cell_atoms, rg2, cnt);
-  if (gptr) count_gd_kernel<<<N, 64, 0, s>>>(gptr, gcol, gval, N, tau, cnt);
+  if (two_hop) {
+    // G^N rows: the neighbour list within rn2, each row sorted ascending
+    count_dist_kernel<<<nbw, 128, 0, s>>>(dR, N, g, cell_of, cell_start, cell_count, cell_atoms, rn2, n_cnt);
+    scan_kernel<<<1, 1024, 0, s>>>(n_cnt, N, n_ptr);
+    long long nn = 0;
+    cudaMemcpyAsync(&nn, n_ptr + N, sizeof(long long), cudaMemcpyDeviceToHost, s);
+    if ((e = cudaStreamSynchronize(s))) return e;
+    if (nn > cap_ncol) {
+      if (n_col) cudaFree(n_col);
+      cap_ncol = nn + nn / 4 + 1024;
+      if ((e = cudaMalloc(&n_col, sizeof(int) * cap_ncol))) return e;
+    }
+    fill_dist_kernel<<<nbw, 128, 0, s>>>(dR, N, g, cell_of, cell_start, cell_count, cell_atoms, rn2, n_ptr, fillc,
+                                         n_col);
+    row_unique_kernel<<<N, 256, 8192 * sizeof(int), s>>>(n_ptr, n_col, ucnt, derr, 8192);
+    // P = G^N G^D above tau, row by row (count, then fill)
+    twohop_kernel<false><<<N, 256, 0, s>>>(dR, N, g, n_ptr, n_col, gptr, gcol, gval, alpha, tau, p_cnt, nullptr,
+                                           nullptr, nullptr, derr);
+    scan_kernel<<<1, 1024, 0, s>>>(p_cnt, N, p_ptr);
+    long long np = 0;
+    cudaMemcpyAsync(&np, p_ptr + N, sizeof(long long), cudaMemcpyDeviceToHost, s);
+    if ((e = cudaStreamSynchronize(s))) return e;
+    if (np > cap_p) {
+      if (p_col) cudaFree(p_col);
+      if (p_val) cudaFree(p_val);
+      cap_p = np + np / 4 + 1024;
+      if ((e = cudaMalloc(&p_col, sizeof(int) * cap_p))) return e;
+      if ((e = cudaMalloc(&p_val, sizeof(double) * cap_p))) return e;
+    }
+    twohop_kernel<true><<<N, 256, 0, s>>>(dR, N, g, n_ptr, n_col, gptr, gcol, gval, alpha, tau, nullptr, p_ptr,
+                                          p_col, p_val, derr);
+    // the entries of P above tau are the rule's edges, added in both directions
+    cudaMemsetAsync(cnt, 0, sizeof(int) * N, s);
+    count_gd_kernel<<<N, 64, 0, s>>>(p_ptr, p_col, p_val, N, tau, cnt);
+  } else {
+    count_dist_kernel<<<nbw, 128, 0, s>>>(dR, N, g, cell_of, cell_start, cell_count, cell_atoms, rg2, cnt);
+    if (gptr) count_gd_kernel<<<N, 64, 0, s>>>(gptr, gcol, gval, N, tau, cnt);
+  }
   // keep_prev: the edges of the graph currently in row_ptr / col_out are candidates as well (they
   // are read here, before the new graph overwrites them)
   if (keep_prev) count_prev_kernel<<<nb, TB, 0, s>>>(row_ptr, N, cnt);
@@ -520,8 +652,14 @@ cudaError_t GraphBuilder::build(const double* dR, int N, const double box[3], do
     cap_cand = ncand + ncand / 4 + 1024;
     if ((e = cudaMalloc(&cand, sizeof(int) * cap_cand))) return e;
   }
-  fill_dist_kernel<<<nbw, 128, 0, s>>>(dR, N, g, cell_of, cell_start, cell_count, cell_atoms, rg2, cptr, fillc, cand);
-  if (gptr) fill_gd_kernel<<<N, 64, 0, s>>>(gptr, gcol, gval, N, tau, cptr, fillc, cand);
+  if (two_hop) {
+    cudaMemsetAsync(fillc, 0, sizeof(int) * N, s);
+    fill_gd_kernel<<<N, 64, 0, s>>>(p_ptr, p_col, p_val, N, tau, cptr, fillc, cand);
+  } else {
+    fill_dist_kernel<<<nbw, 128, 0, s>>>(dR, N, g, cell_of, cell_start, cell_count, cell_atoms, rg2, cptr, fillc,
+                                         cand);
+    if (gptr) fill_gd_kernel<<<N, 64, 0, s>>>(gptr, gcol, gval, N, tau, cptr, fillc, cand);
+  }
   if (keep_prev) fill_prev_kernel<<<N, 64, 0, s>>>(row_ptr, *col_out, N, cptr, fillc, cand);
   const int cap = 8192;
   row_unique_kernel<<<N, 256, cap * sizeof(int), s>>>(cptr, cand, ucnt, derr, cap);

@@ -24,16 +24,28 @@ struct GraphBuilder {
   int* cand = nullptr;
   int cap_n = 0, cap_cells = 0;
   long long cap_cand = 0;
+  // weighted two-hop rule: neighbour rows (G^N) and the thresholded entries of P = G^N G^D
+  int* n_cnt = nullptr;
+  long long* n_ptr = nullptr;
+  int* n_col = nullptr;
+  int* p_cnt = nullptr;
+  long long* p_ptr = nullptr;
+  int* p_col = nullptr;
+  double* p_val = nullptr;
+  long long cap_ncol = 0, cap_p = 0;
   ~GraphBuilder();
   void release();
   // Builds the symmetric CSR of the atom graph into row_ptr (device, N+1) and *col_out
   // (device, grown as needed).  gptr/gcol/gval: optional device CSR of the previous
   // atom-condensed density graph.  keep_prev: the graph already in row_ptr / *col_out keeps all
-  // its edges (the new graph is its union with the rule's edges).
+  // its edges (the new graph is its union with the rule's edges).  rule 0: distance below r_graph
+  // or density-graph entry above tau; rule 1 (with a density graph): the weighted two-hop rule,
+  // edge when P_IJ or P_JI exceeds tau, P = G^N G^D, G^N_IK = exp(-alpha R_IK^2) on the pairs with
+  // R^2 < ln(2 / tau) / alpha and G^N_II = 1 (each G^D row must list a column once).
   cudaError_t build(const double* dR, int N, const double box[3], double r_graph, const long long* gptr,
                     const int* gcol, const double* gval, double tau, long long* row_ptr, int** col_out,
                     long long* col_cap, long long* nnz_host, int* derr, cudaStream_t s, bool exact = true,
-                    bool keep_prev = false);
+                    bool keep_prev = false, int rule = 0, double alpha = 0.7);
 };
 
 struct Partitioner {

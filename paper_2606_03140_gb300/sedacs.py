@@ -38,7 +38,8 @@ class sedacs_params(C.Structure):
                 ("c_k0", C.c_double), ("scc_tol", C.c_double), ("scc_alpha", C.c_double),
                 ("sp2_tol", C.c_double), ("sp2_kmax", C.c_int32), ("ns_iters", C.c_int32),
                 ("ewald_tol", C.c_double), ("judge_every", C.c_int32), ("judge_tol", C.c_double),
-                ("Te", C.c_double), ("mu_given", C.c_int32), ("fermi_lin", C.c_double)]
+                ("Te", C.c_double), ("mu_given", C.c_int32), ("fermi_lin", C.c_double),
+                ("graph_rule", C.c_int32), ("graph_alpha", C.c_double)]
 
 
 def _load():
