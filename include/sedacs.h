@@ -44,7 +44,8 @@ typedef enum {
   SEDACS_ETIMEOUT = 5,   /* a bounded device wait gave up (kernel returned early) */
   SEDACS_ENUMERIC = 6,   /* NaN / Inf found in a result */
   SEDACS_EPRECISION = 7, /* the chemical potential of Eq. 2 was not found (no bracket / no convergence) */
-  SEDACS_ECAPACITY = 8   /* a fixed-size device buffer was too small */
+  SEDACS_ECAPACITY = 8,  /* a fixed-size device buffer was too small */
+  SEDACS_EIO = 9         /* a checkpoint file could not be written, opened or read */
 } sedacs_status;
 
 /* Synthetic sp Slater-Koster SCC-TB model (SI Sec. D).  Species 0 = H, 1 = C, 2 = O.
@@ -279,6 +280,21 @@ sedacs_status sedacs_kernel_stats(sedacs_ctx* ctx, int32_t on, double* sp2_ms, i
  * output (4).  Outputs are host scalars; counters as for sedacs_kernel_stats. */
 sedacs_status sedacs_kernel_stats_fp16(sedacs_ctx* ctx, double* ms, int64_t* launches, double* flops,
                                        double* bytes);
+
+/* ---- Checkpoint of the XL-BOMD state.  sedacs_checkpoint_save writes to the file `path` the
+ * state a shadow-dynamics step continues from (Eqs. NEQ / HW): positions, velocities and forces,
+ * the dynamical charges n, the charges q of the last density, the six-deep history of n of the
+ * dissipative integrator with its head, the step count, mu and the mu of the step before, the
+ * atom-condensed density graph the next graph is built from, and the core lists; the context
+ * must have run sedacs_xlbomd_init (SEDACS_EINVAL otherwise).  sedacs_checkpoint_load restores
+ * that state into a context created with the same atoms, model and parameters (the atom count,
+ * precision form and Te are checked: SEDACS_EINVAL); the next sedacs_xlbomd_step then continues
+ * the trajectory (the R and V it is given are outputs only).  A missing, truncated or foreign
+ * file -> SEDACS_EIO.  The learned preconditioner's parameters are not included (they are read
+ * and set with sedacs_gnn_get_params / sedacs_gnn_set_params).  The paper has no counterpart
+ * beyond the restart files of its MD driver. */
+sedacs_status sedacs_checkpoint_save(sedacs_ctx* ctx, const char* path);
+sedacs_status sedacs_checkpoint_load(sedacs_ctx* ctx, const char* path);
 
 /* ---- Allocation-free distance graph.  The paper has no counterpart to this entry point;
  * it exists for callers that cannot allocate device memory at the time of the call (programs

@@ -1,5 +1,6 @@
 // Host engine of the graph-partitioned shadow-QMD path (see engine.cuh).
 #include <algorithm>
+#include <cstdio>
 #include <cmath>
 #include <cstring>
 #include <limits>
@@ -2365,6 +2366,177 @@ sedacs_status sedacs_xlbomd_step(sedacs_ctx* ctx, double* R, double* V, int32_t 
   STCHK(copy_out(ctx, n_out, ctx->d_n, sizeof(double) * N));
   CUCHK(cudaStreamSynchronize(s));
   return check_dev_err(ctx);
+}
+
+// ---- checkpoint of the XL-BOMD state -----------------------------------------------------------
+// File: magic "SEDACSCK", version, then N, the core count, the step count, the history head,
+// precision, mu and the mu of the step before, the density graph's size; then positions,
+// velocities and forces (3N each), n and q (N each), the six-deep n history (6N), the
+// atom-condensed density graph (row pointers, columns, values) and the core lists (pointers,
+// atoms).  Everything else a step needs (graph, halos, Z, h~, Ewald sums) is rebuilt from these.
+namespace {
+constexpr char kCkMagic[8] = {'S', 'E', 'D', 'A', 'C', 'S', 'C', 'K'};
+constexpr int32_t kCkVersion = 1;
+
+struct CkHeader {
+  char magic[8];
+  int32_t version, n_atoms, n_parts, hist_head, precision, pad;
+  int64_t md_step, gd_nnz;
+  double mu, mu_prev, Te;
+};
+}  // namespace
+
+sedacs_status sedacs_checkpoint_save(sedacs_ctx* ctx, const char* path) {
+  if (!ctx || !path) return SEDACS_EINVAL;
+  if (!ctx->md_ready || !ctx->have_cores || !ctx->have_gd || !ctx->have_subs) {
+    ctx->err = "checkpoint: no XL-BOMD state to save (call sedacs_xlbomd_init first)";
+    return SEDACS_EINVAL;
+  }
+  const int N = ctx->N, P = ctx->lay.n_sub;
+  CUCHK(cudaStreamSynchronize(ctx->stream));
+  std::vector<double> R(3LL * N), V(3LL * N), F(3LL * N), n(N), q(N), hist(6LL * N);
+  std::vector<long long> gptr(N + 1);
+  CUCHK(cudaMemcpy(R.data(), ctx->d_R, sizeof(double) * R.size(), cudaMemcpyDeviceToHost));
+  CUCHK(cudaMemcpy(V.data(), ctx->d_vel, sizeof(double) * V.size(), cudaMemcpyDeviceToHost));
+  CUCHK(cudaMemcpy(F.data(), ctx->d_F, sizeof(double) * F.size(), cudaMemcpyDeviceToHost));
+  CUCHK(cudaMemcpy(n.data(), ctx->d_n, sizeof(double) * N, cudaMemcpyDeviceToHost));
+  CUCHK(cudaMemcpy(q.data(), ctx->d_q, sizeof(double) * N, cudaMemcpyDeviceToHost));
+  CUCHK(cudaMemcpy(hist.data(), ctx->d_hist, sizeof(double) * hist.size(), cudaMemcpyDeviceToHost));
+  CUCHK(cudaMemcpy(gptr.data(), ctx->d_gd_ptr, sizeof(long long) * (N + 1), cudaMemcpyDeviceToHost));
+  const long long nnz = gptr[N];
+  std::vector<int> gcol(nnz);
+  std::vector<double> gval(nnz);
+  CUCHK(cudaMemcpy(gcol.data(), ctx->d_gd_col, sizeof(int) * nnz, cudaMemcpyDeviceToHost));
+  CUCHK(cudaMemcpy(gval.data(), ctx->d_gd_val, sizeof(double) * nnz, cudaMemcpyDeviceToHost));
+  std::vector<long long> cptr(P + 1, 0);
+  std::vector<int> core;
+  for (int i = 0; i < P; ++i) {
+    const int nc = ctx->lay.n_core_atoms[i];
+    for (int a = 0; a < nc; ++a) core.push_back(ctx->sub_atoms_h[ctx->sub_ptr_h[i] + a]);
+    cptr[i + 1] = cptr[i] + nc;
+  }
+  CkHeader h{};
+  std::memcpy(h.magic, kCkMagic, 8);
+  h.version = kCkVersion;
+  h.n_atoms = N;
+  h.n_parts = P;
+  h.hist_head = ctx->hist_head;
+  h.precision = ctx->prm.precision;
+  h.md_step = ctx->md_step;
+  h.gd_nnz = nnz;
+  h.mu = ctx->mu;
+  h.mu_prev = ctx->mu_prev;
+  h.Te = ctx->prm.Te;
+  FILE* f = std::fopen(path, "wb");
+  if (!f) { ctx->err = "checkpoint: cannot open the file for writing"; return SEDACS_EIO; }
+  bool ok = std::fwrite(&h, sizeof(h), 1, f) == 1;
+  auto put = [&](const void* p, size_t bytes) { ok = ok && (bytes == 0 || std::fwrite(p, bytes, 1, f) == 1); };
+  put(R.data(), sizeof(double) * R.size());
+  put(V.data(), sizeof(double) * V.size());
+  put(F.data(), sizeof(double) * F.size());
+  put(n.data(), sizeof(double) * N);
+  put(q.data(), sizeof(double) * N);
+  put(hist.data(), sizeof(double) * hist.size());
+  put(gptr.data(), sizeof(long long) * (N + 1));
+  put(gcol.data(), sizeof(int) * nnz);
+  put(gval.data(), sizeof(double) * nnz);
+  put(cptr.data(), sizeof(long long) * (P + 1));
+  put(core.data(), sizeof(int) * core.size());
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok) { ctx->err = "checkpoint: write failed"; return SEDACS_EIO; }
+  return SEDACS_OK;
+}
+
+sedacs_status sedacs_checkpoint_load(sedacs_ctx* ctx, const char* path) {
+  if (!ctx || !path) return SEDACS_EINVAL;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) { ctx->err = "checkpoint: cannot open the file"; return SEDACS_EIO; }
+  CkHeader h{};
+  bool ok = std::fread(&h, sizeof(h), 1, f) == 1;
+  auto get = [&](void* p, size_t bytes) { ok = ok && (bytes == 0 || std::fread(p, bytes, 1, f) == 1); };
+  const int N = ctx->N;
+  if (!ok || std::memcmp(h.magic, kCkMagic, 8) != 0 || h.version != kCkVersion) {
+    std::fclose(f);
+    ctx->err = "checkpoint: not a checkpoint file of this version";
+    return SEDACS_EIO;
+  }
+  if (h.n_atoms != N || h.precision != ctx->prm.precision || h.Te != ctx->prm.Te || h.n_parts <= 0 ||
+      h.gd_nnz < 0 || h.hist_head < 0 || h.hist_head >= 6) {
+    std::fclose(f);
+    ctx->err = "checkpoint: atom count, precision form or electronic temperature differ from this context";
+    return SEDACS_EINVAL;
+  }
+  const int P = h.n_parts;
+  const long long nnz = h.gd_nnz;
+  std::vector<double> R(3LL * N), V(3LL * N), F(3LL * N), n(N), q(N), hist(6LL * N), gval(nnz);
+  std::vector<long long> gptr(N + 1), cptr(P + 1);
+  std::vector<int> gcol(nnz), core(N);
+  get(R.data(), sizeof(double) * R.size());
+  get(V.data(), sizeof(double) * V.size());
+  get(F.data(), sizeof(double) * F.size());
+  get(n.data(), sizeof(double) * N);
+  get(q.data(), sizeof(double) * N);
+  get(hist.data(), sizeof(double) * hist.size());
+  get(gptr.data(), sizeof(long long) * (N + 1));
+  get(gcol.data(), sizeof(int) * nnz);
+  get(gval.data(), sizeof(double) * nnz);
+  get(cptr.data(), sizeof(long long) * (P + 1));
+  get(core.data(), sizeof(int) * N);
+  std::fclose(f);
+  if (!ok || gptr[0] != 0 || gptr[N] != nnz || cptr[0] != 0 || cptr[P] != N) {
+    ctx->err = "checkpoint: truncated or inconsistent file";
+    return SEDACS_EIO;
+  }
+  for (int A = 0; A < N; ++A)
+    if (gptr[A + 1] < gptr[A]) { ctx->err = "checkpoint: inconsistent density graph"; return SEDACS_EIO; }
+  for (long long p = 0; p < nnz; ++p)
+    if (gcol[p] < 0 || gcol[p] >= N) { ctx->err = "checkpoint: inconsistent density graph"; return SEDACS_EIO; }
+  // cores, checked and set as sedacs_set_cores does
+  std::vector<std::vector<int>> cores(P);
+  std::vector<char> seen(N, 0);
+  for (int i = 0; i < P; ++i) {
+    if (cptr[i + 1] < cptr[i]) { ctx->err = "checkpoint: inconsistent cores"; return SEDACS_EIO; }
+    for (long long k = cptr[i]; k < cptr[i + 1]; ++k) {
+      const int a = core[k];
+      if (a < 0 || a >= N || seen[a]) { ctx->err = "checkpoint: inconsistent cores"; return SEDACS_EIO; }
+      seen[a] = 1;
+      cores[i].push_back(a);
+    }
+    std::sort(cores[i].begin(), cores[i].end());
+  }
+  cudaStream_t s = ctx->stream;
+  CUCHK(cudaMemcpy(ctx->d_R, R.data(), sizeof(double) * R.size(), cudaMemcpyHostToDevice));
+  CUCHK(cudaMemcpy(ctx->d_vel, V.data(), sizeof(double) * V.size(), cudaMemcpyHostToDevice));
+  CUCHK(cudaMemcpy(ctx->d_F, F.data(), sizeof(double) * F.size(), cudaMemcpyHostToDevice));
+  CUCHK(cudaMemcpy(ctx->d_n, n.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
+  CUCHK(cudaMemcpy(ctx->d_q, q.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
+  CUCHK(cudaMemcpy(ctx->d_hist, hist.data(), sizeof(double) * hist.size(), cudaMemcpyHostToDevice));
+  // the density graph serves the next graph build as an external one (as from sedacs_graph_build)
+  CUCHK(grow(&ctx->d_xgd_col, &ctx->xgd_cap, nnz + 1) == cudaSuccess ? cudaSuccess : cudaErrorMemoryAllocation);
+  if (ctx->d_xgd_val) cudaFree(ctx->d_xgd_val);
+  if (ctx->d_xgd_ptr) cudaFree(ctx->d_xgd_ptr);
+  ctx->d_xgd_val = nullptr;
+  ctx->d_xgd_ptr = nullptr;
+  CUCHK(cudaMalloc(&ctx->d_xgd_val, sizeof(double) * ctx->xgd_cap));
+  CUCHK(cudaMalloc(&ctx->d_xgd_ptr, sizeof(long long) * (N + 1)));
+  CUCHK(cudaMemcpy(ctx->d_xgd_ptr, gptr.data(), sizeof(long long) * (N + 1), cudaMemcpyHostToDevice));
+  if (nnz > 0) {
+    CUCHK(cudaMemcpy(ctx->d_xgd_col, gcol.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice));
+    CUCHK(cudaMemcpy(ctx->d_xgd_val, gval.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice));
+  }
+  ctx->have_xgd = true;
+  ctx->have_gd = false;
+  CUCHK(ctx->part.set_cores(cores, N, s));
+  ctx->have_cores = true;
+  ctx->hist_head = h.hist_head;
+  ctx->md_step = h.md_step;
+  ctx->mu = h.mu;
+  ctx->mu_prev = h.mu_prev;
+  ctx->geom_valid = false;
+  ctx->z_valid = false;
+  ctx->md_ready = true;
+  CUCHK(cudaStreamSynchronize(s));
+  return SEDACS_OK;
 }
 
 sedacs_status sedacs_charge_response(sedacs_ctx* ctx, const double* v, double* dq) {

@@ -16,7 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libsedacs.so")
 
 STATUS = {0: "SEDACS_OK", 1: "SEDACS_EINVAL", 2: "SEDACS_ENOMEM", 3: "SEDACS_ECUDA", 4: "SEDACS_ENOCONV",
-          5: "SEDACS_ETIMEOUT", 6: "SEDACS_ENUMERIC", 7: "SEDACS_EPRECISION", 8: "SEDACS_ECAPACITY"}
+          5: "SEDACS_ETIMEOUT", 6: "SEDACS_ENUMERIC", 7: "SEDACS_EPRECISION", 8: "SEDACS_ECAPACITY",
+          9: "SEDACS_EIO"}
 
 
 class SedacsError(RuntimeError):
@@ -76,6 +77,8 @@ def _load():
         "sedacs_reset_counters": (I32, [P]),
         "sedacs_kernel_stats": (I32, [P, I32, P, P, P]),
         "sedacs_kernel_stats_fp16": (I32, [P, P, P, P, P]),
+        "sedacs_checkpoint_save": (I32, [P, C.c_char_p]),
+        "sedacs_checkpoint_load": (I32, [P, C.c_char_p]),
         "sedacs_set_params": (I32, [P, P]),
         "sedacs_graph_build_noalloc": (I32, [P, I32, P, D, P, P, I64, P, P]),
         "sedacs_gnn_num_params": (I32, []),
@@ -108,7 +111,7 @@ EXPORTED = (
     "sedacs_kernel_stats", "sedacs_set_params", "sedacs_graph_build_noalloc", "sedacs_gnn_num_params",
     "sedacs_gnn_init", "sedacs_gnn_set_params", "sedacs_gnn_get_params", "sedacs_gnn_apply", "sedacs_gnn_param_grad",
     "sedacs_gnn_collect", "sedacs_gnn_train", "sedacs_kernel_judge", "sedacs_density_info", "sedacs_charges",
-    "sedacs_kernel_stats_fp16",
+    "sedacs_kernel_stats_fp16", "sedacs_checkpoint_save", "sedacs_checkpoint_load",
 )
 
 
@@ -353,6 +356,16 @@ def sedacs_kernel_stats_fp16(ctx):
     by = C.c_double()
     _check(ctx, _lib.sedacs_kernel_stats_fp16(ctx, C.byref(ms), C.byref(nl), C.byref(fl), C.byref(by)))
     return ms.value, nl.value, fl.value, by.value
+
+
+def sedacs_checkpoint_save(ctx, path: str):
+    """Write the XL-BOMD state of ctx to the file path."""
+    _check(ctx, _lib.sedacs_checkpoint_save(ctx, str(path).encode()))
+
+
+def sedacs_checkpoint_load(ctx, path: str):
+    """Restore the XL-BOMD state written by sedacs_checkpoint_save into ctx (same atoms and parameters)."""
+    _check(ctx, _lib.sedacs_checkpoint_load(ctx, str(path).encode()))
 
 
 def sedacs_graph_build_noalloc(R_dev, box, r_graph: float, row_ptr_dev, col_dev, stream: int = 0) -> tuple[int, int]:
