@@ -141,6 +141,23 @@ __global__ void rows_axpy_kernel(void* y, const void* x, double a, long long n, 
   else reinterpret_cast<float*>(y)[t] += (float)(a * (double)reinterpret_cast<const float*>(x)[t]);
 }
 
+// y += sum_k a_k x_k over the core-row elements (up to four terms, x_k null past the last).
+__global__ void rows_axpy4_kernel(void* y, const void* x0, const void* x1, const void* x2, const void* x3, double a0,
+                                  double a1, double a2, double a3, long long n, int f64) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const void* xs[4] = {x0, x1, x2, x3};
+  const double as[4] = {a0, a1, a2, a3};
+  double acc = 0.0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (!xs[k]) break;
+    acc += as[k] * (f64 ? reinterpret_cast<const double*>(xs[k])[t] : (double)reinterpret_cast<const float*>(xs[k])[t]);
+  }
+  if (f64) reinterpret_cast<double*>(y)[t] += acc;
+  else reinterpret_cast<float*>(y)[t] = (float)((double)reinterpret_cast<float*>(y)[t] + acc);
+}
+
 __global__ void absmax_kernel(const double* a, int N, double* out) {
   __shared__ double red[1024];
   double m = 0.0;
@@ -1340,6 +1357,17 @@ void fermi_uw_rows(sedacs_ctx* ctx) {
   run_op(ctx, ctx->zc == 0 ? OP_F_DW0 : OP_F_DW1, ns, 0);
 }
 
+// D_c += sum_k c_k D_k over the first nt of the slots sx (one pass over the core rows).
+void rows_axpy_terms(sedacs_ctx* ctx, int sy, const int* sx, const double* c, int nt) {
+  const long long n = ctx->lay.rw_total;
+  const void* x[4] = {nullptr, nullptr, nullptr, nullptr};
+  for (int k = 0; k < nt && k < 4; ++k) x[k] = ctx->arena + ctx->slot[sx[k]].base;
+  rows_axpy4_kernel<<<nblk(n, 256), 256, 0, ctx->stream>>>(ctx->arena + ctx->slot[sy].base, x[0], x[1], x[2], x[3],
+                                                          c[0], nt > 1 ? c[1] : 0.0, nt > 2 ? c[2] : 0.0,
+                                                          nt > 3 ? c[3] : 0.0, n, ctx->f64 ? 1 : 0);
+  ctx->launches += 1;
+}
+
 void rows_axpy(sedacs_ctx* ctx, int sy, int sx, double a) {
   const long long n = ctx->lay.rw_total;
   rows_axpy_kernel<<<nblk(n, 256), 256, 0, ctx->stream>>>(ctx->arena + ctx->slot[sy].base,
@@ -1372,6 +1400,7 @@ sedacs_status fermi_density(sedacs_ctx* ctx, double* mu_io) {
   const bool given = ctx->prm.mu_given != 0 && std::isfinite(*mu_io);
   double mu = std::isfinite(*mu_io) ? (given ? *mu_io : std::min(std::max(*mu_io, a), b)) : 0.5 * (lo + hi);
   double dmu = 0.0, np = 0.0;
+  int order = 2;                               // terms of the accepted mu expansion
   double* pop_s = ctx->d_rsp + 6LL * N;      // kept for the response calls (their dN/dmu weights)
   double* scr = ctx->d_rsp + 7LL * N;
   double* pop_t = ctx->d_rsp + 5LL * N;
@@ -1398,34 +1427,59 @@ sedacs_status fermi_density(sedacs_ctx* ctx, double* mu_io) {
     core_pops(ctx, ctx->d_dcoff_d, pop_s, scr, 10);                // sum of D_s populations
     fermi_t_rows(ctx);
     core_pops(ctx, ctx->d_dcoff_t, pop_t, scr, 14);                // sum of D_t populations
-    fermi_uw_rows(ctx);
-    core_pops(ctx, ctx->d_dcoff_u, pop_uw, scr, 11);               // sums of D_u and D_w populations
-    core_pops(ctx, ctx->d_dcoff_w, pop_uw, scr, 12);
     double sc[6];
     CUCHK(cudaMemcpyAsync(sc, ctx->d_scal + 9, sizeof(sc), cudaMemcpyDeviceToHost, s));
     CUCHK(cudaStreamSynchronize(s));
     const double nel = sc[0];
     np = beta * sc[1];
-    const double n2 = beta * beta * sc[5], n3 = beta * beta * beta * sc[2], n4 = beta * beta * beta * beta * sc[3];
+    const double n2 = beta * beta * sc[5];
     const double dn = ne - nel;
     ctx->fermi_hist.insert(ctx->fermi_hist.end(), {mu, dn, np});
-    if (!std::isfinite(nel) || !std::isfinite(np) || !std::isfinite(n3) || !std::isfinite(n4)) {
+    if (!std::isfinite(nel) || !std::isfinite(np) || !std::isfinite(n2)) {
       ctx->err = "non-finite electron count";
       return SEDACS_ENUMERIC;
     }
-    // root of the fourth-order model np d + n2 d^2 / 2 + n3 d^3 / 6 + n4 d^4 / 24 = dn next to the
-    // Newton step dn / np (its step is also the next trial when it lies on the increasing branch)
-    double dq2 = std::numeric_limits<double>::quiet_NaN();
-    if (np > 0.0) {
+    // root of the count model np d + n2 d^2 / 2 + n3 d^3 / 6 + n4 d^4 / 24 = dn next to the Newton
+    // step dn / np (its step is also the next trial when it lies on the increasing branch)
+    auto model_root = [&](double n3, double n4, double* d_out) -> bool {
+      if (!(np > 0.0)) return false;
       double d = dn / np;
-      bool ok = true;
       for (int it = 0; it < 8; ++it) {
         const double gp = np + d * (n2 + d * (0.5 * n3 + d * n4 / 6.0));
-        if (!(gp > 0.0)) { ok = false; break; }
+        if (!(gp > 0.0)) return false;
         d -= (d * (np + d * (0.5 * n2 + d * (n3 / 6.0 + d * n4 / 24.0))) - dn) / gp;
       }
-      if (ok && std::isfinite(d)) dq2 = d;
-      if (ok && std::isfinite(d) && std::fabs(beta * d) <= lin) { dmu = d; done = true; break; }
+      if (!std::isfinite(d)) return false;
+      *d_out = d;
+      return true;
+    };
+    // second order first: accepted within |beta dmu| <= lin2 (remainder (beta dmu)^3 / 6 x 0.125, the
+    // same bound as the fourth order's at lin); the third and fourth orders are computed only when
+    // the second-order step lands where the fourth-order one can be accepted
+    const double lin2 = std::min(lin, ctx->f64 ? 3e-4 : 3e-2);
+    double dq2 = std::numeric_limits<double>::quiet_NaN();
+    double d2 = 0.0;
+    if (model_root(0.0, 0.0, &d2)) {
+      dq2 = d2;
+      if (std::fabs(beta * d2) <= lin2) { dmu = d2; order = 2; done = true; break; }
+      if (std::fabs(beta * d2) <= 1.5 * lin) {
+        fermi_uw_rows(ctx);
+        core_pops(ctx, ctx->d_dcoff_u, pop_uw, scr, 11);           // sums of D_u and D_w populations
+        core_pops(ctx, ctx->d_dcoff_w, pop_uw, scr, 12);
+        double s34[2];
+        CUCHK(cudaMemcpyAsync(s34, ctx->d_scal + 11, sizeof(s34), cudaMemcpyDeviceToHost, s));
+        CUCHK(cudaStreamSynchronize(s));
+        const double n3 = beta * beta * beta * s34[0], n4 = beta * beta * beta * beta * s34[1];
+        if (!std::isfinite(n3) || !std::isfinite(n4)) {
+          ctx->err = "non-finite electron count";
+          return SEDACS_ENUMERIC;
+        }
+        double d4 = 0.0;
+        if (model_root(n3, n4, &d4)) {
+          dq2 = d4;
+          if (std::fabs(beta * d4) <= lin) { dmu = d4; order = 4; done = true; break; }
+        }
+      }
     }
     // a count already within its rounding noise (a clean gap: dN/dmu ~ 0) is accepted as it is
     if (std::fabs(dn) <= (ctx->f64 ? 1e-12 : 1e-7) * ne) { dmu = 0.0; done = true; break; }
@@ -1451,14 +1505,12 @@ sedacs_status fermi_density(sedacs_ctx* ctx, double* mu_io) {
   run_op(ctx, ctx->zc == 0 ? OP_WC0 : OP_WC1, ns, 0);
   if (dmu != 0.0) {
     const double c1 = beta * dmu, c2 = 0.5 * c1 * c1, c3 = c2 * c1 / 3.0, c4 = c3 * c1 / 4.0;
-    rows_axpy(ctx, kDc, kdDc, c1);
-    rows_axpy(ctx, kDc, kdDt, c2);
-    rows_axpy(ctx, kDc, kdDu, c3);
-    rows_axpy(ctx, kDc, kdDw, c4);
+    const int dk[4] = {kdDc, kdDt, kdDu, kdDw};
+    const double ck[4] = {c1, c2, c3, c4};
+    rows_axpy_terms(ctx, kDc, dk, ck, order);
     // W_k = 2 Z_c X_k h~ Z (X_k = s, t, u, w) -> kT1, added with c_k
     const int t2[4] = {OP_F_T2S, OP_F_T2T, OP_F_T2U, OP_F_T2W};
-    const double ck[4] = {c1, c2, c3, c4};
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < order; ++k) {
       run_op(ctx, t2[k], ns, ns);
       run_op(ctx, ctx->zc == 0 ? OP_F_WS0 : OP_F_WS1, ns, 0);
       rows_axpy(ctx, kWc, kT1, ck[k]);
