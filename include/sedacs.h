@@ -281,6 +281,13 @@ sedacs_status sedacs_kernel_stats(sedacs_ctx* ctx, int32_t on, double* sp2_ms, i
 sedacs_status sedacs_kernel_stats_fp16(sedacs_ctx* ctx, double* ms, int64_t* launches, double* flops,
                                        double* bytes);
 
+/* Self-test of the bounded device waits (the paper has no counterpart): one device thread waits on
+ * a flag that nothing sets, gives up after about limit_us microseconds (1 .. 1,000,000) of SM
+ * cycles and raises the timeout bit every bounded wait of the library raises.  Returns
+ * SEDACS_ETIMEOUT (SEDACS_EINVAL for a limit out of range); the bit is cleared as it is reported,
+ * and the context stays usable. */
+sedacs_status sedacs_selftest_wait(sedacs_ctx* ctx, int32_t limit_us);
+
 /* ---- Checkpoint of the XL-BOMD state.  sedacs_checkpoint_save writes to the file `path` the
  * state a shadow-dynamics step continues from (Eqs. NEQ / HW): positions, velocities and forces,
  * the dynamical charges n, the charges q of the last density, the six-deep history of n of the

@@ -158,6 +158,18 @@ __global__ void rows_axpy4_kernel(void* y, const void* x0, const void* x1, const
   else reinterpret_cast<float*>(y)[t] = (float)((double)reinterpret_cast<float*>(y)[t] + acc);
 }
 
+// Self-test of the bounded device waits: one thread spins on a flag that nothing sets, gives up
+// after limit_cycles SM cycles and raises the timeout bit, as the GEMM's mbarrier waits do.
+__global__ void selftest_wait_kernel(const volatile int* flag, long long limit_cycles, int* err) {
+  const long long t0 = clock64();
+  while (*flag == 0) {
+    if (clock64() - t0 > limit_cycles) {
+      atomicOr(err, kErrTimeout);
+      return;
+    }
+  }
+}
+
 __global__ void absmax_kernel(const double* a, int N, double* out) {
   __shared__ double red[1024];
   double m = 0.0;
@@ -2417,6 +2429,17 @@ sedacs_status sedacs_xlbomd_step(sedacs_ctx* ctx, double* R, double* V, int32_t 
   STCHK(copy_out(ctx, V, ctx->d_vel, sizeof(double) * 3 * N));
   STCHK(copy_out(ctx, n_out, ctx->d_n, sizeof(double) * N));
   CUCHK(cudaStreamSynchronize(s));
+  return check_dev_err(ctx);
+}
+
+sedacs_status sedacs_selftest_wait(sedacs_ctx* ctx, int32_t limit_us) {
+  if (!ctx || limit_us <= 0 || limit_us > 1000000) return SEDACS_EINVAL;
+  int* flag = reinterpret_cast<int*>(ctx->d_scal + 15);          // a spare word, cleared, never set
+  CUCHK(cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
+  const long long cycles = (long long)limit_us * 2100LL;        // at most the SM's 2.1 GHz
+  selftest_wait_kernel<<<1, 1, 0, ctx->stream>>>(flag, cycles, ctx->d_err);
+  CUCHK(cudaGetLastError());
+  ctx->launches += 1;
   return check_dev_err(ctx);
 }
 

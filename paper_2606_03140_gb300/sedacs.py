@@ -78,6 +78,7 @@ def _load():
         "sedacs_kernel_stats": (I32, [P, I32, P, P, P]),
         "sedacs_kernel_stats_fp16": (I32, [P, P, P, P, P]),
         "sedacs_checkpoint_save": (I32, [P, C.c_char_p]),
+        "sedacs_selftest_wait": (I32, [P, I32]),
         "sedacs_checkpoint_load": (I32, [P, C.c_char_p]),
         "sedacs_set_params": (I32, [P, P]),
         "sedacs_graph_build_noalloc": (I32, [P, I32, P, D, P, P, I64, P, P]),
@@ -111,7 +112,7 @@ EXPORTED = (
     "sedacs_kernel_stats", "sedacs_set_params", "sedacs_graph_build_noalloc", "sedacs_gnn_num_params",
     "sedacs_gnn_init", "sedacs_gnn_set_params", "sedacs_gnn_get_params", "sedacs_gnn_apply", "sedacs_gnn_param_grad",
     "sedacs_gnn_collect", "sedacs_gnn_train", "sedacs_kernel_judge", "sedacs_density_info", "sedacs_charges",
-    "sedacs_kernel_stats_fp16", "sedacs_checkpoint_save", "sedacs_checkpoint_load",
+    "sedacs_kernel_stats_fp16", "sedacs_checkpoint_save", "sedacs_checkpoint_load", "sedacs_selftest_wait",
 )
 
 
@@ -356,6 +357,11 @@ def sedacs_kernel_stats_fp16(ctx):
     by = C.c_double()
     _check(ctx, _lib.sedacs_kernel_stats_fp16(ctx, C.byref(ms), C.byref(nl), C.byref(fl), C.byref(by)))
     return ms.value, nl.value, fl.value, by.value
+
+
+def sedacs_selftest_wait(ctx, limit_us: int) -> int:
+    """Run the bounded-wait self-test; returns the status (SEDACS_ETIMEOUT = 5 expected)."""
+    return int(_lib.sedacs_selftest_wait(ctx, int(limit_us)))
 
 
 def sedacs_checkpoint_save(ctx, path: str):
