@@ -204,3 +204,57 @@ def test_two_hop_threshold_controls_accuracy():
     assert np.all(np.diff(e[:, 0]) < 0) and np.all(np.diff(e[:, 1]) < 0), e
     slope = np.polyfit(np.log(taus), np.log(e[:, 1]), 1)[0]
     assert slope > 0.3, (slope, e)
+
+
+# ---- core refinement for the 128-orbital tiles ------------------------------------------------
+
+def _refine_case():
+    from paper_2606_03140_gb300 import inputs as I
+
+    s = I.small_water_box(300, 21.0, seed=17)
+    rp, col = graph.build_graph(s.R, s.box, 3.5)
+    cores = graph.rcb_partition(s.R, s.box, 24)
+    norb = np.where(s.species == 0, 1, 4)
+    return s, rp, col, cores, norb
+
+
+def test_refine_cores_valid_cover_and_score_does_not_rise():
+    s, rp, col, cores, norb = _refine_case()
+    new, before, after = graph.refine_cores(rp, col, cores, norb, rounds=50, min_core=12)
+    assert after <= before
+    allat = np.concatenate(new)
+    assert np.array_equal(np.sort(allat), np.arange(s.n_atoms))
+    assert all(len(c) >= 12 for c in new) and len(new) == len(cores)
+    assert all(np.all(np.diff(c) > 0) for c in new)
+
+
+def test_refine_cores_ends_at_a_local_optimum_brute_force():
+    """After convergence no single core-atom move that the rule may make lowers the score."""
+    s, rp, col, cores, norb = _refine_case()
+    new, before, after = graph.refine_cores(rp, col, cores, norb, rounds=200, min_core=12)
+    N = s.n_atoms
+    core_of = np.empty(N, dtype=np.int64)
+    for c, at in enumerate(new):
+        core_of[at] = c
+
+    def orbs(mem):
+        halo = set()
+        for a in mem:
+            for b in col[rp[a]:rp[a + 1]]:
+                if int(b) not in mem:
+                    halo.add(int(b))
+        return int(sum(norb[a] for a in mem) + sum(norb[b] for b in halo))
+
+    mems = [set(int(a) for a in c) for c in new]
+    n = [orbs(m) for m in mems]
+    assert sum(graph.refine_score(x) for x in n) == after
+    for c, m in enumerate(mems):
+        if -(-n[c] // 128) == -(-max(n[c] - 48, 1) // 128) or len(m) <= 12:
+            continue
+        for a in sorted(m):
+            for d in sorted({int(core_of[b]) for b in col[rp[a]:rp[a + 1]] if core_of[b] != c}):
+                nc = orbs(m - {a})
+                nd = orbs(mems[d] | {a})
+                delta = (graph.refine_score(nc) + graph.refine_score(nd) - graph.refine_score(n[c])
+                         - graph.refine_score(n[d]))
+                assert delta >= 0, (c, a, d, delta)
