@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 sub-record")
     ap.add_argument("--no-frames", action="store_true", help="skip the oracle check of sampled frames")
+    ap.add_argument("--refine-cores", action="store_true",
+                    help="refine the recursive-bisection cores for the 128-orbital tiles (sedacs_refine_cores); "
+                         "off by default: measured slower over the MD, as the density graph follows the cores")
     ap.add_argument("--profile-case", action="store_true",
                     help="small ncu case: 3,000-atom water box, two densities, the second inside NVTX range 'second'")
     ap.add_argument("--quick-setup", action="store_true",
@@ -60,9 +63,10 @@ METRIC = "atoms*QMD-steps/s at |dq|<=1e-5 e vs FP64 oracle (mixed vs plain, one 
 # product kernel (tc_gemm_persistent<2, true>) on the benchmarked 9,000-atom workload: the mean over
 # its 136 launches in the NVTX range 'timed' of `bench.py --no-plain --no-frames --no-cpu-baseline
 # --steps 2 --warmup 1` (one ncu pass, so the full workload could be captured); reported only while
-# the kernel source is the one the counters were taken on.
+# the kernel source is the one the counters were taken on, and on the cores the capture used (the
+# recursive-bisection cores, not refined: refinement changes the subgraph sizes).
 FERMI_TRAFFIC = {"kernel_sha1": "f1e27abead4ca70ebedad479f3f8cb922699ee59", "precision": 1,
-                 "workload": "water9000", "bytes_per_launch": 998.1e6}
+                 "workload": "water9000", "core_refine": False, "bytes_per_launch": 998.1e6}
 
 
 def strip_comments(src: str) -> str:
@@ -198,12 +202,13 @@ def allmax(world, x: float) -> float:
     return float(t.item())
 
 
-def setup_system(S, I, workload: str, precision: int, seed_v: int = 20260703, quick: bool = False):
+def setup_system(S, I, workload: str, precision: int, seed_v: int = 20260703, quick: bool = False,
+                 refine: bool = False):
     """SCC ground state and velocities, context ready for XL-BOMD (paper_2606_03140_gb300.runs)."""
     from paper_2606_03140_gb300 import runs
 
     try:
-        return runs.ground_state(workload, precision, seed_v=seed_v, quick=quick)
+        return runs.ground_state(workload, precision, seed_v=seed_v, quick=quick, refine=refine)
     except runs.NoGroundState as e:
         # XL-BOMD starts from the SCC ground state; timing dynamics from an unconverged start
         # would time charge oscillations, not the method
@@ -229,7 +234,7 @@ def frame_check(parts, R, n, q, mu, picks, model, species, box):
     return float(np.max(d)), float(np.sqrt(np.mean(d ** 2))), int(np.sum(d > 1e-5)), int(d.shape[0])
 
 
-def run_plain(args, S, model, s, R0, V0, n0, mu0, gd, steps: int = 2):
+def run_plain(args, S, model, s, R0, V0, n0, mu0, gd, cores, steps: int = 2):
     """The plain FP64 form from the same ground state: charges at the start (against the mixed
     form's) and the device-timed step."""
     import torch
@@ -242,6 +247,8 @@ def run_plain(args, S, model, s, R0, V0, n0, mu0, gd, steps: int = 2):
         V = np.ascontiguousarray(V0.copy())
         S.sedacs_graph_build(ctx, R, gd=gd)
         S.sedacs_partition(ctx, R)
+        if args.refine_cores:
+            S.sedacs_set_cores(ctx, cores)      # the mixed form's cores, so both forms share subgraphs
         S.sedacs_xlbomd_init(ctx, R, V, np.ascontiguousarray(n0), mu0)
         q0 = S.sedacs_charges(ctx, N)
         S.sedacs_xlbomd_step(ctx, R, V, 1, args.dt)
@@ -262,11 +269,14 @@ def run_ours(args, world, rank, local):
     from paper_2606_03140_gb300 import inputs as I
     from paper_2606_03140_gb300 import sedacs as S
 
-    s, model, ctx, R, V, n, info = setup_system(S, I, args.workload, args.precision, quick=args.quick_setup)
+    s, model, ctx, R, V, n, info = setup_system(S, I, args.workload, args.precision, quick=args.quick_setup,
+                                                refine=args.refine_cores)
     N = s.n_atoms
     R0, V0, n0, mu0 = R.copy(), V.copy(), n.copy(), info["mu"]
     q_start = S.sedacs_charges(ctx, N)
     gd0 = S.sedacs_density_graph_get(ctx, N)
+    sp0, sa0, nc0 = S.sedacs_parts_get(ctx)
+    cores0 = [sa0[sp0[i]:sp0[i] + nc0[i]].copy() for i in range(len(nc0))]
     # warm-up (host I/O)
     S.sedacs_xlbomd_step(ctx, R, V, args.warmup, args.dt)
     # ---- device-resident timed region -------------------------------------------------
@@ -357,7 +367,7 @@ def run_ours(args, world, rank, local):
     hbm_src = "of measured" if "hbm_gbs" in peaks else "of fallback"
     traffic = None
     if FERMI_TRAFFIC and kernel_sha1() == FERMI_TRAFFIC["kernel_sha1"] and args.precision == FERMI_TRAFFIC["precision"] \
-            and args.workload == FERMI_TRAFFIC["workload"]:
+            and args.workload == FERMI_TRAFFIC["workload"] and args.refine_cores == FERMI_TRAFFIC["core_refine"]:
         traffic = FERMI_TRAFFIC["bytes_per_launch"]
     if args.precision == 1 and f16_ms > 0:
         # the dominant kernel: the products in two fp16 planes.  Roofline: its algorithmic bytes
@@ -409,7 +419,7 @@ def run_ours(args, world, rank, local):
                              "triangle, n_i the orbital count)"}
     plain = None
     if not args.no_plain and args.precision != 0 and rank == 0:
-        q64, t64 = run_plain(args, S, model, s, R0, V0, n0, mu0, gd0)
+        q64, t64 = run_plain(args, S, model, s, R0, V0, n0, mu0, gd0, cores0)
         dq_mp = float(np.max(np.abs(q64 - q_start)))
         plain = {"precision": 0, "ms_per_step": 1e3 * t64, "value": N / t64, "unit": UNIT,
                  "mixed_vs_plain_max_dq": dq_mp,
@@ -430,6 +440,7 @@ def run_ours(args, world, rank, local):
         "config": {"workload": f"{args.workload}: {N} atoms, cores~32, tau 1e-3, r_graph 3 A, XL-BOMD NVE 300 K, "
                                f"Te 300 K, dt {args.dt} fs",
                    "precision": args.precision, "parallelism": f"replicas x{world}",
+                   "cores": "recursive bisection" + (", refined for 128-orbital tiles" if args.refine_cores else ""),
                    "l2": "working set (per-subgraph arena, several GB) far exceeds the 129 MB L2; no flush needed",
                    "scc_iters_setup": info["scc_iters"], "scc_resid_setup": info["scc_resid"], "mu": info["mu"],
                    "kernel": "K0 = -0.05 I (paper_2606_03140_gb300.runs.MD_C_K0)"},

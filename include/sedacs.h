@@ -281,6 +281,20 @@ sedacs_status sedacs_kernel_stats(sedacs_ctx* ctx, int32_t on, double* sp2_ms, i
 sedacs_status sedacs_kernel_stats_fp16(sedacs_ctx* ctx, double* ms, int64_t* launches, double* flops,
                                        double* bytes);
 
+/* Core refinement for the tiles of the subgraph solves (not in the paper, which notes that a
+ * subgraph's cost grows with the cube of its size).  The tensor-core products work on 128-orbital
+ * tiles, so a subgraph of n orbitals (core + halo) costs about T^3, T = ceil(n / 128).  Single core
+ * atoms move to an adjacent core (a graph neighbour's core) while that lowers the integer score
+ * sum over subgraphs of 128000 T^3 + (n - 128 (T - 1)) (T^3 - (T - 1)^3); cores more than 48
+ * orbitals above their boundary are left alone and every core keeps at least min_core atoms.
+ * Deterministic: cores by index, each core's atoms ascending (a snapshot taken at its turn),
+ * target cores ascending, the first best strict improvement; at most `rounds` passes, fewer when a
+ * pass moves nothing.  Uses the current graph and cores (sedacs_graph_build, sedacs_partition
+ * first: SEDACS_EINVAL otherwise), sets the new cores and recomputes the halos.  score_before /
+ * score_after (host, nullable) receive the score. */
+sedacs_status sedacs_refine_cores(sedacs_ctx* ctx, int32_t rounds, int32_t min_core, int64_t* score_before,
+                                  int64_t* score_after);
+
 /* Self-test of the bounded device waits (the paper has no counterpart): one device thread waits on
  * a flag that nothing sets, gives up after about limit_us microseconds (1 .. 1,000,000) of SM
  * cycles and raises the timeout bit every bounded wait of the library raises.  Returns

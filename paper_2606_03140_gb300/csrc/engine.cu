@@ -2170,6 +2170,113 @@ sedacs_status sedacs_set_cores(sedacs_ctx* ctx, int32_t n_parts, const int64_t* 
   return SEDACS_OK;
 }
 
+// ---- core refinement for the 128-orbital tiles ----------------------------------------------------
+// Each subgraph's solve costs about T^3 with T = ceil(n / 128) (n orbitals of core + halo, the
+// tile size of the tensor-core products).  Single core atoms move to an adjacent core while that
+// lowers the integer score sum 128000 T^3 + (n - 128 (T - 1)) (T^3 - (T - 1)^3): the padded cost
+// plus a pull of n toward the boundary below.  Cores more than 48 orbitals above that boundary
+// are left alone; a core keeps at least min_core atoms.  Order: cores by index, a sorted snapshot
+// of each core's atoms, target cores ascending, the first best strict improvement.
+namespace {
+long long refine_score(long long n) {
+  const long long t = (n + 127) / 128;
+  return 128000 * t * t * t + (n - 128 * (t - 1)) * (t * t * t - (t - 1) * (t - 1) * (t - 1));
+}
+long long ceil128(long long n) { return (n + 127) / 128; }
+}  // namespace
+
+sedacs_status sedacs_refine_cores(sedacs_ctx* ctx, int32_t rounds, int32_t min_core, int64_t* score_before,
+                                  int64_t* score_after) {
+  if (!ctx || rounds < 0 || min_core < 1) return SEDACS_EINVAL;
+  if (!ctx->have_graph || !ctx->have_subs) { ctx->err = "refine: build the graph and the cores first"; return SEDACS_EINVAL; }
+  const int N = ctx->N, P = ctx->lay.n_sub;
+  CUCHK(cudaStreamSynchronize(ctx->stream));
+  std::vector<long long> rp(N + 1);
+  CUCHK(cudaMemcpy(rp.data(), ctx->d_row_ptr, sizeof(long long) * (N + 1), cudaMemcpyDeviceToHost));
+  std::vector<int> col(rp[N]);
+  if (rp[N] > 0) CUCHK(cudaMemcpy(col.data(), ctx->d_col, sizeof(int) * rp[N], cudaMemcpyDeviceToHost));
+  std::vector<int> norb(N), core_of(N, -1);
+  for (int a = 0; a < N; ++a) norb[a] = ctx->model.n_orb[ctx->species_h[a]];
+  std::vector<std::vector<int>> mem(P);
+  for (int c = 0; c < P; ++c) {
+    const int nc = ctx->lay.n_core_atoms[c];
+    for (int k = 0; k < nc; ++k) mem[c].push_back(ctx->sub_atoms_h[ctx->sub_ptr_h[c] + k]);
+    std::sort(mem[c].begin(), mem[c].end());
+    for (int a : mem[c]) core_of[a] = c;
+  }
+  for (int a = 0; a < N; ++a)
+    if (core_of[a] < 0) { ctx->err = "refine: the cores do not cover every atom"; return SEDACS_EINVAL; }
+  std::vector<int> stamp(N, 0);
+  int tag = 0;
+  // orbitals of core c + its halo, with membership read from core_of (skip: an atom left out of
+  // the member list, extra: an atom added to it)
+  auto orbs = [&](int c, int skip, int extra) -> long long {
+    ++tag;
+    long long n = 0;
+    auto visit = [&](int a) {
+      n += norb[a];
+      for (long long p = rp[a]; p < rp[a + 1]; ++p) {
+        const int b = col[p];
+        if (core_of[b] != c && stamp[b] != tag) {
+          stamp[b] = tag;
+          n += norb[b];
+        }
+      }
+    };
+    for (int a : mem[c])
+      if (a != skip) visit(a);
+    if (extra >= 0) visit(extra);
+    return n;
+  };
+  std::vector<long long> n(P);
+  long long before = 0;
+  for (int c = 0; c < P; ++c) {
+    n[c] = orbs(c, -1, -1);
+    before += refine_score(n[c]);
+  }
+  for (int r = 0; r < rounds; ++r) {
+    int moves = 0;
+    for (int c = 0; c < P; ++c) {
+      if (ceil128(n[c]) == ceil128(std::max<long long>(n[c] - 48, 1))) continue;
+      const std::vector<int> snap = mem[c];
+      for (int a : snap) {
+        if ((int)mem[c].size() <= min_core) break;
+        std::vector<int> targets;
+        for (long long p = rp[a]; p < rp[a + 1]; ++p)
+          if (core_of[col[p]] != c) targets.push_back(core_of[col[p]]);
+        std::sort(targets.begin(), targets.end());
+        targets.erase(std::unique(targets.begin(), targets.end()), targets.end());
+        long long best = 0, bnc = 0, bnd = 0;
+        int bd = -1;
+        for (int d : targets) {
+          core_of[a] = d;
+          const long long nc = orbs(c, a, -1), nd = orbs(d, -1, a);
+          core_of[a] = c;
+          const long long delta = refine_score(nc) + refine_score(nd) - refine_score(n[c]) - refine_score(n[d]);
+          if (delta < 0 && (bd < 0 || delta < best)) { best = delta; bd = d; bnc = nc; bnd = nd; }
+        }
+        if (bd >= 0) {
+          mem[c].erase(std::lower_bound(mem[c].begin(), mem[c].end(), a));
+          mem[bd].insert(std::upper_bound(mem[bd].begin(), mem[bd].end(), a), a);
+          core_of[a] = bd;
+          n[c] = bnc;
+          n[bd] = bnd;
+          ++moves;
+        }
+      }
+    }
+    if (moves == 0) break;
+  }
+  long long after = 0;
+  for (int c = 0; c < P; ++c) after += refine_score(n[c]);
+  if (score_before) *score_before = before;
+  if (score_after) *score_after = after;
+  CUCHK(ctx->part.set_cores(mem, N, ctx->stream));
+  ctx->have_cores = true;
+  STCHK(halos_core(ctx));
+  return SEDACS_OK;
+}
+
 sedacs_status sedacs_update_halos(sedacs_ctx* ctx) {
   if (!ctx) return SEDACS_EINVAL;
   return halos_core(ctx);

@@ -23,7 +23,7 @@ MD_C_K0 = 0.05
 
 
 def ground_state(workload: str, precision: int, seed_v: int = 20260703, quick: bool = False,
-                 core_size: int = 32):
+                 core_size: int = 32, refine: bool = False):
     """SCC ground state (mu from Eq. 2 at 300 K) and Maxwell-Boltzmann velocities at 300 K.
 
     Returns (system, model, ctx, R, V, n, info) with ctx ready for sedacs_xlbomd_init (kernel
@@ -31,7 +31,9 @@ def ground_state(workload: str, precision: int, seed_v: int = 20260703, quick: b
     Krylov) in the three-plane bf16 form (precision 4, 24-bit products); a context of the
     requested form (FP64 plain, or form 1) then receives its charges, mu and density graph, so
     all forms start from the same state.
-    quick=True starts from zero charges (same per-step work, no SCC)."""
+    quick=True starts from zero charges (same per-step work, no SCC).
+    refine=True refines the recursive-bisection cores for the 128-orbital tiles of the subgraph
+    solves (sedacs_refine_cores) after each partition."""
     s = I.workload(workload)
     model = I.default_model()
     R = np.ascontiguousarray(s.R.copy())
@@ -43,6 +45,8 @@ def ground_state(workload: str, precision: int, seed_v: int = 20260703, quick: b
     ctx = S.sedacs_create(s.species, s.box, model, prm)
     S.sedacs_graph_build(ctx, R)
     S.sedacs_partition(ctx, R)
+    if refine:
+        S.sedacs_refine_cores(ctx)
     it = it2 = 0
     res2 = None
     if quick:
@@ -60,6 +64,8 @@ def ground_state(workload: str, precision: int, seed_v: int = 20260703, quick: b
         ctx = S.sedacs_create(s.species, s.box, model, prm)
         S.sedacs_graph_build(ctx, R, gd=gd)
         S.sedacs_partition(ctx, R)
+        if refine:
+            S.sedacs_refine_cores(ctx)
     # dynamics with the scaled-delta kernel K0 = -c I (SI Sec. B)
     prm.kernel = 0
     prm.c_k0 = MD_C_K0

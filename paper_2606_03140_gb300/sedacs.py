@@ -79,6 +79,7 @@ def _load():
         "sedacs_kernel_stats_fp16": (I32, [P, P, P, P, P]),
         "sedacs_checkpoint_save": (I32, [P, C.c_char_p]),
         "sedacs_selftest_wait": (I32, [P, I32]),
+        "sedacs_refine_cores": (I32, [P, I32, I32, P, P]),
         "sedacs_checkpoint_load": (I32, [P, C.c_char_p]),
         "sedacs_set_params": (I32, [P, P]),
         "sedacs_graph_build_noalloc": (I32, [P, I32, P, D, P, P, I64, P, P]),
@@ -113,6 +114,7 @@ EXPORTED = (
     "sedacs_gnn_init", "sedacs_gnn_set_params", "sedacs_gnn_get_params", "sedacs_gnn_apply", "sedacs_gnn_param_grad",
     "sedacs_gnn_collect", "sedacs_gnn_train", "sedacs_kernel_judge", "sedacs_density_info", "sedacs_charges",
     "sedacs_kernel_stats_fp16", "sedacs_checkpoint_save", "sedacs_checkpoint_load", "sedacs_selftest_wait",
+    "sedacs_refine_cores",
 )
 
 
@@ -357,6 +359,14 @@ def sedacs_kernel_stats_fp16(ctx):
     by = C.c_double()
     _check(ctx, _lib.sedacs_kernel_stats_fp16(ctx, C.byref(ms), C.byref(nl), C.byref(fl), C.byref(by)))
     return ms.value, nl.value, fl.value, by.value
+
+
+def sedacs_refine_cores(ctx, rounds: int = 4, min_core: int = 16) -> tuple[int, int]:
+    """Refine the cores for the 128-orbital tiles; returns (score before, score after)."""
+    b = C.c_int64()
+    a = C.c_int64()
+    _check(ctx, _lib.sedacs_refine_cores(ctx, int(rounds), int(min_core), C.byref(b), C.byref(a)))
+    return b.value, a.value
 
 
 def sedacs_selftest_wait(ctx, limit_us: int) -> int:

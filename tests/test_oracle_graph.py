@@ -218,6 +218,21 @@ def _refine_case():
     return s, rp, col, cores, norb
 
 
+def test_refine_score_orders_by_padded_tiles_then_size():
+    """The score ranks subgraphs by their padded cube cost T^3 (T = 128-orbital tiles) first, and
+    within one T by size, so that a move that drops a subgraph below a tile boundary always wins."""
+    prev = None
+    for n in range(1, 18 * 128 + 1):
+        t = (n + 127) // 128
+        sc = graph.refine_score(n)
+        assert sc // 128000 == t ** 3, n
+        if prev is not None:
+            assert sc > prev, n
+        prev = sc
+    # at the boundaries: 128 orbitals fill one tile, 129 need 2 x 2 x 2
+    assert graph.refine_score(128) < 2 * 128000 < graph.refine_score(129)
+
+
 def test_refine_cores_valid_cover_and_score_does_not_rise():
     s, rp, col, cores, norb = _refine_case()
     new, before, after = graph.refine_cores(rp, col, cores, norb, rounds=50, min_core=12)
