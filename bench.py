@@ -228,7 +228,7 @@ def frame_check(parts, R, n, q, mu, picks, model, species, box):
     halos = [sa[sp[i] + nc[i]:sp[i + 1]] for i in picks]
     atoms = np.unique(np.concatenate([sa[sp[i]:sp[i + 1]] for i in picks]))
     V = oew.coulomb_potential(R, species, model.hubbard_u, box, n, rows=atoms)
-    ref = odn.density(R, species, box, model, n, cores, halos, mu=mu, V=V)
+    ref = odn.density(R, species, box, model, n, cores, halos, mu=mu, V=V, eig="lapack")
     a = np.concatenate(cores)
     d = np.abs(q[a] - ref.q[a])
     return float(np.max(d)), float(np.sqrt(np.mean(d ** 2))), int(np.sum(d > 1e-5)), int(d.shape[0])
@@ -501,7 +501,8 @@ class OracleStep:
         t_graph = time.perf_counter() - t0
         pick = self.rng.choice(len(cores), size=min(self.sample, len(cores)), replace=False)
         t0 = time.perf_counter()
-        odn.density(s.R, s.species, s.box, self.m, self.n, [cores[i] for i in pick], [hal[i] for i in pick], V=self.V)
+        odn.density(s.R, s.species, s.box, self.m, self.n, [cores[i] for i in pick], [hal[i] for i in pick], V=self.V,
+                    eig="lapack")
         t_sub = time.perf_counter() - t0
         t_step = t_graph + 2.0 * self.t_ew + t_sub * len(cores) / len(pick)
         return {"t_step": t_step, "t_graph": t_graph, "t_sub": t_sub, "P": len(cores), "picked": len(pick)}

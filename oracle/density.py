@@ -14,7 +14,9 @@ What is computed, in the paper's order:
    Partitioned Graphs"); h~ = Z h Z.
 4. The Fermi operator D = [exp(beta (h~ - mu I)) + I]^(-1) (Eq. 2) through the
    eigen-decomposition of h~ (the paper allows direct diagonalisation, Sec. "Density
-   Matrix Evaluation on Partitioned Graphs"); spin factor 2, closed shell.
+   Matrix Evaluation on Partitioned Graphs"); spin factor 2, closed shell.  Steps 3-4
+   run in plain C by cyclic Jacobi rotations (``cjacobi``, default) or through
+   numpy.linalg.eigh (``eig="lapack"``).
 5. One chemical potential mu for the whole system with Tr[D S] = N_e (Eq. 2, with the
    trace read as the collected count): N(mu) = 2 sum_i sum_k w_ik f(eps_ik - mu) = N_e,
    w_ik the core Mulliken weight of state k of subgraph i, f the Fermi function at Te
@@ -48,7 +50,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import BOHR_A, KB_HA, ewald, sk
+from . import BOHR_A, KB_HA, cjacobi, ewald, sk
 
 
 def fermi(x: np.ndarray, beta: float) -> np.ndarray:
@@ -130,23 +132,62 @@ class DensityResult:
     Te: float = 300.0
 
 
-def subgraph_setup(atoms, n_core, R, species, box, model, V):
-    """h, s, Z = s^-1/2, eigenpairs of h~ = Z h Z, and core weights of one subgraph."""
+# Eigensolver of the subgraph solves: "jacobi" is the plain-C cyclic Jacobi method of
+# ``oracle/csrc/jacobi.c`` (Z, h~, eigenpairs and core weights in C, subgraphs spread over the host
+# threads); "lapack" is numpy.linalg.eigh with the same steps in numpy.  The two agree to ~1e-13 on
+# the eigenvalues (tests/test_oracle_jacobi.py).
+EIG = "jacobi"
+
+
+def subgraph_blocks(atoms, R, species, box, model, V):
+    """h = H[n] and s = S restricted to one subgraph's orbitals, with H0, orbitals per atom and
+    orbital offsets: H[n] = H0 + 1/2 (S V + V S), V diagonal per atom."""
     H0, S, norb, off = sk.hs_blocks_for_atoms(atoms, R, species, box, model)
     vorb = np.repeat(V[atoms], norb)
     H = H0 + 0.5 * S * (vorb[:, None] + vorb[None, :])
+    return H0, H, S, norb, off
+
+
+def _solution(atoms, n_core, blocks, Z, eps, X, Cc, w):
+    H0, H, S, norb, off = blocks
+    Ht = Z @ H @ Z
+    Ht = 0.5 * (Ht + Ht.T)
+    return SubgraphSolution(atoms=np.asarray(atoms), n_core=int(n_core), norb=norb, off=off,
+                            H0=H0, H=H, S=S, Z=Z, eps=eps, C=Cc, X=X, w=w, bounds=gershgorin(Ht))
+
+
+def _eig_lapack(H, S, nco):
     lam, U = np.linalg.eigh(S)
     Z = (U * (1.0 / np.sqrt(lam))[None, :]) @ U.T
     Ht = Z @ H @ Z
     Ht = 0.5 * (Ht + Ht.T)
     eps, X = np.linalg.eigh(Ht)
     Cc = Z @ X
-    nco = int(off[n_core])
     SC = S @ Cc
     w = np.sum(Cc[:nco, :] * SC[:nco, :], axis=0)
-    return SubgraphSolution(atoms=np.asarray(atoms), n_core=int(n_core), norb=norb, off=off,
-                            H0=H0, H=H, S=S, Z=Z, eps=eps, C=Cc, X=X, w=w,
-                            bounds=gershgorin(Ht))
+    return Z, eps, X, Cc, w
+
+
+def subgraph_setup(atoms, n_core, R, species, box, model, V, eig: str | None = None):
+    """h, s, Z = s^-1/2, eigenpairs of h~ = Z h Z, and core weights of one subgraph."""
+    blocks = subgraph_blocks(atoms, R, species, box, model, V)
+    _, H, S, _, off = blocks
+    nco = int(off[n_core])
+    if (eig or EIG) == "jacobi":
+        sol = cjacobi.subgraph_eig(H, S, nco)
+    else:
+        sol = _eig_lapack(H, S, nco)
+    return _solution(atoms, n_core, blocks, *sol)
+
+
+def subgraph_setup_all(atom_lists, n_cores, R, species, box, model, V, eig: str | None = None):
+    """subgraph_setup over many subgraphs (the Jacobi route solves them on the host threads)."""
+    blocks = [subgraph_blocks(a, R, species, box, model, V) for a in atom_lists]
+    if (eig or EIG) == "jacobi":
+        sols = cjacobi.subgraph_eig_batch([(b[1], b[2], int(b[4][nc])) for b, nc in zip(blocks, n_cores)])
+    else:
+        sols = [_eig_lapack(b[1], b[2], int(b[4][nc])) for b, nc in zip(blocks, n_cores)]
+    return [_solution(a, nc, b, *sol) for a, nc, b, sol in zip(atom_lists, n_cores, blocks, sols)]
 
 
 def collected_count(eps_list, w_list, mu: float, beta: float) -> float:
@@ -188,7 +229,8 @@ def entropy_density(f: np.ndarray) -> np.ndarray:
 
 
 def density(R, species, box, model, n, cores, halo_lists, Te: float = 300.0, mu: float | None = None,
-            mode: str = "fermi", sp2_tol: float = 1e-9, V: np.ndarray | None = None) -> DensityResult:
+            mode: str = "fermi", sp2_tol: float = 1e-9, V: np.ndarray | None = None,
+            eig: str | None = None) -> DensityResult:
     """Graph-partitioned density at trial charges n: charges, band energy, mu, core rows of D and W.
 
     mode "fermi": Fermi occupations at Te (default), mu from Eq. 2 (``solve_mu``) unless
@@ -199,10 +241,8 @@ def density(R, species, box, model, n, cores, halo_lists, Te: float = 300.0, mu:
     species = np.asarray(species)
     if V is None:
         V = ewald.coulomb_potential(R, species, model.hubbard_u, box, n)
-    subs = []
-    for core, halo in zip(cores, halo_lists):
-        atoms = np.concatenate([core, halo]).astype(np.int64)
-        subs.append(subgraph_setup(atoms, len(core), R, species, box, model, V))
+    atom_lists = [np.concatenate([core, halo]).astype(np.int64) for core, halo in zip(cores, halo_lists)]
+    subs = subgraph_setup_all(atom_lists, [len(c) for c in cores], R, species, box, model, V, eig=eig)
     n_e = float(np.sum(np.asarray(model.z_val)[species]))
     if mode == "sp2" and mu is None:
         raise ValueError("the T -> 0 SP2 occupations take a given chemical potential")

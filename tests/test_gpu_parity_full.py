@@ -23,6 +23,10 @@ With these seeded trial charges mu lies inside a band (dN/dmu ~ 1,900 e/Ha, 76 l
   beta / 4 x 2.1e-6 ~ 5.5e-4 e; so mu is held to 2.5e-6 Ha, those atoms to 6e-4 e and the RMS
   over all atoms to 1e-5 e.
 
+The oracle's subgraph eigensolves take its LAPACK route here (562 solves of ~500 orbitals; the
+plain-C Jacobi route agrees with it to ~1e-13 on the eigenvalues and 1e-11 e on the charges, and
+would take minutes at this size).
+
 The plain FP64 form is held to 5e-9 e on every atom: its recursion's inverse polynomial (degree 15,
 fit error 8.2e-13) errs by that much at each doubling, and a level at mu carries the error of the
 first doubling amplified by 2^n (n = 11 here), ~1.7e-9 in its occupation.
@@ -51,10 +55,10 @@ def full():
     V = oew.coulomb_potential(s.R, s.species, m.hubbard_u, s.box, n)
     rp0, col0 = og.build_graph(s.R, s.box, 3.0)
     cores = og.rcb_partition(s.R, s.box, 32)
-    r0 = odn.density(s.R, s.species, s.box, m, n, cores, og.halos(rp0, col0, cores), V=V)
+    r0 = odn.density(s.R, s.species, s.box, m, n, cores, og.halos(rp0, col0, cores), V=V, eig="lapack")
     rp1, col1 = og.build_graph(s.R, s.box, 3.0, r0.gd, 1e-3)
     hal1 = og.halos(rp1, col1, cores)
-    ref = odn.density(s.R, s.species, s.box, m, n, cores, hal1, V=V)
+    ref = odn.density(s.R, s.species, s.box, m, n, cores, hal1, V=V, eig="lapack")
     atoms = np.concatenate([cores[i] for i in PICK])
     Fref = odn.forces(ref, n, s.R, s.species, s.box, m, atoms=atoms)
     R = np.ascontiguousarray(s.R)

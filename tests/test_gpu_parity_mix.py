@@ -2,7 +2,7 @@
 cores and halos bit for bit on the whole system, charges of sampled subgraphs (C/O sp and H s
 orbitals) within the 1e-5 e bound, at zero trial charges and one chemical potential in a clean
 window of the sampled spectra, given to both sides (Fermi occupations at 300 K; the oracle solves
-the sampled subgraphs one by one)."""
+the sampled subgraphs one by one, through its LAPACK eigensolver route)."""
 import numpy as np
 import pytest
 
@@ -24,14 +24,14 @@ def test_mixture_graph_and_sampled_charges():
     cores = og.rcb_partition(s.R, s.box, 32)
     hal = og.halos(rp_o, col_o, cores)
     res0 = odn.density(s.R, s.species, s.box, m, np.zeros(s.n_atoms), [cores[i] for i in PICK],
-                       [hal[i] for i in PICK], mu=-0.1, V=np.zeros(s.n_atoms))
+                       [hal[i] for i in PICK], mu=-0.1, V=np.zeros(s.n_atoms), eig="lapack")
     e = np.sort(np.concatenate([sg.eps[sg.w > 1e-6] for sg in res0.subs]))
     e = e[(e > -0.35) & (e < 0.05)]
     k = int(np.argmax(np.diff(e)))
     mu = 0.5 * (e[k] + e[k + 1])
     assert e[k + 1] - e[k] > 0.05
     ref = odn.density(s.R, s.species, s.box, m, np.zeros(s.n_atoms), [cores[i] for i in PICK],
-                      [hal[i] for i in PICK], mu=mu, V=np.zeros(s.n_atoms))
+                      [hal[i] for i in PICK], mu=mu, V=np.zeros(s.n_atoms), eig="lapack")
     R = np.ascontiguousarray(s.R)
     ctx = S.sedacs_create(s.species, s.box, m, S.sedacs_default_params(core_size=32, precision=1, mu_given=1))
     try:
