@@ -2147,6 +2147,7 @@ sedacs_status sedacs_partition(sedacs_ctx* ctx, const double* R, int32_t* n_part
 
 sedacs_status sedacs_set_cores(sedacs_ctx* ctx, int32_t n_parts, const int64_t* core_ptr, const int32_t* core) {
   if (!ctx || n_parts <= 0 || !core_ptr || !core) return SEDACS_EINVAL;
+  if (n_parts > ctx->N) { ctx->err = "more cores than atoms"; return SEDACS_EINVAL; }
   std::vector<int64_t> cp(n_parts + 1);
   CUCHK(cudaMemcpy(cp.data(), core_ptr, sizeof(int64_t) * (n_parts + 1), cudaMemcpyDefault));
   if (cp[0] != 0 || cp[n_parts] != ctx->N) { ctx->err = "cores must cover every atom once"; return SEDACS_EINVAL; }
@@ -2155,7 +2156,7 @@ sedacs_status sedacs_set_cores(sedacs_ctx* ctx, int32_t n_parts, const int64_t* 
   std::vector<std::vector<int>> cores(n_parts);
   std::vector<char> seen(ctx->N, 0);
   for (int i = 0; i < n_parts; ++i) {
-    if (cp[i + 1] < cp[i]) return SEDACS_EINVAL;
+    if (cp[i + 1] <= cp[i]) { ctx->err = "every core holds at least one atom"; return SEDACS_EINVAL; }
     for (long long q = cp[i]; q < cp[i + 1]; ++q) {
       const int a = all[q];
       if (a < 0 || a >= ctx->N || seen[a]) { ctx->err = "cores must cover every atom once"; return SEDACS_EINVAL; }
@@ -2642,14 +2643,32 @@ sedacs_status sedacs_checkpoint_load(sedacs_ctx* ctx, const char* path) {
     ctx->err = "checkpoint: not a checkpoint file of this version";
     return SEDACS_EIO;
   }
-  if (h.n_atoms != N || h.precision != ctx->prm.precision || h.Te != ctx->prm.Te || h.n_parts <= 0 ||
-      h.gd_nnz < 0 || h.hist_head < 0 || h.hist_head >= 6) {
+  if (h.n_atoms != N || h.precision != ctx->prm.precision || h.Te != ctx->prm.Te) {
     std::fclose(f);
     ctx->err = "checkpoint: atom count, precision form or electronic temperature differ from this context";
     return SEDACS_EINVAL;
   }
+  if (h.n_parts <= 0 || h.n_parts > N || h.gd_nnz < 0 || h.gd_nnz > 1LL * N * N || h.hist_head < 0 ||
+      h.hist_head >= 6) {
+    std::fclose(f);
+    ctx->err = "checkpoint: inconsistent header";
+    return SEDACS_EIO;
+  }
   const int P = h.n_parts;
   const long long nnz = h.gd_nnz;
+  {
+    // the file must hold exactly what the header announces (checked before allocating for it)
+    const long long want = (long long)sizeof(h) + 8LL * (3LL * N * 3 + 2LL * N + 6LL * N) + 8LL * (N + 1) +
+                           12LL * nnz + 8LL * (P + 1) + 4LL * N;
+    const long pos = std::ftell(f);
+    const bool sized = pos >= 0 && std::fseek(f, 0, SEEK_END) == 0;
+    const long end = sized ? std::ftell(f) : -1;
+    if (!sized || end != want || std::fseek(f, pos, SEEK_SET) != 0) {
+      std::fclose(f);
+      ctx->err = "checkpoint: truncated or inconsistent file";
+      return SEDACS_EIO;
+    }
+  }
   std::vector<double> R(3LL * N), V(3LL * N), F(3LL * N), n(N), q(N), hist(6LL * N), gval(nnz);
   std::vector<long long> gptr(N + 1), cptr(P + 1);
   std::vector<int> gcol(nnz), core(N);
@@ -2677,7 +2696,7 @@ sedacs_status sedacs_checkpoint_load(sedacs_ctx* ctx, const char* path) {
   std::vector<std::vector<int>> cores(P);
   std::vector<char> seen(N, 0);
   for (int i = 0; i < P; ++i) {
-    if (cptr[i + 1] < cptr[i]) { ctx->err = "checkpoint: inconsistent cores"; return SEDACS_EIO; }
+    if (cptr[i + 1] <= cptr[i]) { ctx->err = "checkpoint: inconsistent cores"; return SEDACS_EIO; }
     for (long long k = cptr[i]; k < cptr[i + 1]; ++k) {
       const int a = core[k];
       if (a < 0 || a >= N || seen[a]) { ctx->err = "checkpoint: inconsistent cores"; return SEDACS_EIO; }

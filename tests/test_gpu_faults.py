@@ -8,6 +8,8 @@
   SEDACS_ETIMEOUT (sedacs_selftest_wait: the same bit every bounded wait of the library raises);
   the context stays usable.
 * An SCC cut off after two iterations from zero charges returns SEDACS_ENOCONV.
+* Invalid cores given by the host are refused with SEDACS_EINVAL and leave the context's cores as
+  they were.
 """
 import numpy as np
 import pytest
@@ -74,3 +76,33 @@ def test_scc_cut_short_reports_enoconv():
     finally:
         S.sedacs_destroy(ctx)
     assert not ok and it == 2 and resid > 1e-3
+
+
+def test_invalid_cores_are_refused_and_context_recovers():
+    """Cores that leave an atom out, repeat one, hold no atom or outnumber the atoms are refused
+    with SEDACS_EINVAL before anything reaches the device; the context keeps its cores."""
+    from paper_2606_03140_gb300 import sedacs as S
+
+    s, ctx, R = _ctx(S)
+    try:
+        sp, sa, nc = S.sedacs_parts_get(ctx)
+        good = [sa[sp[i]:sp[i] + nc[i]].copy() for i in range(len(nc))]
+        n = np.ascontiguousarray(I.random_charges(96, 3, 0.05))
+        mu0, q0, _, _ = S.sedacs_subgraph_density(ctx, R, n)
+        bad_sets = [
+            [good[0][1:]] + good[1:],                                   # an atom left out
+            [np.concatenate([good[0], good[1][:1]])] + good[1:],        # an atom in two cores
+            good + [np.zeros(0, np.int32)],                             # an empty core
+            [np.array([a], np.int32) for a in range(96)] + [np.array([0], np.int32)],  # 97 cores
+        ]
+        for cores in bad_sets:
+            with pytest.raises(S.SedacsError) as ei:
+                S.sedacs_set_cores(ctx, cores)
+            assert ei.value.status == 1                                 # SEDACS_EINVAL
+        sp1, sa1, nc1 = S.sedacs_parts_get(ctx)
+        assert np.array_equal(sp1, sp) and np.array_equal(sa1, sa) and np.array_equal(nc1, nc)
+        mu1, q1, _, _ = S.sedacs_subgraph_density(ctx, R, n)
+        # the second solve may start mu from the first one's, so equal up to the solve's tolerance
+        assert abs(mu1 - mu0) < 1e-8 and np.max(np.abs(q1 - q0)) < 1e-6
+    finally:
+        S.sedacs_destroy(ctx)
