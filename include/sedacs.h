@@ -281,6 +281,18 @@ sedacs_status sedacs_kernel_stats(sedacs_ctx* ctx, int32_t on, double* sp2_ms, i
 sedacs_status sedacs_kernel_stats_fp16(sedacs_ctx* ctx, double* ms, int64_t* launches, double* flops,
                                        double* bytes);
 
+/* Assignment of whole subgraphs to n_ranks ranks for a step sharded over several GPUs (host
+ * only; needs no context and no GPU).  The subgraph solves are independent, with a cost that grows
+ * as the cube of the orbital count (Sec. "Scalability"); the caller passes one cost per subgraph
+ * (host array, >= 0 and finite; n_i^3 for the subgraph solves).  LPT (Graham 1969): subgraphs in
+ * descending cost, equal costs by ascending index, each to the rank with the least load so far,
+ * equal loads to the lowest rank; the largest load is within 4/3 - 1/(3 n_ranks) of the optimum.
+ * owner[n_sub] receives each subgraph's rank, rank_load[n_ranks] each rank's summed cost (host
+ * arrays, caller-owned).  n_sub < 0, n_ranks <= 0, a null array or a negative or non-finite cost
+ * -> SEDACS_EINVAL. */
+sedacs_status sedacs_shard_lpt(int32_t n_sub, const double* cost, int32_t n_ranks, int32_t* owner,
+                               double* rank_load);
+
 /* Core refinement for the tiles of the subgraph solves (not in the paper, which notes that a
  * subgraph's cost grows with the cube of its size).  The tensor-core products work on 128-orbital
  * tiles, so a subgraph of n orbitals (core + halo) costs about T^3, T = ceil(n / 128).  Single core

@@ -13,7 +13,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsedacs.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--extended-lambda", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
-SOURCES = ["dense_gemm.cu", "dense_ops.cu", "graph.cu", "ewald.cu", "sk.cu", "engine.cu", "noalloc.cu", "gnn.cu"]
+SOURCES = ["dense_gemm.cu", "dense_ops.cu", "graph.cu", "ewald.cu", "sk.cu", "engine.cu", "noalloc.cu", "gnn.cu",
+           "shard.cu"]
 
 
 def nvcc() -> str:

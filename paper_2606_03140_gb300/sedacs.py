@@ -80,6 +80,7 @@ def _load():
         "sedacs_checkpoint_save": (I32, [P, C.c_char_p]),
         "sedacs_selftest_wait": (I32, [P, I32]),
         "sedacs_refine_cores": (I32, [P, I32, I32, P, P]),
+        "sedacs_shard_lpt": (I32, [I32, P, I32, P, P]),
         "sedacs_checkpoint_load": (I32, [P, C.c_char_p]),
         "sedacs_set_params": (I32, [P, P]),
         "sedacs_graph_build_noalloc": (I32, [P, I32, P, D, P, P, I64, P, P]),
@@ -114,7 +115,7 @@ EXPORTED = (
     "sedacs_gnn_init", "sedacs_gnn_set_params", "sedacs_gnn_get_params", "sedacs_gnn_apply", "sedacs_gnn_param_grad",
     "sedacs_gnn_collect", "sedacs_gnn_train", "sedacs_kernel_judge", "sedacs_density_info", "sedacs_charges",
     "sedacs_kernel_stats_fp16", "sedacs_checkpoint_save", "sedacs_checkpoint_load", "sedacs_selftest_wait",
-    "sedacs_refine_cores",
+    "sedacs_refine_cores", "sedacs_shard_lpt",
 )
 
 
@@ -367,6 +368,15 @@ def sedacs_refine_cores(ctx, rounds: int = 4, min_core: int = 16) -> tuple[int, 
     a = C.c_int64()
     _check(ctx, _lib.sedacs_refine_cores(ctx, int(rounds), int(min_core), C.byref(b), C.byref(a)))
     return b.value, a.value
+
+
+def sedacs_shard_lpt(cost, n_ranks: int):
+    """LPT assignment of subgraphs (costs) to ranks: (owner per subgraph, load per rank)."""
+    c = np.ascontiguousarray(cost, dtype=np.float64)
+    owner = np.zeros(max(len(c), 1), np.int32)
+    load = np.zeros(max(int(n_ranks), 1), np.float64)
+    _check(None, _lib.sedacs_shard_lpt(len(c), _ptr(c), int(n_ranks), _ptr(owner), _ptr(load)))
+    return owner[:len(c)], load[:int(n_ranks)]
 
 
 def sedacs_selftest_wait(ctx, limit_us: int) -> int:
