@@ -37,7 +37,7 @@ def _rank(rank, world, port, out):
 def test_replicas_take_the_slowest_rank():
     mp = pytest.importorskip("torch.multiprocessing")
     port = _free_port()
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:       # no fork of a threaded test process
         out = mgr.dict()
         mp.spawn(_rank, args=(2, port, out), nprocs=2, join=True)
         res = dict(out)

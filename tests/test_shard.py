@@ -164,7 +164,7 @@ def test_sharded_step_exchange_matches_single_process_oracle():
     from oracle import density as odn
 
     port = _free_port()
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:       # no fork of a threaded test process
         out = mgr.dict()
         mp.spawn(_rank, args=(2, port, out), nprocs=2, join=True)
         res = dict(out)
