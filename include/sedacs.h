@@ -154,7 +154,10 @@ sedacs_status sedacs_graph_get(sedacs_ctx* ctx, int64_t* row_ptr, int32_t* col);
  * positions into round(N/core_size) cores, then the one-hop halo of every core on the
  * current graph.  *n_parts receives the number of subgraphs. */
 sedacs_status sedacs_partition(sedacs_ctx* ctx, const double* R, int32_t* n_parts);
-/* Use caller-given cores (core_ptr [n_parts+1], core atoms ascending) instead of RCB. */
+/* Use caller-given cores (core_ptr [n_parts+1], core [N]; host or device arrays, read only)
+ * instead of RCB, each core's atoms sorted on entry.  Every atom in exactly one core, every core
+ * holding at least one atom (so n_parts <= N); otherwise SEDACS_EINVAL with the context's cores
+ * unchanged.  With a graph present the halos are recomputed. */
 sedacs_status sedacs_set_cores(sedacs_ctx* ctx, int32_t n_parts, const int64_t* core_ptr, const int32_t* core);
 /* Recompute the halos of the current cores on the current graph. */
 sedacs_status sedacs_update_halos(sedacs_ctx* ctx);
