@@ -44,7 +44,7 @@ static double off_norm2(int n, const double* a) {
 /* Eigen-decomposition of the symmetric n x n matrix a (row-major, destroyed).  On return
  * w[0..n) holds the eigenvalues in ascending order and column k of v (row-major n x n) the unit
  * eigenvector of w[k].  work: n^2 + n doubles.  Returns the number of sweeps, -1 without
- * convergence within 60 sweeps, -2 for n < 0. */
+ * convergence within 60 sweeps, -2 for n < 0, -4 when out of memory. */
 int oracle_jacobi_eigh(int n, double* a, double* v, double* w, double* work) {
   if (n < 0) return -2;
   if (n == 0) return 0;
@@ -100,7 +100,7 @@ int oracle_jacobi_eigh(int n, double* a, double* v, double* w, double* work) {
   /* ascending order: selection of the smallest remaining diagonal entry (ties keep index order) */
   for (int i = 0; i < n; ++i) w[i] = a[(int64_t)i * n + i];
   int* idx = (int*)malloc(sizeof(int) * (size_t)n);
-  if (!idx) return -2;
+  if (!idx) return -4;
   for (int i = 0; i < n; ++i) idx[i] = i;
   for (int i = 0; i < n; ++i) {
     int m = i;
