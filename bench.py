@@ -546,7 +546,7 @@ def run_reference(args, world, rank):
     return {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": args.workload, "implementation": "FP64 oracle (numpy/scipy) on host cores",
+            "config": {"workload": args.workload, "implementation": "FP64 oracle (numpy/scipy, subgraph eigensolves by its LAPACK route) on host cores",
                        "extrapolated": "each step's time is a bounded sample scaled to the full step (see cpu_baseline)"},
             "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
