@@ -133,8 +133,9 @@ static void matmul(int n, const double* a, const double* b, double* c) {
 }
 
 /* Steps 1-6 above for one subgraph.  h, s: n x n (row-major, read only).  Outputs: z (n x n),
- * eps (n), xv (n x n, the eigenvectors X of h~ in columns), cst (n x n, C = Z X), w (n).  Returns 0, or the negative status of the eigensolver
- * (-1: no convergence), or -3 when s is not positive definite, -4 when out of memory. */
+ * eps (n), xv (n x n, the eigenvectors X of h~ in columns), cst (n x n, C = Z X), w (n).
+ * Returns 0, or the negative status of the eigensolver (-1: no convergence), or -3 when s is not
+ * positive definite, -4 when out of memory. */
 int oracle_subgraph_eig(int n, int n_core_orb, const double* h, const double* s, double* z, double* eps,
                         double* xv, double* cst, double* w) {
   if (n < 0 || n_core_orb < 0 || n_core_orb > n) return -2;
