@@ -16,8 +16,9 @@ ewald    periodic Gaussian-gamma Coulomb matrix, potential and gradients (Ewald)
 graph    distance + density threshold graph, recursive coordinate bisection, halos
 density  subgraph solve (S^-1/2, Fermi operator), global mu, collection,
          Mulliken charges, shadow energy and forces
-cjacobi  the subgraph eigensolves in plain C by cyclic Jacobi rotations
-         (csrc/jacobi.c, compiled with gcc; density's default route)
+cjacobi  the plain-C parts: subgraph eigensolves by cyclic Jacobi rotations
+         (csrc/jacobi.c; density's default route) and the bisection for mu on
+         the collected count (csrc/mu.c), compiled with gcc
 dynamics SCC with linear mixing, XL-BOMD integrator, low-rank Krylov kernel
 gnn      message-passing preconditioner network, forward and backward
 

@@ -1,13 +1,17 @@
-"""ctypes access to the plain-C cyclic Jacobi eigensolver of the oracle (``oracle/csrc/jacobi.c``).
+"""ctypes access to the plain-C parts of the oracle: the cyclic Jacobi eigensolver and subgraph
+solve (``oracle/csrc/jacobi.c``) and the bisection for mu on the collected count
+(``oracle/csrc/mu.c``).
 
 Test infrastructure only (see ``oracle/__init__``).  The library is compiled with gcc (no vendor
 or CUDA code, no -march flags, IEEE arithmetic) into ``oracle/_build/`` by the package build step,
-or here on first use when it is missing or older than its source.
+or here on first use when it is missing or older than its sources.
 
 Pinned by tests: the 2 x 2 closed form; the eigenvalues a + 2 b cos(k pi / (n + 1)) of the
 tridiagonal Toeplitz matrix; a spectrum planted by an orthogonal similarity; eigenvectors
 orthonormal and A V = V diag(w); the subgraph solve against the LAPACK route of
-``density.subgraph_setup`` (eigenvalues, Z s Z = I, core weights) on water subgraphs.
+``density.subgraph_setup`` (eigenvalues, Z s Z = I, core weights) on water subgraphs; mu in the
+gap with the exact count in the full limit and against a brute-force scan of the count on a
+truncated graph (``tests/test_oracle_density.py``); the count against a plain sum.
 """
 from __future__ import annotations
 
@@ -18,17 +22,17 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-SRC = os.path.join(_HERE, "csrc", "jacobi.c")
-LIB = os.path.join(_HERE, "_build", "libjacobi.so")
+SRCS = [os.path.join(_HERE, "csrc", f) for f in ("jacobi.c", "mu.c")]
+LIB = os.path.join(_HERE, "_build", "liboracle.so")
 _lib = None
 
 
 def compile_lib(force: bool = False) -> str:
-    """gcc -O2 -fopenmp shared library from jacobi.c (rebuilt when the source is newer)."""
-    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
+    """gcc -O2 -fopenmp shared library from the C sources (rebuilt when a source is newer)."""
+    if force or not os.path.exists(LIB) or any(os.path.getmtime(LIB) < os.path.getmtime(f) for f in SRCS):
         os.makedirs(os.path.dirname(LIB), exist_ok=True)
         tmp = LIB + f".{os.getpid()}.tmp"
-        subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-o", tmp, SRC, "-lm"], check=True)
+        subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-o", tmp, *SRCS, "-lm"], check=True)
         os.replace(tmp, LIB)
     return LIB
 
@@ -44,6 +48,10 @@ def _load():
         lib.oracle_subgraph_eig.restype = C.c_int
         lib.oracle_subgraph_eig_batch.argtypes = [C.c_int, P, P, P, P, P, P, P, P, P, P, P, P]
         lib.oracle_subgraph_eig_batch.restype = C.c_int
+        lib.oracle_collected_count.argtypes = [C.c_int64, P, P, C.c_double, C.c_double]
+        lib.oracle_collected_count.restype = C.c_double
+        lib.oracle_solve_mu.argtypes = [C.c_int64, P, P, C.c_double, C.c_double, P]
+        lib.oracle_solve_mu.restype = C.c_int
         _lib = lib
     return _lib
 
@@ -113,3 +121,28 @@ def subgraph_eig_batch(blocks):
         out.append((Z[a:b].reshape(m, m), E[vo[i]:vo[i + 1]].copy(), X[a:b].reshape(m, m), Cs[a:b].reshape(m, m),
                     W[vo[i]:vo[i + 1]].copy()))
     return out
+
+
+def _flat(eps_list, w_list):
+    e = np.ascontiguousarray(np.concatenate([np.asarray(x, dtype=np.float64).ravel() for x in eps_list]))
+    w = np.ascontiguousarray(np.concatenate([np.asarray(x, dtype=np.float64).ravel() for x in w_list]))
+    if e.shape != w.shape:
+        raise ValueError("one core weight per state")
+    return e, w
+
+
+def collected_count(eps_list, w_list, mu: float, beta: float) -> float:
+    """N(mu) = 2 sum_i sum_k w_ik f(eps_ik - mu) (Eq. 2), summed in C in state order."""
+    e, w = _flat(eps_list, w_list)
+    return float(_load().oracle_collected_count(len(e), _p(e), _p(w), float(mu), float(beta)))
+
+
+def solve_mu(eps_list, w_list, n_e: float, beta: float) -> float:
+    """mu of Eq. 2 by bisection in C (bracket [min eps - 1, max eps + 1], |N - N_e| < 1e-11 or a
+    bracket narrower than 1e-15 Ha)."""
+    e, w = _flat(eps_list, w_list)
+    mu = C.c_double()
+    st = _load().oracle_solve_mu(len(e), _p(e), _p(w), float(n_e), float(beta), C.byref(mu))
+    if st < 0:
+        raise ValueError("mu bisection needs at least one state and finite inputs")
+    return mu.value

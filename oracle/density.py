@@ -201,21 +201,10 @@ def solve_mu(eps_list, w_list, n_e: float, beta: float) -> float:
     N(mu) is non-decreasing in mu (core weights of the collected states are positive up
     to the truncation; the test keeps the bracket).  Start [min eps - 1, max eps + 1];
     stop when |N - N_e| < 1e-11 or the interval is narrower than 1e-15 Ha; return the
-    midpoint.
+    midpoint.  The bisection runs in plain C (``oracle/csrc/mu.c``); ``collected_count`` above
+    is the same count in numpy, which the tests scan against it.
     """
-    lo = min(float(np.min(e)) for e in eps_list) - 1.0
-    hi = max(float(np.max(e)) for e in eps_list) + 1.0
-    mid = 0.5 * (lo + hi)
-    for _ in range(400):
-        mid = 0.5 * (lo + hi)
-        nel = collected_count(eps_list, w_list, mid, beta)
-        if abs(nel - n_e) < 1e-11 or hi - lo < 1e-15:
-            break
-        if nel < n_e:
-            lo = mid
-        else:
-            hi = mid
-    return mid
+    return cjacobi.solve_mu(eps_list, w_list, n_e, beta)
 
 
 def entropy_density(f: np.ndarray) -> np.ndarray:

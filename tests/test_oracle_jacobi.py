@@ -125,3 +125,19 @@ def test_density_jacobi_equals_lapack():
     assert abs(a.mu - b.mu) < 1e-11
     assert np.max(np.abs(a.q - b.q)) < 1e-11
     assert abs(a.e_band - b.e_band) < 1e-10
+
+
+def test_collected_count_in_c_equals_plain_sum_and_bisection_meets_the_count():
+    rng = np.random.default_rng(12)
+    eps = [np.sort(rng.uniform(-1.2, 0.4, k)) for k in (7, 11, 5)]
+    w = [rng.uniform(0.0, 1.0, len(e)) for e in eps]
+    beta = 1.0 / (3.166811563e-6 * 3000.0)
+    for mu in (-0.6, -0.1, 0.05):
+        plain = 2.0 * sum(float(np.sum(wi / (1.0 + np.exp(beta * (ei - mu))))) for ei, wi in zip(eps, w))
+        assert abs(J.collected_count(eps, w, mu, beta) - plain) < 1e-12
+    n_e = 0.8 * 2.0 * sum(float(x.sum()) for x in w)
+    mu = J.solve_mu(eps, w, n_e, beta)
+    assert abs(J.collected_count(eps, w, mu, beta) - n_e) < 1e-9
+    assert min(float(e.min()) for e in eps) - 1.0 < mu < max(float(e.max()) for e in eps) + 1.0
+    with pytest.raises(ValueError):
+        J.solve_mu([np.zeros(0)], [np.zeros(0)], 1.0, beta)
